@@ -1,0 +1,243 @@
+/*
+ * gofmm.h -- C ABI of the B300-native GOFMM library (libgofmm.so).
+ *
+ * GOFMM (geometry-oblivious fast multipole method, Yu, Levitt, Reiz, Biros,
+ * SC'17) compresses a dense SPD matrix K, known only through its entries, into
+ * a hierarchical matrix K~ = D + S + UV (§1, eq. hmatrix) and then multiplies
+ * K~ by blocks of right-hand sides.  This library does the compression on the
+ * host in FP64 (Alg. 2) and the evaluation U = K~ W (Alg. 7, Table 2) on one
+ * GPU in hand-written sm_103a kernels.
+ *
+ * Conventions shared by every entry point
+ *  - Return value: GOFMM_OK (0) on success, a negative GOFMM_ERR_* code
+ *    otherwise; gofmm_last_error() then describes the failure (per thread).
+ *  - Indices are 0-based int64.  Dense blocks are row-major.
+ *  - No entry point keeps a pointer the caller passed in after it returns,
+ *    except the callback context of gofmm_entries, which must stay valid for
+ *    the duration of gofmm_compress / gofmm_import only.
+ *  - Nothing here synchronises the device unless the entry point says so.
+ */
+#ifndef GOFMM_H
+#define GOFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes -------------------------------------------------------- */
+#define GOFMM_OK 0
+#define GOFMM_ERR_ARG (-1)         /* invalid argument (null, size, mode)       */
+#define GOFMM_ERR_CALLBACK (-2)    /* the entry callback returned nonzero       */
+#define GOFMM_ERR_NONFINITE (-3)   /* an entry was NaN or Inf                   */
+#define GOFMM_ERR_NOMEM (-4)       /* host or device allocation failed          */
+#define GOFMM_ERR_CUDA (-5)        /* a CUDA runtime call failed                */
+#define GOFMM_ERR_TIMEOUT (-6)     /* a bounded device wait gave up             */
+#define GOFMM_ERR_UNSUPPORTED (-7) /* valid but unsupported combination         */
+#define GOFMM_ERR_IO (-8)          /* file could not be read or written         */
+
+/* ---- how entries of K are obtained (§1 problem statement) ---------------- */
+#define GOFMM_GEN_CALLBACK 0 /* only through gofmm_block_fn                       */
+#define GOFMM_GEN_GAUSSIAN 1 /* K_ij = exp(-|x_i-x_j|^2/(2h^2)) + shift [i==j]   */
+#define GOFMM_GEN_IMQ 2      /* K_ij = 1/sqrt(1+|x_i-x_j|^2/h^2) + shift [i==j]  */
+
+/* ---- partitioning distance (§2.1, §3) ------------------------------------ */
+#define GOFMM_DIST_GRAM_L2 0      /* d_ij^2 = K_ii + K_jj - 2 K_ij ("kernel")   */
+#define GOFMM_DIST_ANGLE 1        /* d_ij = 1 - K_ij^2 / (K_ii K_jj)            */
+#define GOFMM_DIST_LEXICOGRAPHIC 2 /* input order (HSS-style test mode)        */
+#define GOFMM_DIST_RANDOM 3       /* seeded random order                       */
+
+/* ---- far-list construction (§2.2, Algs. 4-5) ----------------------------- */
+#define GOFMM_FAR_SYMMETRIC 0 /* same-level dual traversal: K~ symmetric      */
+#define GOFMM_FAR_PAPER 1     /* FindFar + MergeFar literally (cross-level)   */
+
+/* ---- where the evaluation gets K blocks (Alg. 2 steps 10-11) ------------- */
+#define GOFMM_CACHE_BLOCKS 0 /* Kba / SKba cached at compression, kept in HBM  */
+#define GOFMM_CACHE_NONE 1   /* entries generated inside the evaluation kernels
+                                (generator kinds only)                          */
+
+/* ---- data types and arithmetic of gofmm_evaluate ------------------------- */
+#define GOFMM_DTYPE_F64 0
+#define GOFMM_DTYPE_F32 1
+
+#define GOFMM_PREC_FP64 0   /* FP64 everywhere (parity mode; F64 data)          */
+#define GOFMM_PREC_FP32 1   /* FP32 SIMT everywhere (F32 data)                  */
+#define GOFMM_PREC_TF32 2   /* S2S/S2N/L2L on TF32 tensor cores, FP32 accumulate */
+#define GOFMM_PREC_BF16 3   /* ... on BF16 tensor cores, FP32 accumulate        */
+#define GOFMM_PREC_BF16X3 4 /* ... split BF16 (hi*hi + hi*lo + lo*hi), FP32 acc */
+
+/*
+ * Entry callback: fill out[i*nJ + j] = K(I[i], J[j]) for 0 <= i < nI,
+ * 0 <= j < nJ (row-major, FP64) and return 0.  Any nonzero return aborts the
+ * calling entry point with GOFMM_ERR_CALLBACK.  The library may call it with
+ * any index sets and from one thread at a time.
+ */
+typedef int (*gofmm_block_fn)(void* ctx, const int64_t* I, int64_t nI,
+                              const int64_t* J, int64_t nJ, double* out);
+
+/* The matrix K (N x N, SPD). */
+typedef struct gofmm_entries {
+    int kind;             /* GOFMM_GEN_*                                       */
+    int dim;              /* point dimension (generator kinds)                 */
+    int64_t n;            /* N                                                 */
+    const double* points; /* generator kinds: N x dim row-major host array;
+                             read during the call only.  The method itself only
+                             ever sees entries computed from them.             */
+    double bandwidth;     /* h (Gaussian) or l (IMQ)                           */
+    double diag_shift;    /* added to K_ii (generator kinds)                   */
+    gofmm_block_fn fn;    /* GOFMM_GEN_CALLBACK                                */
+    void* ctx;            /* passed to fn                                      */
+} gofmm_entries;
+
+/* Compression parameters (§3 "Parameter selection"). */
+typedef struct gofmm_params {
+    int64_t leaf_size;      /* m: leaves hold at most m indices               */
+    int64_t max_rank;       /* s: skeletons hold at most s indices            */
+    double tau;             /* adaptive ID tolerance (relative to |R_00|)     */
+    double budget;          /* direct-evaluation budget, fraction of N/m      */
+    int kappa;              /* neighbours per index                           */
+    int distance;           /* GOFMM_DIST_*                                   */
+    int far_mode;           /* GOFMM_FAR_*                                    */
+    int cache_mode;         /* GOFMM_CACHE_*                                  */
+    int n_centroid;         /* centroid sample size of Alg. 1                 */
+    int n_sample;           /* sampled rows I' per ID; 0 = 2 * max_rank       */
+    int ann_max_iter;       /* randomized-tree neighbour search: iterations  */
+    int num_threads;        /* host threads for compression; 0 = all         */
+    double ann_target_recall; /* ... stop once the sampled recall reaches it */
+    int64_t knn_exact_max;  /* exhaustive neighbour search up to this N       */
+    uint64_t seed;          /* seeds every random choice of the method        */
+    int device;             /* CUDA device that will evaluate                 */
+    int reserved;
+} gofmm_params;
+
+/* Figures of a compressed matrix (for the flop/byte accounting). */
+typedef struct gofmm_stats_t {
+    int64_t n, depth, n_leaves;
+    int64_t min_rank, max_rank;     /* over non-root nodes                       */
+    double mean_rank;
+    int64_t near_pairs, far_pairs;  /* ordered pairs                             */
+    int64_t max_near;               /* largest |Near(beta)|                      */
+    /* algorithmic flops per right-hand side column (Table 2, real shapes) */
+    double flops_n2s, flops_s2s, flops_s2n, flops_l2l;
+    /* entries held by the cached K blocks (near, far) */
+    int64_t near_entries, far_entries;
+    int64_t interp_entries;         /* sum over nodes of s * ncols               */
+    int64_t skel_total;             /* sum over non-root nodes of s              */
+    int ann_iterations;
+    double ann_recall;
+    double compress_seconds;
+} gofmm_stats_t;
+
+typedef struct gofmm_handle gofmm_handle;
+
+/* Fill *p with the defaults: m 64, s 64, tau 1e-5, budget 0.03, kappa 32,
+ * Gram-l2 distance, symmetric far lists, cached blocks, n_c 32, I' = 2s,
+ * 10 ANN iterations / 0.8 recall, exhaustive kNN up to N = 16384, seed 0,
+ * device 0. */
+void gofmm_default_params(gofmm_params* p);
+
+/*
+ * Compress K (Alg. 2): neighbour search, metric tree (Alg. 1), Near (Alg. 3,
+ * budget ballot, symmetrised), Far (Algs. 4-5 or the symmetric reading),
+ * adaptive ID skeletons and interpolation matrices (Alg. 6, FP64 pivoted QR +
+ * triangular solve) and, in GOFMM_CACHE_BLOCKS mode, the near blocks K_ba
+ * and far skeleton blocks K_b~a~.  Runs on host cores only; device memory is
+ * taken on the first gofmm_prepare / gofmm_evaluate.
+ *   K   : entries (kind, n, points or callback).
+ *   p   : parameters; NULL means gofmm_default_params.
+ *   out : receives a new handle, owned by the caller (gofmm_free).
+ * Errors: ERR_ARG (n < 1, leaf_size < 1, max_rank < 1, kappa < 1, tau < 0,
+ * unknown mode, CACHE_NONE with a callback), ERR_CALLBACK, ERR_NONFINITE,
+ * ERR_NOMEM.  On error *out is NULL and nothing is leaked.
+ */
+int gofmm_compress(const gofmm_entries* K, const gofmm_params* p, gofmm_handle** out);
+
+/*
+ * Upload the compressed structure to p.device and size the evaluation
+ * workspace for up to r_max right-hand sides in the given precision.
+ * gofmm_evaluate calls this itself when needed; call it first to keep
+ * allocation out of timed regions and before capturing a stream.
+ * Synchronises the device.  Errors: ERR_ARG, ERR_UNSUPPORTED, ERR_NOMEM,
+ * ERR_CUDA.
+ */
+int gofmm_prepare(gofmm_handle* h, int64_t r_max, int precision);
+
+/*
+ * U = K~ W (Alg. 7: N2S, S2S, S2N, L2L) on the device, asynchronously on
+ * `stream` (a cudaStream_t; NULL = legacy default stream).
+ *   W   : device pointer, N x r row-major in the ORIGINAL index order,
+ *         leading dimension ldw >= r, element type `dtype`.
+ *   U   : device pointer, N x r, leading dimension ldu >= r, same dtype;
+ *         overwritten (not accumulated).  W and U must not overlap.
+ *   r   : number of right-hand sides, r >= 1.
+ *   precision : GOFMM_PREC_*; FP64 needs DTYPE_F64, the others DTYPE_F32.
+ * The handle's workspace is reused by every call: calls on one handle must
+ * be ordered (same stream, or synchronised by the caller).
+ * Errors: ERR_ARG, ERR_UNSUPPORTED, ERR_NOMEM, ERR_CUDA.
+ */
+int gofmm_evaluate(gofmm_handle* h, const void* W, int64_t ldw, void* U, int64_t ldu,
+                   int64_t r, int dtype, int precision, void* stream);
+
+/*
+ * As gofmm_evaluate, but W and U are HOST pointers (pinned memory gives the
+ * fastest copies).  Copies W to the device, evaluates, copies U back and
+ * synchronises `stream` before returning.
+ */
+int gofmm_evaluate_host(gofmm_handle* h, const void* W, int64_t ldw, void* U, int64_t ldu,
+                        int64_t r, int dtype, int precision, void* stream);
+
+/* Release the handle and all its host and device memory (synchronises the
+ * device first).  NULL is accepted. */
+int gofmm_free(gofmm_handle* h);
+
+/*
+ * Write the compressed structure (tree order, Near/Far lists, skeletons,
+ * interpolation matrices, parameters) to `path` as a flat little-endian
+ * binary file (checkpoint).  Cached K blocks are not written.
+ */
+int gofmm_export(const gofmm_handle* h, const char* path);
+
+/*
+ * Read a structure written by gofmm_export.  K supplies entries for the
+ * cached blocks (CACHE_BLOCKS) or the in-kernel generator (CACHE_NONE); it
+ * must describe the same matrix as at export time.
+ */
+int gofmm_import(const char* path, const gofmm_entries* K, int cache_mode, int device,
+                 gofmm_handle** out);
+
+/* Figures of the compressed matrix. */
+int gofmm_stats(const gofmm_handle* h, gofmm_stats_t* s);
+
+/*
+ * Stage timing: when enabled, gofmm_evaluate records CUDA events on its
+ * stream around each stage.  gofmm_stage_times then synchronises on the last
+ * event and fills ms[0..4] with the milliseconds of the last call's stages
+ * (0 gather + leaf N2S, 1 inner N2S levels, 2 S2S+S2N levels, 3 leaf S2N+L2L,
+ * 4 whole call).
+ */
+int gofmm_set_timing(gofmm_handle* h, int enable);
+int gofmm_stage_times(gofmm_handle* h, float* ms, int n);
+
+/*
+ * Structure views (for tests and tools).  Each copies into caller memory
+ * and returns the element count; pass out = NULL to query the count.
+ *   what = 0: perm (tree position -> original index), N int64
+ *   what = 1: leaf offsets, n_leaves + 1 int64
+ *   what = 2: near lists as CSR: n_leaves + 1 offsets, then the leaf numbers
+ *   what = 3: far lists as CSR over heap ids: n_nodes + 1 offsets, then heap ids
+ *   what = 4: skeletons as CSR over heap ids (root empty)
+ *   what = 5: interpolation matrices P of all nodes in heap order, each
+ *             s x ncols row-major (ncols = leaf size for a leaf, s_l + s_r
+ *             otherwise), concatenated as doubles
+ * A negative return is an error code (unknown `what`, NULL handle).
+ */
+int64_t gofmm_view(const gofmm_handle* h, int what, void* out);
+
+/* Description of the last error on this thread ("" if none). */
+const char* gofmm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GOFMM_H */

@@ -179,6 +179,15 @@ def knn_key(kind: str, kii, kjj, kij):
     raise ValueError(kind)
 
 
+def metric_of(distance: str) -> str:
+    """Distance used wherever one is needed (neighbour search, splits): the
+    angle distance when chosen, the Gram-l2 distance otherwise -- the
+    lexicographic and random partitionings still need neighbours for the
+    near lists and the row sampling (reading: §3 lists them as
+    partitionings only)."""
+    return ANGLE if distance == ANGLE else GRAM_L2
+
+
 def tree_depth(n: int, m: int) -> int:
     """Reading of §2.1 "splitting terminates at leaf size m" for a complete
     tree: the depth is the smallest L with ceil(n / 2^L) <= m, and every node
@@ -336,23 +345,23 @@ def all_nearest_neighbors(K, diagK, n: int, prm: Params):
     (neighbours, iterations, recall)."""
     kappa = min(prm.kappa, n)
     if n <= prm.knn_exact_max:
-        c, _ = knn_exact(K, diagK, np.arange(n), n, kappa, prm.distance)
+        c, _ = knn_exact(K, diagK, np.arange(n), n, kappa, metric_of(prm.distance))
         return c, 0, 1.0
     cur_c = np.full((n, kappa), -1, dtype=np.int64)
     cur_k = np.full((n, kappa), np.inf)
     sample = np.sort(partial_shuffle(np.arange(n, dtype=np.int64), min(100, n),
                                      stream_key(prm.seed, _P_ANN_RECALL, 0)))
-    exact_c, _ = knn_exact(K, diagK, sample, n, kappa, prm.distance)
+    exact_c, _ = knn_exact(K, diagK, sample, n, kappa, metric_of(prm.distance))
     recall = 0.0
     it = 0
     for it in range(1, prm.ann_max_iter + 1):
         def split(idx, h, _it=it):
-            return random_split(K, diagK, idx, prm.distance,
+            return random_split(K, diagK, idx, metric_of(prm.distance),
                                 stream_key(prm.seed, _P_ANN_SPLIT, (_it << 24) | h))
         tr = build_tree(K, diagK, n, prm, split=split)
         for b in range(tr.n_leaves):
             lf = tr.node_idx[tr.leaf_node(b)]
-            D = knn_key(prm.distance, diagK[lf][:, None], diagK[lf][None, :], K(lf, lf))
+            D = knn_key(metric_of(prm.distance), diagK[lf][:, None], diagK[lf][None, :], K(lf, lf))
             # unfilled slots carry distinct placeholder ids >= n and an
             # infinite key, so they sort after every real candidate
             cc = np.where(cur_c[lf] < 0, n + np.arange(kappa)[None, :], cur_c[lf])

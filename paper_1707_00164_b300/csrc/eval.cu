@@ -1,0 +1,592 @@
+// Device side of the GOFMM evaluation U = K~ W (Alg. 7, Table 2) on one GPU.
+//
+// Launch sequence of one evaluation (all on the caller's stream):
+//   stage 0  gather W (original order) into tree order WT, then the leaf
+//            N2S tasks  w~_b = P_{b~b} WT[b]                   (Table 2 N2S)
+//   stage 1  one grouped launch per inner level, bottom-up:
+//            w~_a = P_{a~[l~r~]} [w~_l; w~_r]                  (N2S, POST)
+//   stage 2  one grouped launch per level, top-down:
+//            u~_b = sum_{a in Far(b)} K_{b~a~} w~_a            (S2S)
+//                 + (P^T_{p~[l~r~]} u~_p)[rows of b]           (S2N, PRE)
+//   stage 3  one grouped launch over the leaves, scattered to the original
+//            order:  U[b] = P^T_{b~b} u~_b + sum_{a in Near(b)} K_{ba} WT[a]
+//                                                              (S2N leaf + L2L)
+// Every launch is a grouped GEMM (eval_plan.hpp) whose tasks own disjoint
+// output rows; the sum over slabs runs in a fixed order inside one CTA, so
+// results are deterministic and nothing is accumulated with atomics.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+
+#include "eval_plan.hpp"
+#include "eval_state.hpp"
+
+namespace gofmm {
+
+// ------------------------------------------------------------- kernels --
+namespace {
+
+// WT[i, :] = W[perm[i], :]  (step a0: tree-order gather)
+template <typename T>
+__global__ void gather_rows_kernel(const T* __restrict__ W, int64_t ldw, const int64_t* __restrict__ perm,
+                                   T* __restrict__ WT, int64_t n, int r) {
+    const int64_t row = int64_t(blockIdx.x) * blockDim.y + threadIdx.y;
+    if (row >= n) return;
+    const T* src = W + perm[row] * ldw;
+    T* dst = WT + row * int64_t(r);
+    for (int c = threadIdx.x; c < r; c += blockDim.x) dst[c] = src[c];
+}
+
+// Cached K blocks generated from the points in FP64 (Kba / SKba caching of
+// Alg. 2 steps 10-11, done on the device for generator matrices).
+template <typename T>
+__global__ void gen_blocks_kernel(const GenBlock* __restrict__ blks, const int64_t* __restrict__ idx,
+                                  const double* __restrict__ pts, int dim, int kind, double h, double shift,
+                                  T* __restrict__ dst) {
+    const GenBlock b = blks[blockIdx.x];
+    const int64_t total = int64_t(b.nr) * b.nc;
+    const double two_h2 = 2.0 * h * h, h2 = h * h;
+    for (int64_t e = int64_t(blockIdx.y) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.y) * blockDim.x) {
+        const int i = int(e / b.nc), j = int(e % b.nc);
+        const int64_t ri = idx[b.roff + i], cj = idx[b.coff + j];
+        double acc = 0.0;
+        for (int d = 0; d < dim; ++d) {
+            const double t = pts[ri * dim + d] - pts[cj * dim + d];
+            acc += t * t;
+        }
+        double v = kind == GOFMM_GEN_GAUSSIAN ? exp(-(acc / two_h2)) : 1.0 / sqrt(1.0 + acc / h2);
+        if (ri == cj) v += shift;
+        dst[b.dst + e] = T(v);
+    }
+}
+
+template <typename T>
+struct GemmParams {
+    const Task* tasks;
+    const Tile* tiles;
+    const Slab* slabs;
+    const T* kstore;
+    const T* pstore;
+    const T* b0;
+    const T* b1;
+    const T* b2;
+    int64_t ldb;
+    const int64_t* idx;
+    const T* pts;
+    int dim, gen_kind;
+    T gen_inv, gen_shift;  // Gaussian: exp(-d2*inv), inv = 1/(2h^2); IMQ: rsqrt(1 + d2*inv), inv = 1/h^2
+    T* out;
+    int64_t ldo;
+    const int64_t* out_map;
+    int r;
+};
+
+__device__ __forceinline__ double kexp(double x) { return exp(x); }
+__device__ __forceinline__ float kexp(float x) { return expf(x); }
+__device__ __forceinline__ double krsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float krsqrt(float x) { return rsqrtf(x); }
+
+// Kernel entry K(i, j) generated in the working precision (fused sampling).
+template <typename T>
+__device__ __forceinline__ T gen_entry(const GemmParams<T>& p, int64_t ri, int64_t cj) {
+    T acc = T(0);
+    for (int d = 0; d < p.dim; ++d) {
+        const T t = p.pts[ri * p.dim + d] - p.pts[cj * p.dim + d];
+        acc += t * t;
+    }
+    T v = p.gen_kind == GOFMM_GEN_GAUSSIAN ? kexp(-acc * p.gen_inv) : krsqrt(T(1) + acc * p.gen_inv);
+    if (ri == cj) v += p.gen_shift;
+    return v;
+}
+
+// Grouped GEMM on CUDA cores (FP64 parity mode and the plain FP32 mode).
+// CTA tile BM x BN = (16 TM) x (16 TN), 256 threads, each owning TM x TN
+// outputs split in two halves of the tile for conflict-free shared reads.
+template <typename T, int TM, int TN>
+__global__ void __launch_bounds__(256) gemm_simt_kernel(const GemmParams<T> p) {
+    constexpr int BM = 16 * TM, BN = 16 * TN, BK = 8;
+    __shared__ T As[BK][BM];
+    __shared__ T Bs[BK][BN];
+    const Tile tl = p.tiles[blockIdx.x];
+    const Task tk = p.tasks[tl.task];
+    const int m0 = tl.m0;
+    const int n0 = blockIdx.y * BN;
+    const int mrows = min(BM, tk.m - m0);
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    T acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+
+    for (int si = tk.slab0; si < tk.slab1; ++si) {
+        const Slab sl = p.slabs[si];
+        const T* bptr = (sl.b_src == B_WT ? p.b0 : sl.b_src == B_WTIL ? p.b1 : p.b2) + sl.b_row * p.ldb;
+        const T* aptr = (sl.a_src == A_KSTORE ? p.kstore : p.pstore) + sl.a_off;
+        for (int k0 = 0; k0 < sl.k; k0 += BK) {
+            for (int e = tid; e < BM * BK; e += 256) {
+                const int mm = e / BK, kk = e % BK;
+                T v = T(0);
+                if (mm < mrows && k0 + kk < sl.k) {
+                    if (sl.a_src == A_GEN)
+                        v = gen_entry(p, p.idx[sl.a_off + m0 + mm], p.idx[sl.a_col + k0 + kk]);
+                    else
+                        v = aptr[int64_t(m0 + mm) * sl.lda + k0 + kk];
+                }
+                As[kk][mm] = v;
+            }
+            for (int e = tid; e < BK * BN; e += 256) {
+                const int kk = e / BN, nn = e % BN;
+                T v = T(0);
+                if (k0 + kk < sl.k && n0 + nn < p.r) v = bptr[int64_t(k0 + kk) * p.ldb + n0 + nn];
+                Bs[kk][nn] = v;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                T a[TM], b[TN];
+#pragma unroll
+                for (int i = 0; i < TM; ++i)
+                    a[i] = As[kk][i < TM / 2 ? ty * (TM / 2) + i : BM / 2 + ty * (TM / 2) + i - TM / 2];
+#pragma unroll
+                for (int j = 0; j < TN; ++j)
+                    b[j] = Bs[kk][j < TN / 2 ? tx * (TN / 2) + j : BN / 2 + tx * (TN / 2) + j - TN / 2];
+#pragma unroll
+                for (int i = 0; i < TM; ++i)
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int row = i < TM / 2 ? ty * (TM / 2) + i : BM / 2 + ty * (TM / 2) + i - TM / 2;
+        if (row >= mrows) continue;
+        int64_t orow = tk.out_row + m0 + row;
+        if (p.out_map) orow = p.out_map[orow];
+        T* o = p.out + orow * p.ldo;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int col = n0 + (j < TN / 2 ? tx * (TN / 2) + j : BN / 2 + tx * (TN / 2) + j - TN / 2);
+            if (col < p.r) o[col] = acc[i][j];
+        }
+    }
+}
+
+}  // namespace
+
+static void build_plan(const Structure& st, bool cached, DeviceState& D) {
+    const int64_t nn = st.n_nodes(), nl = st.n_leaves(), N = st.n;
+    const int L = st.depth;
+    D.n = N;
+    D.skel_off.assign(nn, -1);
+    int64_t S = 0;
+    for (int64_t h = 1; h < nn; ++h) { D.skel_off[h] = S; S += int64_t(st.skel[h].size()); }
+    D.S_tot = S;
+    D.idx = st.perm;
+    for (int64_t h = 1; h < nn; ++h) D.idx.insert(D.idx.end(), st.skel[h].begin(), st.skel[h].end());
+    // P-store: P_h (s x ncols) then P_h^T (ncols x s)
+    D.p_off.assign(nn, -1);
+    D.pt_off.assign(nn, -1);
+    D.pstore_host.clear();
+    for (int64_t h = 1; h < nn; ++h) {
+        const int64_t s = int64_t(st.skel[h].size()), nc = st.ncols(h);
+        D.p_off[h] = int64_t(D.pstore_host.size());
+        D.pstore_host.insert(D.pstore_host.end(), st.P[h].begin(), st.P[h].end());
+        D.pt_off[h] = int64_t(D.pstore_host.size());
+        for (int64_t c = 0; c < nc; ++c)
+            for (int64_t t = 0; t < s; ++t) D.pstore_host.push_back(st.P[h][size_t(t * nc + c)]);
+    }
+    D.pstore_elems = int64_t(D.pstore_host.size());
+    // K-store layout
+    D.kblocks.clear();
+    std::vector<std::vector<int64_t>> near_koff(nl), far_koff(nn);
+    int64_t K = 0;
+    for (int64_t b = 0; b < nl; ++b) {
+        const int64_t hb = st.leaf_node(b);
+        for (int64_t a : st.near[b]) {
+            const int64_t ha = st.leaf_node(a);
+            near_koff[b].push_back(K);
+            D.kblocks.push_back(GenBlock{K, st.node_off[hb], st.node_off[ha], int32_t(st.node_size[hb]),
+                                         int32_t(st.node_size[ha])});
+            K += st.node_size[hb] * st.node_size[ha];
+        }
+    }
+    for (int64_t h = 1; h < nn; ++h)
+        for (int64_t a : st.far[h]) {
+            far_koff[h].push_back(K);
+            const int64_t sh = int64_t(st.skel[h].size()), sa = int64_t(st.skel[a].size());
+            D.kblocks.push_back(GenBlock{K, N + D.skel_off[h], N + D.skel_off[a], int32_t(sh), int32_t(sa)});
+            K += sh * sa;
+        }
+    D.kstore_elems = cached ? K : 0;
+
+    // u~ is identically zero below nodes with no far field on the path to
+    // the root; those tasks and the push slabs reading them are skipped.
+    std::vector<char> field(nn, 0);
+    for (int64_t h = 1; h < nn; ++h) field[h] = !st.far[h].empty() || (h > 0 && field[(h - 1) / 2]);
+
+    D.launches.clear();
+    auto add_launch = [&](int out_buf, int stage) -> Launch& {
+        D.launches.emplace_back();
+        D.launches.back().out_buf = out_buf;
+        D.launches.back().stage = stage;
+        return D.launches.back();
+    };
+    auto slab = [](int a_src, int64_t a_off, int64_t a_col, int lda, int k, int b_src, int64_t b_row) {
+        Slab s;
+        s.a_off = a_off; s.a_col = a_col; s.b_row = b_row; s.k = k; s.lda = lda; s.a_src = a_src; s.b_src = b_src;
+        return s;
+    };
+    if (L == 0) {
+        // a single leaf: U = K W
+        Launch& lo = add_launch(OUT_U, 3);
+        Task t{0, int32_t(N), 0, 0, 0};
+        lo.slabs.push_back(cached ? slab(A_KSTORE, 0, 0, int(N), int(N), B_WT, 0)
+                                  : slab(A_GEN, 0, 0, 0, int(N), B_WT, 0));
+        t.slab1 = 1;
+        lo.tasks.push_back(t);
+        return;
+    }
+    // stage 0: leaf N2S
+    {
+        Launch& l = add_launch(OUT_WTIL, 0);
+        for (int64_t b = 0; b < nl; ++b) {
+            const int64_t h = st.leaf_node(b);
+            Task t{D.skel_off[h], int32_t(st.skel[h].size()), int32_t(l.slabs.size()), 0, 0};
+            l.slabs.push_back(slab(A_PSTORE, D.p_off[h], 0, int(st.node_size[h]), int(st.node_size[h]), B_WT,
+                                   st.node_off[h]));
+            t.slab1 = int32_t(l.slabs.size());
+            l.tasks.push_back(t);
+        }
+    }
+    // stage 1: inner N2S, bottom-up
+    for (int lvl = L - 1; lvl >= 1; --lvl) {
+        Launch& l = add_launch(OUT_WTIL, 1);
+        for (int64_t h = (int64_t(1) << lvl) - 1; h < (int64_t(2) << lvl) - 1; ++h) {
+            const int nc = int(st.ncols(h));
+            Task t{D.skel_off[h], int32_t(st.skel[h].size()), int32_t(l.slabs.size()), 0, 0};
+            l.slabs.push_back(slab(A_PSTORE, D.p_off[h], 0, nc, nc, B_WTIL, D.skel_off[2 * h + 1]));
+            t.slab1 = int32_t(l.slabs.size());
+            l.tasks.push_back(t);
+        }
+    }
+    // stage 2: S2S + S2N push, top-down
+    for (int lvl = 1; lvl <= L; ++lvl) {
+        Launch& l = add_launch(OUT_UTIL, 2);
+        for (int64_t h = (int64_t(1) << lvl) - 1; h < (int64_t(2) << lvl) - 1; ++h) {
+            if (!field[h]) continue;
+            const int64_t sh = int64_t(st.skel[h].size());
+            Task t{D.skel_off[h], int32_t(sh), int32_t(l.slabs.size()), 0, 0};
+            for (size_t u = 0; u < st.far[h].size(); ++u) {
+                const int64_t a = st.far[h][u];
+                const int sa = int(st.skel[a].size());
+                l.slabs.push_back(cached ? slab(A_KSTORE, far_koff[h][u], 0, sa, sa, B_WTIL, D.skel_off[a])
+                                         : slab(A_GEN, N + D.skel_off[h], N + D.skel_off[a], 0, sa, B_WTIL,
+                                                D.skel_off[a]));
+            }
+            const int64_t p = (h - 1) / 2;
+            if (p > 0 && field[p]) {
+                const int sp = int(st.skel[p].size());
+                const int64_t rowoff = (h == 2 * p + 1) ? 0 : int64_t(st.skel[2 * p + 1].size());
+                l.slabs.push_back(slab(A_PSTORE, D.pt_off[p] + rowoff * sp, 0, sp, sp, B_UTIL, D.skel_off[p]));
+            }
+            t.slab1 = int32_t(l.slabs.size());
+            l.tasks.push_back(t);
+        }
+        if (l.tasks.empty()) D.launches.pop_back();
+    }
+    // stage 3: leaf S2N + L2L, scattered to the original order
+    {
+        Launch& l = add_launch(OUT_U, 3);
+        for (int64_t b = 0; b < nl; ++b) {
+            const int64_t h = st.leaf_node(b);
+            Task t{st.node_off[h], int32_t(st.node_size[h]), int32_t(l.slabs.size()), 0, 0};
+            for (size_t u = 0; u < st.near[b].size(); ++u) {
+                const int64_t ha = st.leaf_node(st.near[b][u]);
+                const int na = int(st.node_size[ha]);
+                l.slabs.push_back(cached ? slab(A_KSTORE, near_koff[b][u], 0, na, na, B_WT, st.node_off[ha])
+                                         : slab(A_GEN, st.node_off[h], st.node_off[ha], 0, na, B_WT,
+                                                st.node_off[ha]));
+            }
+            if (field[h]) {
+                const int sh = int(st.skel[h].size());
+                l.slabs.push_back(slab(A_PSTORE, D.pt_off[h], 0, sh, sh, B_UTIL, D.skel_off[h]));
+            }
+            t.slab1 = int32_t(l.slabs.size());
+            l.tasks.push_back(t);
+        }
+    }
+    // heaviest tasks first inside every launch (better tail behaviour)
+    for (Launch& l : D.launches) {
+        std::vector<int64_t> work(l.tasks.size());
+        for (size_t i = 0; i < l.tasks.size(); ++i) {
+            int64_t k = 0;
+            for (int s = l.tasks[i].slab0; s < l.tasks[i].slab1; ++s) k += l.slabs[s].k;
+            work[i] = k * l.tasks[i].m;
+        }
+        std::vector<size_t> o(l.tasks.size());
+        for (size_t i = 0; i < o.size(); ++i) o[i] = i;
+        std::stable_sort(o.begin(), o.end(), [&](size_t a, size_t b) { return work[a] > work[b]; });
+        std::vector<Task> t2;
+        for (size_t i : o) t2.push_back(l.tasks[i]);
+        l.tasks = t2;
+    }
+}
+
+std::pair<Tile*, int> tiles_for(Launch& l, int bm) {
+    auto it = l.tiles.find(bm);
+    if (it != l.tiles.end()) return it->second;
+    std::vector<Tile> t;
+    for (size_t i = 0; i < l.tasks.size(); ++i)
+        for (int m0 = 0; m0 < std::max(l.tasks[i].m, 1); m0 += bm) t.push_back(Tile{int32_t(i), m0});
+    auto v = std::make_pair(dupload(t), int(t.size()));
+    l.tiles[bm] = v;
+    return v;
+}
+
+static void ensure_base(Handle& H) {
+    if (H.dev) return;
+    const Structure& st = H.st;
+    const bool cached = st.prm.cache_mode == GOFMM_CACHE_BLOCKS;
+    auto D = std::make_unique<DeviceState>();
+    D->device = st.prm.device;
+    build_plan(st, cached, *D);
+    D->d_idx = dupload(D->idx);
+    for (Launch& l : D->launches) {
+        l.d_tasks = dupload(l.tasks);
+        l.d_slabs = dupload(l.slabs);
+    }
+    D->d_kblocks = dupload(D->kblocks);
+    if (H.K.is_generator()) {
+        D->d_pts64 = dupload(H.K.pts);
+        std::vector<float> p32(H.K.pts.begin(), H.K.pts.end());
+        D->d_pts32 = dupload(p32);
+    }
+    for (int i = 0; i < 5; ++i) CUDA_OK(cudaEventCreate(&D->ev[i]));
+    D->ev_ok = true;
+    H.dev = D.release();
+}
+
+template <typename T>
+static void ensure_stores(Handle& H, int fi) {
+    DeviceState& D = *H.dev;
+    Family& F = D.fam[fi];
+    if (F.stores) return;
+    const Structure& st = H.st;
+    std::vector<T> ps(D.pstore_host.begin(), D.pstore_host.end());
+    F.pstore = dupload(ps);
+    if (D.kstore_elems > 0) {
+        T* ks = dalloc<T>(size_t(D.kstore_elems));
+        F.kstore = ks;
+        if (H.K.is_generator()) {
+            if (!D.kblocks.empty()) {
+                dim3 grid(unsigned(D.kblocks.size()), 8);
+                gen_blocks_kernel<T><<<grid, 256>>>(D.d_kblocks, D.d_idx, D.d_pts64, H.K.dim, H.K.kind, H.K.h,
+                                                    H.K.shift, ks);
+                CUDA_OK(cudaGetLastError());
+            }
+        } else {
+            std::vector<T> host(size_t(D.kstore_elems));
+            size_t pos = 0;
+            for (const auto& lst : st.near_blocks)
+                for (const auto& blk : lst)
+                    for (double v : blk) host[pos++] = T(v);
+            for (const auto& lst : st.far_blocks)
+                for (const auto& blk : lst)
+                    for (double v : blk) host[pos++] = T(v);
+            if (int64_t(pos) != D.kstore_elems) fail(GOFMM_ERR_ARG, "cached blocks do not match the plan");
+            CUDA_OK(cudaMemcpy(ks, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice));
+        }
+        CUDA_OK(cudaDeviceSynchronize());
+    }
+    F.stores = true;
+}
+
+template <typename T>
+static void ensure_workspace(Handle& H, int fi, int64_t r) {
+    DeviceState& D = *H.dev;
+    Family& F = D.fam[fi];
+    if (F.ws_r >= r) return;
+    dfree(F.WT); dfree(F.WTIL); dfree(F.UTIL); dfree(F.dW); dfree(F.dU);
+    F.WT = F.WTIL = F.UTIL = F.dW = F.dU = nullptr;
+    F.ws_r = 0;
+    F.WT = dalloc<T>(size_t(D.n * r));
+    F.WTIL = dalloc<T>(size_t(std::max<int64_t>(D.S_tot, 1) * r));
+    F.UTIL = dalloc<T>(size_t(std::max<int64_t>(D.S_tot, 1) * r));
+    F.ws_r = r;
+}
+
+template <typename T>
+static void ensure_staging(Handle& H, int fi, int64_t r) {
+    Family& F = H.dev->fam[fi];
+    if (F.dW) return;
+    F.dW = dalloc<T>(size_t(H.dev->n * F.ws_r));
+    F.dU = dalloc<T>(size_t(H.dev->n * F.ws_r));
+    (void)r;
+}
+
+static int family_of(int precision) { return precision == GOFMM_PREC_FP64 ? 0 : 1; }
+
+void device_prepare(Handle& H, int64_t r_max, int precision) {
+    if (r_max < 1) fail(GOFMM_ERR_ARG, "r_max must be >= 1");
+    if (precision < GOFMM_PREC_FP64 || precision > GOFMM_PREC_BF16X3) fail(GOFMM_ERR_ARG, "unknown precision");
+    DeviceGuard g(H.st.prm.device);
+    ensure_base(H);
+    if (family_of(precision) == 0) {
+        ensure_stores<double>(H, 0);
+        ensure_workspace<double>(H, 0, r_max);
+    } else {
+        ensure_stores<float>(H, 1);
+        ensure_workspace<float>(H, 1, r_max);
+        if (precision != GOFMM_PREC_FP32) tc_prepare(H, *H.dev, r_max, precision);
+    }
+    CUDA_OK(cudaDeviceSynchronize());
+}
+
+template <typename T, int TM, int TN>
+static int run_simt(Handle& H, const T* W, int64_t ldw, T* U, int64_t ldu, int r, cudaStream_t s) {
+    DeviceState& D = *H.dev;
+    Family& F = D.fam[std::is_same<T, double>::value ? 0 : 1];
+    constexpr int BM = 16 * TM, BN = 16 * TN;
+    T* WT = static_cast<T*>(F.WT);
+    T* WTIL = static_cast<T*>(F.WTIL);
+    T* UTIL = static_cast<T*>(F.UTIL);
+    int launches = 0;
+    const bool timing = H.timing && D.ev_ok;
+    if (timing) CUDA_OK(cudaEventRecord(D.ev[0], s));
+    {
+        dim3 blk(32, 8), grid(unsigned((D.n + 7) / 8));
+        gather_rows_kernel<T><<<grid, blk, 0, s>>>(W, ldw, D.d_idx, WT, D.n, r);
+        CUDA_OK(cudaGetLastError());
+        ++launches;
+    }
+    GemmParams<T> p{};
+    p.kstore = static_cast<const T*>(F.kstore);
+    p.pstore = static_cast<const T*>(F.pstore);
+    p.b0 = WT; p.b1 = WTIL; p.b2 = UTIL;
+    p.ldb = r;
+    p.idx = D.d_idx;
+    p.pts = std::is_same<T, double>::value ? reinterpret_cast<const T*>(D.d_pts64)
+                                           : reinterpret_cast<const T*>(D.d_pts32);
+    p.dim = H.K.dim;
+    p.gen_kind = H.K.kind;
+    p.gen_inv = H.K.kind == GOFMM_GEN_GAUSSIAN ? T(1.0 / (2.0 * H.K.h * H.K.h)) : T(1.0 / (H.K.h * H.K.h));
+    p.gen_shift = T(H.K.shift);
+    p.r = r;
+    int stage_done = 0;
+    for (size_t li = 0; li < D.launches.size(); ++li) {
+        Launch& l = D.launches[li];
+        while (timing && stage_done < l.stage) { CUDA_OK(cudaEventRecord(D.ev[++stage_done], s)); }
+        auto tl = tiles_for(l, BM);
+        if (tl.second == 0) continue;
+        p.tasks = l.d_tasks;
+        p.slabs = l.d_slabs;
+        p.tiles = tl.first;
+        if (l.out_buf == OUT_U) { p.out = U; p.ldo = ldu; p.out_map = D.d_idx; }
+        else { p.out = l.out_buf == OUT_WTIL ? WTIL : UTIL; p.ldo = r; p.out_map = nullptr; }
+        dim3 grid(unsigned(tl.second), unsigned((r + BN - 1) / BN));
+        gemm_simt_kernel<T, TM, TN><<<grid, 256, 0, s>>>(p);
+        CUDA_OK(cudaGetLastError());
+        ++launches;
+    }
+    while (timing && stage_done < 4) { CUDA_OK(cudaEventRecord(D.ev[++stage_done], s)); }
+    return launches;
+}
+
+void device_evaluate(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu, int64_t r, int dtype,
+                     int precision, void* stream, bool host_buffers) {
+    if (!W || !U) fail(GOFMM_ERR_ARG, "W and U must not be NULL");
+    if (r < 1 || r > (int64_t(1) << 30)) fail(GOFMM_ERR_ARG, "r must be >= 1");
+    if (ldw < r || ldu < r) fail(GOFMM_ERR_ARG, "leading dimensions must be >= r");
+    if (precision < GOFMM_PREC_FP64 || precision > GOFMM_PREC_BF16X3) fail(GOFMM_ERR_ARG, "unknown precision");
+    if (dtype != GOFMM_DTYPE_F64 && dtype != GOFMM_DTYPE_F32) fail(GOFMM_ERR_ARG, "unknown dtype");
+    if ((precision == GOFMM_PREC_FP64) != (dtype == GOFMM_DTYPE_F64))
+        fail(GOFMM_ERR_UNSUPPORTED, "FP64 precision needs F64 data and the other precisions F32 data");
+    const size_t es = dtype == GOFMM_DTYPE_F64 ? 8 : 4;
+    {
+        const char* w0 = static_cast<const char*>(W);
+        const char* u0 = static_cast<const char*>(U);
+        const size_t span_w = size_t(H.st.n - 1) * size_t(ldw) * es + size_t(r) * es;
+        const size_t span_u = size_t(H.st.n - 1) * size_t(ldu) * es + size_t(r) * es;
+        if (w0 < u0 + span_u && u0 < w0 + span_w) fail(GOFMM_ERR_ARG, "W and U overlap");
+    }
+    DeviceGuard g(H.st.prm.device);
+    const int fi = family_of(precision);
+    Family* F = H.dev ? &H.dev->fam[fi] : nullptr;
+    const bool ready = H.dev && F->stores && F->ws_r >= r &&
+                       (precision <= GOFMM_PREC_FP32 || tc_ready(*H.dev, r, precision));
+    if (!ready) device_prepare(H, std::max<int64_t>(r, F ? F->ws_r : 0), precision);
+    DeviceState& D = *H.dev;
+    F = &D.fam[fi];
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const void* Wd = W;
+    void* Ud = U;
+    int64_t ldw_d = ldw, ldu_d = ldu;
+    if (host_buffers) {
+        if (fi == 0) ensure_staging<double>(H, 0, r);
+        else ensure_staging<float>(H, 1, r);
+        CUDA_OK(cudaMemcpy2DAsync(F->dW, size_t(r) * es, W, size_t(ldw) * es, size_t(r) * es, size_t(D.n),
+                                  cudaMemcpyHostToDevice, s));
+        Wd = F->dW;
+        Ud = F->dU;
+        ldw_d = ldu_d = r;
+    }
+    if (precision == GOFMM_PREC_FP64)
+        D.last_launches = run_simt<double, 4, 4>(H, static_cast<const double*>(Wd), ldw_d,
+                                                 static_cast<double*>(Ud), ldu_d, int(r), s);
+    else if (precision == GOFMM_PREC_FP32)
+        D.last_launches = run_simt<float, 8, 8>(H, static_cast<const float*>(Wd), ldw_d,
+                                                static_cast<float*>(Ud), ldu_d, int(r), s);
+    else
+        D.last_launches = tc_run(H, D, static_cast<const float*>(Wd), ldw_d, static_cast<float*>(Ud), ldu_d,
+                                 int(r), precision, s);
+    if (host_buffers) {
+        CUDA_OK(cudaMemcpy2DAsync(U, size_t(ldu) * es, F->dU, size_t(r) * es, size_t(r) * es, size_t(D.n),
+                                  cudaMemcpyDeviceToHost, s));
+        CUDA_OK(cudaStreamSynchronize(s));
+    }
+}
+
+void device_stage_times(Handle& H, float* ms, int n) {
+    if (!H.dev || !H.dev->ev_ok) fail(GOFMM_ERR_ARG, "no evaluation recorded");
+    DeviceState& D = *H.dev;
+    DeviceGuard g(H.st.prm.device);
+    CUDA_OK(cudaEventSynchronize(D.ev[4]));
+    float t[5] = {0, 0, 0, 0, 0};
+    for (int i = 0; i < 4; ++i) CUDA_OK(cudaEventElapsedTime(&t[i], D.ev[i], D.ev[i + 1]));
+    CUDA_OK(cudaEventElapsedTime(&t[4], D.ev[0], D.ev[4]));
+    for (int i = 0; i < n && i < 5; ++i) ms[i] = t[i];
+    if (n > 5) ms[5] = float(D.last_launches);
+}
+
+void device_destroy(Handle& H) {
+    if (!H.dev) return;
+    DeviceState* D = H.dev;
+    H.dev = nullptr;
+    int old = -1;
+    cudaGetDevice(&old);
+    cudaSetDevice(D->device);
+    cudaDeviceSynchronize();
+    tc_destroy(*D);
+    for (Launch& l : D->launches) {
+        dfree(l.d_tasks);
+        dfree(l.d_slabs);
+        for (auto& kv : l.tiles) dfree(kv.second.first);
+    }
+    dfree(D->d_idx); dfree(D->d_pts64); dfree(D->d_pts32); dfree(D->d_kblocks);
+    for (Family& F : D->fam) {
+        dfree(F.kstore); dfree(F.pstore); dfree(F.WT); dfree(F.WTIL); dfree(F.UTIL); dfree(F.dW); dfree(F.dU);
+    }
+    if (D->ev_ok)
+        for (auto& e : D->ev) cudaEventDestroy(e);
+    delete D;
+    if (old >= 0) cudaSetDevice(old);
+}
+
+}  // namespace gofmm

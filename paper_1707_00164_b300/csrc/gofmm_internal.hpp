@@ -1,0 +1,145 @@
+// Internal types of libgofmm: host-side compressed structure, parameters and
+// the device-side evaluation plan.  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "gofmm.h"
+
+namespace gofmm {
+
+// Failure carried to the ABI boundary, where it becomes a return code plus
+// gofmm_last_error().
+struct Error {
+    int code;
+    std::string msg;
+};
+[[noreturn]] void fail(int code, const std::string& msg);
+
+// ---------------------------------------------------------------------------
+// Counter-based random numbers: SplitMix64 (Steele, Lea, Flood, OOPSLA 2014).
+// Output i of the stream keyed by `key` is mix64(key + (i+1) * gamma).  Every
+// random choice of the method (centroid samples of Alg. 1, random projection
+// splits, ANN recall sample, importance-sampled rows) comes from a stream
+// keyed by (seed, purpose, id).
+// ---------------------------------------------------------------------------
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+inline uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+inline uint64_t sm_output(uint64_t key, uint64_t i) { return mix64(key + (i + 1) * kGamma); }
+enum Purpose : uint64_t { kCentroid = 1, kAnnSplit = 2, kAnnRecall = 3, kSample = 4, kRandomPerm = 5 };
+inline uint64_t stream_key(uint64_t seed, uint64_t purpose, uint64_t sub) {
+    return sm_output(seed, (purpose << 40) | sub);
+}
+// First k entries of a Fisher-Yates shuffle of a driven by the stream `key`
+// (step t swaps t with t + (u_t mod (n - t))); `a` is modified in place.
+void partial_shuffle(std::vector<int64_t>& a, int64_t k, uint64_t key);
+
+// ---------------------------------------------------------------------------
+// Entries of K: generator (Gaussian / IMQ from points) or user callback.
+// ---------------------------------------------------------------------------
+struct Entries {
+    int kind = GOFMM_GEN_CALLBACK;
+    int dim = 0;
+    int64_t n = 0;
+    std::vector<double> pts;  // generator kinds: N x dim
+    double h = 1.0, shift = 0.0;
+    gofmm_block_fn fn = nullptr;
+    void* ctx = nullptr;
+
+    // out[i*nJ + j] = K(I[i], J[j]); throws Error on callback failure or a
+    // non-finite entry.
+    void block(const int64_t* I, int64_t nI, const int64_t* J, int64_t nJ, double* out) const;
+    double diag(int64_t i) const;
+    bool is_generator() const { return kind != GOFMM_GEN_CALLBACK; }
+};
+
+struct Params {
+    int64_t m = 64, s = 64;
+    double tau = 1e-5, budget = 0.03;
+    int kappa = 32, distance = GOFMM_DIST_GRAM_L2, far_mode = GOFMM_FAR_SYMMETRIC;
+    int cache_mode = GOFMM_CACHE_BLOCKS;
+    int n_centroid = 32, n_sample = 0, ann_max_iter = 10, num_threads = 0;
+    double ann_target_recall = 0.8;
+    int64_t knn_exact_max = 16384;
+    uint64_t seed = 0;
+    int device = 0;
+};
+
+// ---------------------------------------------------------------------------
+// Compressed structure (host, FP64).  Nodes use heap numbering: root 0,
+// children 2h+1 and 2h+2, every leaf at depth `depth`.
+// ---------------------------------------------------------------------------
+struct Structure {
+    Params prm;
+    int64_t n = 0;
+    int depth = 0;
+    std::vector<int64_t> perm;            // tree position -> original index
+    std::vector<int64_t> node_off;        // per node: first tree position
+    std::vector<int64_t> node_size;       // per node: number of indices
+    std::vector<std::vector<int64_t>> near;  // per leaf number: leaf numbers (sorted)
+    std::vector<std::vector<int64_t>> far;   // per node: far nodes (sorted heap ids)
+    std::vector<std::vector<int64_t>> skel;  // per node: skeleton (original indices, pivot order)
+    std::vector<std::vector<double>> P;      // per node: s x ncols row-major
+    // Blocks cached at compression time for callback matrices (FP64,
+    // row-major): near_blocks[b][t] = K(leaf b, Near(b)[t]);
+    // far_blocks[h][t] = K(skel h, skel Far(h)[t]).
+    std::vector<std::vector<std::vector<double>>> near_blocks, far_blocks;
+    int ann_iters = 0;
+    double ann_recall = 1.0;
+    double compress_seconds = 0.0;
+
+    int64_t n_nodes() const { return (int64_t(2) << depth) - 1; }
+    int64_t n_leaves() const { return int64_t(1) << depth; }
+    int64_t leaf_node(int64_t b) const { return (int64_t(1) << depth) - 1 + b; }
+    bool is_leaf(int64_t h) const { return h >= (int64_t(1) << depth) - 1; }
+    int64_t ncols(int64_t h) const {
+        return is_leaf(h) ? node_size[h]
+                          : int64_t(skel[2 * h + 1].size() + skel[2 * h + 2].size());
+    }
+};
+
+int tree_depth(int64_t n, int64_t m);
+void compress(const Entries& K, Structure& st);  // throws Error
+void fill_node_extents(Structure& st);            // node_off/node_size from leaf sizes
+void cache_blocks_host(const Entries& K, Structure& st);
+
+// pivoted QR + ID (exposed for tests through the structure only)
+struct IdResult {
+    std::vector<int64_t> perm;  // pivot order of the columns
+    int64_t s = 0;
+    std::vector<double> P;      // s x n row-major, original column order
+};
+IdResult interpolative_decomposition(std::vector<double>& A_colmajor, int64_t m, int64_t n,
+                                     int64_t max_rank, double tau);
+
+void export_structure(const Structure& st, const Entries* K, const std::string& path);
+void import_structure(const std::string& path, Structure& st);
+
+}  // namespace gofmm
+
+namespace gofmm {
+
+struct DeviceState;  // device-resident plan and workspace (eval.cu)
+
+// Everything a gofmm_handle owns.
+struct Handle {
+    Structure st;
+    Entries K;               // generator kinds keep their points; callbacks are dropped
+    DeviceState* dev = nullptr;
+    bool timing = false;
+};
+
+// Device side (eval.cu); all throw Error.
+void device_prepare(Handle& H, int64_t r_max, int precision);
+void device_evaluate(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu, int64_t r,
+                     int dtype, int precision, void* stream, bool host_buffers);
+void device_destroy(Handle& H);
+void device_stage_times(Handle& H, float* ms, int n);
+
+}  // namespace gofmm

@@ -1,0 +1,298 @@
+"""Python binding of libgofmm (include/gofmm.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls, without the
+``gofmm_`` prefix.  Device buffers are torch tensors (PyTorch supplies device
+memory and streams); host buffers are numpy arrays.  Nothing here computes:
+if the native library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Callable, Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libgofmm.so")
+
+OK = 0
+ERR_ARG, ERR_CALLBACK, ERR_NONFINITE, ERR_NOMEM = -1, -2, -3, -4
+ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_IO = -5, -6, -7, -8
+GEN_CALLBACK, GEN_GAUSSIAN, GEN_IMQ = 0, 1, 2
+DIST_GRAM_L2, DIST_ANGLE, DIST_LEXICOGRAPHIC, DIST_RANDOM = 0, 1, 2, 3
+FAR_SYMMETRIC, FAR_PAPER = 0, 1
+CACHE_BLOCKS, CACHE_NONE = 0, 1
+DTYPE_F64, DTYPE_F32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_TF32, PREC_BF16, PREC_BF16X3 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "tf32": PREC_TF32, "bf16": PREC_BF16,
+              "bf16x3": PREC_BF16X3}
+
+BLOCK_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(C.c_int64), C.c_int64,
+                       C.POINTER(C.c_int64), C.c_int64, C.POINTER(C.c_double))
+
+
+class EntriesC(C.Structure):
+    _fields_ = [("kind", C.c_int), ("dim", C.c_int), ("n", C.c_int64),
+                ("points", C.POINTER(C.c_double)), ("bandwidth", C.c_double),
+                ("diag_shift", C.c_double), ("fn", BLOCK_FN), ("ctx", C.c_void_p)]
+
+
+class ParamsC(C.Structure):
+    _fields_ = [("leaf_size", C.c_int64), ("max_rank", C.c_int64), ("tau", C.c_double),
+                ("budget", C.c_double), ("kappa", C.c_int), ("distance", C.c_int),
+                ("far_mode", C.c_int), ("cache_mode", C.c_int), ("n_centroid", C.c_int),
+                ("n_sample", C.c_int), ("ann_max_iter", C.c_int), ("num_threads", C.c_int),
+                ("ann_target_recall", C.c_double), ("knn_exact_max", C.c_int64),
+                ("seed", C.c_uint64), ("device", C.c_int), ("reserved", C.c_int)]
+
+
+class StatsC(C.Structure):
+    _fields_ = [("n", C.c_int64), ("depth", C.c_int64), ("n_leaves", C.c_int64),
+                ("min_rank", C.c_int64), ("max_rank", C.c_int64), ("mean_rank", C.c_double),
+                ("near_pairs", C.c_int64), ("far_pairs", C.c_int64), ("max_near", C.c_int64),
+                ("flops_n2s", C.c_double), ("flops_s2s", C.c_double), ("flops_s2n", C.c_double),
+                ("flops_l2l", C.c_double), ("near_entries", C.c_int64), ("far_entries", C.c_int64),
+                ("interp_entries", C.c_int64), ("skel_total", C.c_int64),
+                ("ann_iterations", C.c_int), ("ann_recall", C.c_double),
+                ("compress_seconds", C.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"native library not built: {LIB_PATH} "
+                          "(run python -m paper_1707_00164_b300.build)")
+    lib = C.CDLL(LIB_PATH)
+    H = C.c_void_p
+    sig = {
+        "gofmm_default_params": (None, [C.POINTER(ParamsC)]),
+        "gofmm_compress": (C.c_int, [C.POINTER(EntriesC), C.POINTER(ParamsC), C.POINTER(H)]),
+        "gofmm_prepare": (C.c_int, [H, C.c_int64, C.c_int]),
+        "gofmm_evaluate": (C.c_int, [H, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int64,
+                                     C.c_int, C.c_int, C.c_void_p]),
+        "gofmm_evaluate_host": (C.c_int, [H, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                          C.c_int64, C.c_int, C.c_int, C.c_void_p]),
+        "gofmm_free": (C.c_int, [H]),
+        "gofmm_export": (C.c_int, [H, C.c_char_p]),
+        "gofmm_import": (C.c_int, [C.c_char_p, C.POINTER(EntriesC), C.c_int, C.c_int, C.POINTER(H)]),
+        "gofmm_stats": (C.c_int, [H, C.POINTER(StatsC)]),
+        "gofmm_set_timing": (C.c_int, [H, C.c_int]),
+        "gofmm_stage_times": (C.c_int, [H, C.POINTER(C.c_float), C.c_int]),
+        "gofmm_view": (C.c_int64, [H, C.c_int, C.c_void_p]),
+        "gofmm_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+LIB = _load()
+
+
+class GofmmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libgofmm error {code}: {msg}")
+        self.code = code
+
+
+def last_error() -> str:
+    return LIB.gofmm_last_error().decode()
+
+
+def _check(rc: int):
+    if rc != OK:
+        raise GofmmError(rc, last_error())
+
+
+class Entries:
+    """gofmm_entries: a generator (points kept alive here) or a callback
+    ``fn(I, J) -> ndarray`` returning the nI x nJ block K(I, J)."""
+
+    def __init__(self, kind: int, n: int, points: Optional[np.ndarray] = None,
+                 bandwidth: float = 1.0, shift: float = 0.0, fn: Optional[Callable] = None):
+        self.kind, self.n = kind, int(n)
+        self.points = None if points is None else np.ascontiguousarray(points, dtype=np.float64)
+        self.bandwidth, self.shift, self.fn = float(bandwidth), float(shift), fn
+        self._cb = None
+
+    @staticmethod
+    def gaussian(points, h, shift):
+        return Entries(GEN_GAUSSIAN, len(points), points, h, shift)
+
+    @staticmethod
+    def imq(points, l, shift):
+        return Entries(GEN_IMQ, len(points), points, l, shift)
+
+    @staticmethod
+    def callback(n, fn):
+        return Entries(GEN_CALLBACK, n, fn=fn)
+
+    def c(self) -> EntriesC:
+        e = EntriesC()
+        e.kind, e.n = self.kind, self.n
+        e.bandwidth, e.diag_shift = self.bandwidth, self.shift
+        if self.points is not None:
+            e.dim = self.points.shape[1]
+            e.points = self.points.ctypes.data_as(C.POINTER(C.c_double))
+        if self.fn is not None:
+            user = self.fn
+
+            def tramp(ctx, I, nI, J, nJ, out):
+                try:
+                    Ia = np.ctypeslib.as_array(I, shape=(nI,)).copy()
+                    Ja = np.ctypeslib.as_array(J, shape=(nJ,)).copy()
+                    blk = np.asarray(user(Ia, Ja), dtype=np.float64)
+                    np.ctypeslib.as_array(out, shape=(nI, nJ))[...] = blk
+                    return 0
+                except Exception:  # reported to the library as a failing callback
+                    return 1
+
+            self._cb = BLOCK_FN(tramp)
+            e.fn = self._cb
+        return e
+
+
+def default_params(**over) -> ParamsC:
+    p = ParamsC()
+    LIB.gofmm_default_params(C.byref(p))
+    for k, v in over.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Handle:
+    def __init__(self, ptr: C.c_void_p):
+        self.ptr = ptr
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            LIB.gofmm_free(self.ptr)
+            self.ptr = None
+
+
+def compress(entries: Entries, params: Optional[ParamsC] = None) -> Handle:
+    e = entries.c()
+    out = C.c_void_p()
+    _check(LIB.gofmm_compress(C.byref(e), C.byref(params) if params is not None else None,
+                              C.byref(out)))
+    return Handle(out)
+
+
+def prepare(h: Handle, r_max: int, precision: int):
+    _check(LIB.gofmm_prepare(h.ptr, int(r_max), int(precision)))
+
+
+def _dtype_code(t) -> int:
+    name = str(t.dtype)
+    if name in ("torch.float64", "float64"):
+        return DTYPE_F64
+    if name in ("torch.float32", "float32"):
+        return DTYPE_F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def evaluate(h: Handle, W, U, precision: int, stream=None):
+    """U = K~ W for torch CUDA tensors (N x r, unit column stride) on
+    `stream` (a torch.cuda.Stream; default: the current stream)."""
+    import torch
+    if W.dim() != 2 or U.dim() != 2 or W.stride(1) != 1 or U.stride(1) != 1:
+        raise ValueError("W and U must be 2-D with unit column stride")
+    if not (W.is_cuda and U.is_cuda):
+        raise ValueError("W and U must be CUDA tensors (use evaluate_host for host buffers)")
+    if W.shape != U.shape or W.dtype != U.dtype:
+        raise ValueError("W and U must have the same shape and dtype")
+    s = stream if stream is not None else torch.cuda.current_stream(W.device)
+    _check(LIB.gofmm_evaluate(h.ptr, C.c_void_p(W.data_ptr()), W.stride(0), C.c_void_p(U.data_ptr()),
+                              U.stride(0), W.shape[1], _dtype_code(W), int(precision),
+                              C.c_void_p(s.cuda_stream)))
+
+
+def evaluate_host(h: Handle, W: np.ndarray, U: np.ndarray, precision: int, stream=None):
+    """As evaluate, with host numpy arrays (C-contiguous rows); blocks until
+    U holds the result."""
+    if W.ndim != 2 or W.shape != U.shape or W.dtype != U.dtype:
+        raise ValueError("W and U must be 2-D arrays of one shape and dtype")
+    if W.strides[1] != W.itemsize or U.strides[1] != U.itemsize:
+        raise ValueError("W and U need unit column stride")
+    sp = None if stream is None else C.c_void_p(stream.cuda_stream)
+    _check(LIB.gofmm_evaluate_host(h.ptr, C.c_void_p(W.ctypes.data), W.strides[0] // W.itemsize,
+                                   C.c_void_p(U.ctypes.data), U.strides[0] // U.itemsize,
+                                   W.shape[1], _dtype_code(W), int(precision), sp))
+
+
+def free(h: Handle):
+    if h.ptr:
+        rc = LIB.gofmm_free(h.ptr)
+        h.ptr = None
+        _check(rc)
+
+
+def export(h: Handle, path: str):
+    _check(LIB.gofmm_export(h.ptr, path.encode()))
+
+
+def import_(path: str, entries: Entries, cache_mode: int = CACHE_BLOCKS, device: int = 0) -> Handle:
+    e = entries.c()
+    out = C.c_void_p()
+    _check(LIB.gofmm_import(path.encode(), C.byref(e), int(cache_mode), int(device), C.byref(out)))
+    return Handle(out)
+
+
+def stats(h: Handle) -> dict:
+    s = StatsC()
+    _check(LIB.gofmm_stats(h.ptr, C.byref(s)))
+    return {name: getattr(s, name) for name, _ in StatsC._fields_}
+
+
+def set_timing(h: Handle, enable: bool):
+    _check(LIB.gofmm_set_timing(h.ptr, int(bool(enable))))
+
+
+def stage_times(h: Handle) -> dict:
+    ms = (C.c_float * 6)()
+    _check(LIB.gofmm_stage_times(h.ptr, ms, 6))
+    return dict(n2s_leaf=ms[0], n2s_inner=ms[1], s2s_s2n=ms[2], leaf_l2l=ms[3], total=ms[4],
+                launches=int(ms[5]))
+
+
+def view(h: Handle, what: int) -> np.ndarray:
+    n = LIB.gofmm_view(h.ptr, what, None)
+    if n < 0:
+        raise GofmmError(int(n), last_error())
+    out = np.empty(n, dtype=np.float64 if what == 5 else np.int64)
+    LIB.gofmm_view(h.ptr, what, C.c_void_p(out.ctypes.data))
+    return out
+
+
+def structure(h: Handle) -> dict:
+    """Tree order, near/far lists, skeletons and interpolation matrices as
+    Python objects (heap numbering: root 0, children 2h+1, 2h+2)."""
+    st = stats(h)
+    L = st["depth"]
+    nn = (2 << L) - 1
+    nl = 1 << L
+
+    def csr(arr, count):
+        off = arr[:count + 1]
+        vals = arr[count + 1:]
+        return [vals[off[i]:off[i + 1]] for i in range(count)]
+
+    perm = view(h, 0)
+    leaf_off = view(h, 1)
+    near = csr(view(h, 2), nl)
+    far = csr(view(h, 3), nn)
+    skel = csr(view(h, 4), nn)
+    pvals = view(h, 5)
+    P, pos = {}, 0
+    first_leaf = nl - 1
+    for node in range(1, nn):
+        s = skel[node].size
+        nc = (leaf_off[node - first_leaf + 1] - leaf_off[node - first_leaf]) if node >= first_leaf \
+            else skel[2 * node + 1].size + skel[2 * node + 2].size
+        P[node] = pvals[pos:pos + s * nc].reshape(s, nc)
+        pos += s * nc
+    return dict(depth=L, perm=perm, leaf_off=leaf_off, near=near, far=far, skel=skel, P=P)
