@@ -213,8 +213,9 @@ int gofmm_stats(const gofmm_handle* h, gofmm_stats_t* s);
  * Stage timing: when enabled, gofmm_evaluate records CUDA events on its
  * stream around each stage.  gofmm_stage_times then synchronises on the last
  * event and fills ms[0..4] with the milliseconds of the last call's stages
- * (0 gather + leaf N2S, 1 inner N2S levels, 2 S2S+S2N levels, 3 leaf S2N+L2L,
- * 4 whole call).
+ * (0 gather of W into tree order, 1 N2S upward pass, 2 S2S+S2N levels,
+ * 3 leaf S2N+L2L with scatter, 4 whole call) and, if n > 5, ms[5] with the
+ * number of kernels the call launched.
  */
 int gofmm_set_timing(gofmm_handle* h, int enable);
 int gofmm_stage_times(gofmm_handle* h, float* ms, int n);

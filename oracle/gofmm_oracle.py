@@ -661,6 +661,51 @@ def evaluate(st: Structure, K, W: np.ndarray) -> np.ndarray:
     return U
 
 
+def evaluate_leaves(st: Structure, K, W: np.ndarray, leaves) -> Dict[int, np.ndarray]:
+    """Rows of U = K~ W belonging to the given leaves (leaf numbers), by the
+    same tasks as `evaluate` restricted to what those rows read: N2S on every
+    node, then S2S and S2N only along the root-to-leaf paths, then the leaf
+    S2N and L2L.  Returns {leaf: rows of U in the leaf's index order}."""
+    tree = st.tree
+    L = tree.depth
+    W = np.asarray(W, dtype=np.float64)
+    r = W.shape[1]
+    wt: Dict[int, np.ndarray] = {}
+    for lvl in range(L, 0, -1):
+        for h in tree.level_nodes(lvl):
+            if lvl == L:
+                wt[h] = st.P[h] @ W[tree.node_idx[h]]
+            else:
+                wt[h] = st.P[h] @ np.vstack([wt[2 * h + 1], wt[2 * h + 2]])
+    out = {}
+    for b in leaves:
+        leaf = tree.leaf_node(int(b))
+        path = []
+        h = leaf
+        while h > 0:
+            path.append(h)
+            h = (h - 1) // 2
+        path.reverse()
+        ut = None
+        for depth_i, h in enumerate(path):
+            cur = np.zeros((st.skel[h].size, r))
+            for a in st.far.get(h, []):
+                cur += K(st.skel[h], st.skel[int(a)]) @ wt[int(a)]
+            if ut is not None:
+                p = path[depth_i - 1]
+                t = st.P[p].T @ ut
+                sl = st.skel[2 * p + 1].size
+                cur += t[:sl] if h == 2 * p + 1 else t[sl:]
+            ut = cur
+        rows = tree.node_idx[leaf]
+        u = st.P[leaf].T @ ut if ut is not None else np.zeros((rows.size, r))
+        for a in st.near[int(b)]:
+            cols = tree.node_idx[tree.leaf_node(int(a))]
+            u = u + K(rows, cols) @ W[cols]
+        out[int(b)] = u
+    return out
+
+
 def dense_rows(K, rows: np.ndarray, W: np.ndarray, block=256) -> np.ndarray:
     """Exact rows of K W by brute force."""
     n = W.shape[0]

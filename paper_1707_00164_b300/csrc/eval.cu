@@ -1,9 +1,9 @@
 // Device side of the GOFMM evaluation U = K~ W (Alg. 7, Table 2) on one GPU.
 //
 // Launch sequence of one evaluation (all on the caller's stream):
-//   stage 0  gather W (original order) into tree order WT, then the leaf
-//            N2S tasks  w~_b = P_{b~b} WT[b]                   (Table 2 N2S)
-//   stage 1  one grouped launch per inner level, bottom-up:
+//   stage 0  gather W (original order) into tree order WT       (step a0)
+//   stage 1  leaf N2S tasks  w~_b = P_{b~b} WT[b], then one grouped launch
+//            per inner level, bottom-up:
 //            w~_a = P_{a~[l~r~]} [w~_l; w~_r]                  (N2S, POST)
 //   stage 2  one grouped launch per level, top-down:
 //            u~_b = sum_{a in Far(b)} K_{b~a~} w~_a            (S2S)
@@ -253,9 +253,9 @@ static void build_plan(const Structure& st, bool cached, DeviceState& D) {
         lo.tasks.push_back(t);
         return;
     }
-    // stage 0: leaf N2S
+    // stage 1 (upward): leaf N2S, then inner N2S bottom-up
     {
-        Launch& l = add_launch(OUT_WTIL, 0);
+        Launch& l = add_launch(OUT_WTIL, 1);
         for (int64_t b = 0; b < nl; ++b) {
             const int64_t h = st.leaf_node(b);
             Task t{D.skel_off[h], int32_t(st.skel[h].size()), int32_t(l.slabs.size()), 0, 0};
@@ -265,7 +265,6 @@ static void build_plan(const Structure& st, bool cached, DeviceState& D) {
             l.tasks.push_back(t);
         }
     }
-    // stage 1: inner N2S, bottom-up
     for (int lvl = L - 1; lvl >= 1; --lvl) {
         Launch& l = add_launch(OUT_WTIL, 1);
         for (int64_t h = (int64_t(1) << lvl) - 1; h < (int64_t(2) << lvl) - 1; ++h) {
@@ -466,6 +465,7 @@ static int run_simt(Handle& H, const T* W, int64_t ldw, T* U, int64_t ldu, int r
         CUDA_OK(cudaGetLastError());
         ++launches;
     }
+    if (timing) CUDA_OK(cudaEventRecord(D.ev[1], s));
     GemmParams<T> p{};
     p.kstore = static_cast<const T*>(F.kstore);
     p.pstore = static_cast<const T*>(F.pstore);
@@ -479,7 +479,7 @@ static int run_simt(Handle& H, const T* W, int64_t ldw, T* U, int64_t ldu, int r
     p.gen_inv = H.K.kind == GOFMM_GEN_GAUSSIAN ? T(1.0 / (2.0 * H.K.h * H.K.h)) : T(1.0 / (H.K.h * H.K.h));
     p.gen_shift = T(H.K.shift);
     p.r = r;
-    int stage_done = 0;
+    int stage_done = 1;  // events ev[0..stage_done] recorded; ev[i+1] closes stage i
     for (size_t li = 0; li < D.launches.size(); ++li) {
         Launch& l = D.launches[li];
         while (timing && stage_done < l.stage) { CUDA_OK(cudaEventRecord(D.ev[++stage_done], s)); }

@@ -255,7 +255,7 @@ def set_timing(h: Handle, enable: bool):
 def stage_times(h: Handle) -> dict:
     ms = (C.c_float * 6)()
     _check(LIB.gofmm_stage_times(h.ptr, ms, 6))
-    return dict(n2s_leaf=ms[0], n2s_inner=ms[1], s2s_s2n=ms[2], leaf_l2l=ms[3], total=ms[4],
+    return dict(gather=ms[0], upward=ms[1], downward=ms[2], leaf=ms[3], total=ms[4],
                 launches=int(ms[5]))
 
 

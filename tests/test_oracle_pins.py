@@ -288,3 +288,17 @@ def test_c1_against_dense_brute_force():
     est = O.eps2(U[rows], O.dense_rows(K, rows, W))
     assert full < 1e-2            # s = 64 caps the rank below what tau asks
     assert 0.3 < est / full < 3.0
+
+
+def test_path_restricted_rows_equal_full_evaluation():
+    """evaluate_leaves follows the same tasks along root-to-leaf paths; it
+    must reproduce the rows of the full Alg. 7 evaluation (HSS and FMM
+    lists, cross-level far pairs)."""
+    for far in (O.FAR_SYMMETRIC, O.FAR_PAPER):
+        K, w, st = _small_structure(1024, leaf_size=32, budget=0.05, far=far)
+        W = w.rhs(r=6)
+        U = O.evaluate(st, K, W)
+        got = O.evaluate_leaves(st, K, W, [0, 5, 31])
+        for b, rows in got.items():
+            idx = st.tree.node_idx[st.tree.leaf_node(b)]
+            assert np.abs(rows - U[idx]).max() <= 1e-13 * np.abs(U).max()
