@@ -437,12 +437,16 @@ void device_prepare(Handle& H, int64_t r_max, int precision) {
     if (precision < GOFMM_PREC_FP64 || precision > GOFMM_PREC_BF16X3) fail(GOFMM_ERR_ARG, "unknown precision");
     DeviceGuard g(H.st.prm.device);
     ensure_base(H);
+    // tile lists of the SIMT kernels (tile heights 64 / 128) are made here so
+    // that a prepared evaluation allocates nothing
     if (family_of(precision) == 0) {
         ensure_stores<double>(H, 0);
         ensure_workspace<double>(H, 0, r_max);
+        for (Launch& l : H.dev->launches) tiles_for(l, 64);
     } else {
         ensure_stores<float>(H, 1);
         ensure_workspace<float>(H, 1, r_max);
+        for (Launch& l : H.dev->launches) tiles_for(l, 128);
         if (precision != GOFMM_PREC_FP32) tc_prepare(H, *H.dev, r_max, precision);
     }
     CUDA_OK(cudaDeviceSynchronize());
