@@ -3,7 +3,7 @@
 Host C++ (compression, C ABI) is compiled with g++ -O3 -fopenmp
 -ffp-contract=off; the CUDA sources with nvcc for arch sm_103a only; the
 shared library links the CUDA runtime statically.  Usage:
-    python -m paper_1707_00164_b300.build [--force]
+    python paper_1707_00164_b300/build.py [--force]
 """
 from __future__ import annotations
 

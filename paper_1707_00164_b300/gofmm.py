@@ -61,7 +61,7 @@ class StatsC(C.Structure):
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"native library not built: {LIB_PATH} "
-                          "(run python -m paper_1707_00164_b300.build)")
+                          "(run python paper_1707_00164_b300/build.py)")
     lib = C.CDLL(LIB_PATH)
     H = C.c_void_p
     sig = {
