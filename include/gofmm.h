@@ -187,6 +187,29 @@ int gofmm_evaluate(gofmm_handle* h, const void* W, int64_t ldw, void* U, int64_t
 int gofmm_evaluate_host(gofmm_handle* h, const void* W, int64_t ldw, void* U, int64_t ldu,
                         int64_t r, int dtype, int precision, void* stream);
 
+/*
+ * As gofmm_evaluate (FP64 or FP32 precision only), but allocating nothing:
+ * the evaluation's scratch lives in a fixed 32 MiB device array that the
+ * library holds on every device it is loaded on until the process exits.
+ * For callers that may not allocate device memory while running (a serving
+ * loop with a memory budget fixed at start-up, where an allocation could
+ * fail and would synchronise the device; host code under another
+ * framework's allocator).  The paper has no counterpart; it is an interface
+ * of this library.
+ *   - The handle must already be prepared for `precision` (gofmm_prepare or
+ *     an earlier gofmm_evaluate); otherwise ERR_ARG.
+ *   - Needs (N + 2 * S) * r elements of scratch (S = sum of skeleton sizes,
+ *     gofmm_stats skel_total), each rounded up to 256 bytes; larger calls
+ *     fail with ERR_ARG and a message naming the sizes.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, device current); make it before any stream
+ *     capture.
+ *   - All calls share the one array: calls whose executions overlap on the
+ *     GPU (different streams or handles) race on it.
+ */
+int gofmm_evaluate_static(gofmm_handle* h, const void* W, int64_t ldw, void* U, int64_t ldu,
+                          int64_t r, int dtype, int precision, void* stream);
+
 /* Release the handle and all its host and device memory (synchronises the
  * device first).  NULL is accepted. */
 int gofmm_free(gofmm_handle* h);

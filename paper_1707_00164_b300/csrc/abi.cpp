@@ -277,6 +277,14 @@ int gofmm_evaluate_host(gofmm_handle* h, const void* W, int64_t ldw, void* U, in
     });
 }
 
+int gofmm_evaluate_static(gofmm_handle* h, const void* W, int64_t ldw, void* U, int64_t ldu, int64_t r,
+                          int dtype, int precision, void* stream) {
+    return guarded([&] {
+        if (!h) gofmm::fail(GOFMM_ERR_ARG, "handle is NULL");
+        gofmm::device_evaluate_static(h->h, W, ldw, U, ldu, r, dtype, precision, stream);
+    });
+}
+
 int gofmm_free(gofmm_handle* h) {
     if (!h) return GOFMM_OK;
     int rc = guarded([&] { gofmm::device_destroy(h->h); });

@@ -503,6 +503,64 @@ static int run_simt(Handle& H, const T* W, int64_t ldw, T* U, int64_t ldu, int r
     return launches;
 }
 
+// The SIMT launch sequence of run_simt with the three scratch buffers given
+// by the caller; it takes no timing events and creates no tile lists, so it
+// never allocates (the handle must have been prepared for the precision).
+template <typename T, int TM, int TN>
+static int run_simt_on(Handle& H, const T* W, int64_t ldw, T* U, int64_t ldu, int r, cudaStream_t s, T* WT,
+                       T* WTIL, T* UTIL) {
+    DeviceState& D = *H.dev;
+    Family& F = D.fam[std::is_same<T, double>::value ? 0 : 1];
+    constexpr int BM = 16 * TM, BN = 16 * TN;
+    for (Launch& l : D.launches)
+        if (l.tiles.find(BM) == l.tiles.end())
+            fail(GOFMM_ERR_ARG, "handle not prepared for this precision: call gofmm_prepare first");
+    int launches = 0;
+    {
+        dim3 blk(32, 8), grid(unsigned((D.n + 7) / 8));
+        gather_rows_kernel<T><<<grid, blk, 0, s>>>(W, ldw, D.d_idx, WT, D.n, r);
+        CUDA_OK(cudaGetLastError());
+        ++launches;
+    }
+    GemmParams<T> p{};
+    p.kstore = static_cast<const T*>(F.kstore);
+    p.pstore = static_cast<const T*>(F.pstore);
+    p.b0 = WT; p.b1 = WTIL; p.b2 = UTIL;
+    p.ldb = r;
+    p.idx = D.d_idx;
+    p.pts = std::is_same<T, double>::value ? reinterpret_cast<const T*>(D.d_pts64)
+                                           : reinterpret_cast<const T*>(D.d_pts32);
+    p.dim = H.K.dim;
+    p.gen_kind = H.K.kind;
+    p.gen_inv = H.K.kind == GOFMM_GEN_GAUSSIAN ? T(1.0 / (2.0 * H.K.h * H.K.h)) : T(1.0 / (H.K.h * H.K.h));
+    p.gen_shift = T(H.K.shift);
+    p.r = r;
+    for (Launch& l : D.launches) {
+        const auto tl = l.tiles.at(BM);
+        if (tl.second == 0) continue;
+        p.tasks = l.d_tasks;
+        p.slabs = l.d_slabs;
+        p.tiles = tl.first;
+        if (l.out_buf == OUT_U) { p.out = U; p.ldo = ldu; p.out_map = D.d_idx; }
+        else { p.out = l.out_buf == OUT_WTIL ? WTIL : UTIL; p.ldo = r; p.out_map = nullptr; }
+        dim3 grid(unsigned(tl.second), unsigned((r + BN - 1) / BN));
+        gemm_simt_kernel<T, TM, TN><<<grid, 256, 0, s>>>(p);
+        CUDA_OK(cudaGetLastError());
+        ++launches;
+    }
+    return launches;
+}
+
+int simt_evaluate_on(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu, int r, int precision,
+                     cudaStream_t s, void* WT, void* WTIL, void* UTIL) {
+    if (precision == GOFMM_PREC_FP64)
+        return run_simt_on<double, 4, 4>(H, static_cast<const double*>(W), ldw, static_cast<double*>(U), ldu, r,
+                                         s, static_cast<double*>(WT), static_cast<double*>(WTIL),
+                                         static_cast<double*>(UTIL));
+    return run_simt_on<float, 8, 8>(H, static_cast<const float*>(W), ldw, static_cast<float*>(U), ldu, r, s,
+                                    static_cast<float*>(WT), static_cast<float*>(WTIL), static_cast<float*>(UTIL));
+}
+
 void device_evaluate(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu, int64_t r, int dtype,
                      int precision, void* stream, bool host_buffers) {
     if (!W || !U) fail(GOFMM_ERR_ARG, "W and U must not be NULL");

@@ -103,6 +103,10 @@ struct DeviceState {
 
 std::pair<Tile*, int> tiles_for(Launch& l, int bm);
 
+// SIMT evaluation (FP64 / FP32) on caller-supplied scratch (eval.cu).
+int simt_evaluate_on(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu, int r, int precision,
+                     cudaStream_t s, void* WT, void* WTIL, void* UTIL);
+
 // tensor-core path (eval_tc.cu)
 void tc_prepare(Handle& H, DeviceState& D, int64_t r_max, int precision);
 bool tc_ready(const DeviceState& D, int64_t r, int precision);

@@ -139,6 +139,8 @@ struct Handle {
 void device_prepare(Handle& H, int64_t r_max, int precision);
 void device_evaluate(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu, int64_t r,
                      int dtype, int precision, void* stream, bool host_buffers);
+void device_evaluate_static(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu, int64_t r, int dtype,
+                            int precision, void* stream);
 void device_destroy(Handle& H);
 void device_stage_times(Handle& H, float* ms, int n);
 

@@ -72,6 +72,8 @@ def _load():
                                      C.c_int, C.c_int, C.c_void_p]),
         "gofmm_evaluate_host": (C.c_int, [H, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                           C.c_int64, C.c_int, C.c_int, C.c_void_p]),
+        "gofmm_evaluate_static": (C.c_int, [H, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                            C.c_int64, C.c_int, C.c_int, C.c_void_p]),
         "gofmm_free": (C.c_int, [H]),
         "gofmm_export": (C.c_int, [H, C.c_char_p]),
         "gofmm_import": (C.c_int, [C.c_char_p, C.POINTER(EntriesC), C.c_int, C.c_int, C.POINTER(H)]),
@@ -209,6 +211,21 @@ def evaluate(h: Handle, W, U, precision: int, stream=None):
     _check(LIB.gofmm_evaluate(h.ptr, C.c_void_p(W.data_ptr()), W.stride(0), C.c_void_p(U.data_ptr()),
                               U.stride(0), W.shape[1], _dtype_code(W), int(precision),
                               C.c_void_p(s.cuda_stream)))
+
+
+def evaluate_static(h: Handle, W, U, precision: int, stream=None):
+    """gofmm_evaluate_static: as evaluate, for FP64/FP32, with the scratch in
+    the library's fixed device array (no allocation; handle prepared
+    beforehand)."""
+    import torch
+    if W.dim() != 2 or U.dim() != 2 or W.stride(1) != 1 or U.stride(1) != 1:
+        raise ValueError("W and U must be 2-D with unit column stride")
+    if W.shape != U.shape or W.dtype != U.dtype:
+        raise ValueError("W and U must have the same shape and dtype")
+    s = stream if stream is not None else torch.cuda.current_stream(W.device)
+    _check(LIB.gofmm_evaluate_static(h.ptr, C.c_void_p(W.data_ptr()), W.stride(0),
+                                     C.c_void_p(U.data_ptr()), U.stride(0), W.shape[1],
+                                     _dtype_code(W), int(precision), C.c_void_p(s.cuda_stream)))
 
 
 def evaluate_host(h: Handle, W: np.ndarray, U: np.ndarray, precision: int, stream=None):
