@@ -210,6 +210,14 @@ int gofmm_evaluate_host(gofmm_handle* h, const void* W, int64_t ldw, void* U, in
 int gofmm_evaluate_static(gofmm_handle* h, const void* W, int64_t ldw, void* U, int64_t ldu,
                           int64_t r, int dtype, int precision, void* stream);
 
+/*
+ * Wait for `stream` and report errors the kernels recorded asynchronously:
+ * GOFMM_ERR_TIMEOUT when a tensor-core kernel gave up one of its bounded
+ * waits (it then returned without finishing; the outputs of that call are
+ * invalid), GOFMM_ERR_CUDA for a CUDA error.
+ */
+int gofmm_synchronize(gofmm_handle* h, void* stream);
+
 /* Release the handle and all its host and device memory (synchronises the
  * device first).  NULL is accepted. */
 int gofmm_free(gofmm_handle* h);

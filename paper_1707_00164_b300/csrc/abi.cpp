@@ -285,6 +285,13 @@ int gofmm_evaluate_static(gofmm_handle* h, const void* W, int64_t ldw, void* U, 
     });
 }
 
+int gofmm_synchronize(gofmm_handle* h, void* stream) {
+    return guarded([&] {
+        if (!h) gofmm::fail(GOFMM_ERR_ARG, "handle is NULL");
+        gofmm::device_synchronize(h->h, stream);
+    });
+}
+
 int gofmm_free(gofmm_handle* h) {
     if (!h) return GOFMM_OK;
     int rc = guarded([&] { gofmm::device_destroy(h->h); });

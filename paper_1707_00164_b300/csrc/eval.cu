@@ -5,15 +5,17 @@
 //   stage 1  leaf N2S tasks  w~_b = P_{b~b} WT[b], then one grouped launch
 //            per inner level, bottom-up:
 //            w~_a = P_{a~[l~r~]} [w~_l; w~_r]                  (N2S, POST)
-//   stage 2  one grouped launch per level, top-down:
+//   stage 2  one grouped launch over all levels:
 //            u~_b = sum_{a in Far(b)} K_{b~a~} w~_a            (S2S)
-//                 + (P^T_{p~[l~r~]} u~_p)[rows of b]           (S2N, PRE)
+//            then one launch per level, top-down, accumulating in place
+//            u~_b += (P^T_{p~[l~r~]} u~_p)[rows of b]          (S2N, PRE)
 //   stage 3  one grouped launch over the leaves, scattered to the original
 //            order:  U[b] = P^T_{b~b} u~_b + sum_{a in Near(b)} K_{ba} WT[a]
 //                                                              (S2N leaf + L2L)
 // Every launch is a grouped GEMM (eval_plan.hpp) whose tasks own disjoint
 // output rows; the sum over slabs runs in a fixed order inside one CTA, so
-// results are deterministic and nothing is accumulated with atomics.
+// results are deterministic and nothing is accumulated with atomics (the
+// in-place S2N pushes read and write only rows their own thread owns).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -83,6 +85,7 @@ struct GemmParams {
     int64_t ldo;
     const int64_t* out_map;
     int r;
+    int accumulate;  // out += sum of slabs (else out = sum of slabs)
 };
 
 __device__ __forceinline__ double kexp(double x) { return exp(x); }
@@ -173,7 +176,7 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(const GemmParams<T> p) {
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
             const int col = n0 + (j < TN / 2 ? tx * (TN / 2) + j : BN / 2 + tx * (TN / 2) + j - TN / 2);
-            if (col < p.r) o[col] = acc[i][j];
+            if (col < p.r) o[col] = p.accumulate ? o[col] + acc[i][j] : acc[i][j];
         }
     }
 }
@@ -275,10 +278,11 @@ static void build_plan(const Structure& st, bool cached, DeviceState& D) {
             l.tasks.push_back(t);
         }
     }
-    // stage 2: S2S + S2N push, top-down
-    for (int lvl = 1; lvl <= L; ++lvl) {
+    // stage 2: S2S for every node with a field, all levels in one launch
+    // (tasks of every level run side by side, heaviest first) ...
+    {
         Launch& l = add_launch(OUT_UTIL, 2);
-        for (int64_t h = (int64_t(1) << lvl) - 1; h < (int64_t(2) << lvl) - 1; ++h) {
+        for (int64_t h = 1; h < nn; ++h) {
             if (!field[h]) continue;
             const int64_t sh = int64_t(st.skel[h].size());
             Task t{D.skel_off[h], int32_t(sh), int32_t(l.slabs.size()), 0, 0};
@@ -289,12 +293,23 @@ static void build_plan(const Structure& st, bool cached, DeviceState& D) {
                                          : slab(A_GEN, N + D.skel_off[h], N + D.skel_off[a], 0, sa, B_WTIL,
                                                 D.skel_off[a]));
             }
+            t.slab1 = int32_t(l.slabs.size());
+            l.tasks.push_back(t);
+        }
+        if (l.tasks.empty()) D.launches.pop_back();
+    }
+    // ... then the S2N pushes level by level, top-down, accumulated in place:
+    // u~_h += (P^T_{p~[l~r~]} u~_p)[rows of h]
+    for (int lvl = 2; lvl <= L; ++lvl) {
+        Launch& l = add_launch(OUT_UTIL, 2);
+        l.accumulate = 1;
+        for (int64_t h = (int64_t(1) << lvl) - 1; h < (int64_t(2) << lvl) - 1; ++h) {
             const int64_t p = (h - 1) / 2;
-            if (p > 0 && field[p]) {
-                const int sp = int(st.skel[p].size());
-                const int64_t rowoff = (h == 2 * p + 1) ? 0 : int64_t(st.skel[2 * p + 1].size());
-                l.slabs.push_back(slab(A_PSTORE, D.pt_off[p] + rowoff * sp, 0, sp, sp, B_UTIL, D.skel_off[p]));
-            }
+            if (!field[p]) continue;
+            const int sp = int(st.skel[p].size());
+            const int64_t rowoff = (h == 2 * p + 1) ? 0 : int64_t(st.skel[2 * p + 1].size());
+            Task t{D.skel_off[h], int32_t(st.skel[h].size()), int32_t(l.slabs.size()), 0, 0};
+            l.slabs.push_back(slab(A_PSTORE, D.pt_off[p] + rowoff * sp, 0, sp, sp, B_UTIL, D.skel_off[p]));
             t.slab1 = int32_t(l.slabs.size());
             l.tasks.push_back(t);
         }
@@ -492,6 +507,7 @@ static int run_simt(Handle& H, const T* W, int64_t ldw, T* U, int64_t ldu, int r
         p.tasks = l.d_tasks;
         p.slabs = l.d_slabs;
         p.tiles = tl.first;
+        p.accumulate = l.accumulate;
         if (l.out_buf == OUT_U) { p.out = U; p.ldo = ldu; p.out_map = D.d_idx; }
         else { p.out = l.out_buf == OUT_WTIL ? WTIL : UTIL; p.ldo = r; p.out_map = nullptr; }
         dim3 grid(unsigned(tl.second), unsigned((r + BN - 1) / BN));
@@ -541,6 +557,7 @@ static int run_simt_on(Handle& H, const T* W, int64_t ldw, T* U, int64_t ldu, in
         p.tasks = l.d_tasks;
         p.slabs = l.d_slabs;
         p.tiles = tl.first;
+        p.accumulate = l.accumulate;
         if (l.out_buf == OUT_U) { p.out = U; p.ldo = ldu; p.out_map = D.d_idx; }
         else { p.out = l.out_buf == OUT_WTIL ? WTIL : UTIL; p.ldo = r; p.out_map = nullptr; }
         dim3 grid(unsigned(tl.second), unsigned((r + BN - 1) / BN));
@@ -613,6 +630,15 @@ void device_evaluate(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu
                                   cudaMemcpyDeviceToHost, s));
         CUDA_OK(cudaStreamSynchronize(s));
     }
+}
+
+void device_synchronize(Handle& H, void* stream) {
+    if (!H.dev) return;
+    DeviceGuard g(H.st.prm.device);
+    CUDA_OK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    CUDA_OK(cudaGetLastError());
+    if (const int e = tc_error(*H.dev))
+        fail(GOFMM_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait (code " + std::to_string(e) + ")");
 }
 
 void device_stage_times(Handle& H, float* ms, int n) {

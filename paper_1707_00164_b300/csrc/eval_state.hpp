@@ -61,6 +61,7 @@ inline void dfree(void* p) {
 struct Launch {
     int out_buf = OUT_WTIL;
     int stage = 0;
+    int accumulate = 0;  // out += sum of slabs
     std::vector<Task> tasks;
     std::vector<Slab> slabs;
     Task* d_tasks = nullptr;
@@ -113,5 +114,6 @@ bool tc_ready(const DeviceState& D, int64_t r, int precision);
 int tc_run(Handle& H, DeviceState& D, const float* W, int64_t ldw, float* U, int64_t ldu, int r, int precision,
            cudaStream_t s);
 void tc_destroy(DeviceState& D);
+int tc_error(const DeviceState& D);  // deferred error code of a tensor-core kernel, 0 if none
 
 }  // namespace gofmm

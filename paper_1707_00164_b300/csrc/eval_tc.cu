@@ -1,18 +1,771 @@
-// Tensor-core evaluation path (TF32 / BF16 / split-BF16x3 on sm_103a).
+// Tensor-core evaluation path for sm_103a: tcgen05.mma (TF32, BF16, split
+// BF16x3 with FP32 accumulation) on operands staged in shared memory by bulk
+// copies, accumulators in tensor memory (TMEM).
+//
+// Formulation.  Every grouped-GEMM task of the evaluation plan computes
+//     out[m x r] = sum_slabs A_slab[m x k] * B_slab[k x r]
+// (A: a cached K block, an interpolation matrix P or P^T; B: rows of a
+// right-hand-side buffer).  On the tensor cores it runs transposed,
+//     out^T[r x m] = sum_slabs B_slab^T[r x k] * A_slab^T[k x m],
+// so the 128-row MMA dimension M is a tile of the r right-hand sides (always
+// full) and the ragged block height m (a skeleton or leaf size) is the MMA's
+// N (padded to a multiple of 16, at most 256; taller tasks are split).
+// Both MMA operands are K-major and 128-byte swizzled:
+//   MMA A = right-hand sides in "RT" layout: for every 128 columns of r and
+//           every chunk of KC rows (128 bytes of K), one 128 x 128 B tile;
+//           node segments are padded to whole chunks (padding stays zero);
+//   MMA B = the blocks, per block and chunk one n_pad x 128 B tile.
+// Every tile sits in HBM exactly as the MMA reads it from shared memory, so
+// a single linear cp.async.bulk stages it (no tensor maps).
+//
+// Kernel: one CTA per (task, 128-column tile of r), 6 warps.  Warp 0 streams
+// A/B chunk tiles into a ring of shared-memory stages (mbarrier
+// complete_tx); warp 1 allocates TMEM and one thread issues the MMAs (4 per
+// chunk, 12 for BF16x3) and commits each stage back to the producer; warps
+// 2-5 read the accumulator (tcgen05.ld) and write the outputs: the next
+// stage's RT operand (rounded to TF32 / BF16 / BF16 hi+lo) or, for the
+// leaves, U scattered to the original order in FP32.  Every wait is bounded;
+// on timeout the kernel records an error code, drains what it issued and
+// returns.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <memory>
+
 #include "eval_state.hpp"
 
 namespace gofmm {
 
-struct TcState {};
+enum TcMode : int { TC_TF32 = 0, TC_BF16 = 1, TC_BF16X3 = 2 };
 
-void tc_prepare(Handle&, DeviceState&, int64_t, int) {
-    fail(GOFMM_ERR_UNSUPPORTED, "tensor-core precisions are not built in this library version");
+struct TcSlab {
+    int64_t b_off;     // byte offset of the slab's first chunk tile in the B store
+    int32_t a_buf;     // 0 WT, 1 WTIL, 2 UTIL
+    int32_t a_chunk0;  // first chunk of the slab's K range in that RT buffer
+    int32_t nchunks;
+    int32_t pad;
+};
+
+struct TcTask {
+    int64_t out_pos;  // OUT_U: tree position of row 0; else first chunk of the output segment
+    int32_t m;        // valid output rows (<= 256)
+    int32_t n_pad;    // MMA N: m rounded up to 16
+    int32_t slab0, slab1;
+    int32_t out_kind;  // OUT_WTIL, OUT_UTIL, OUT_U
+    int32_t accumulate;
+    int32_t nchunks;   // chunks over all slabs
+    int32_t pad;
+};
+
+// Conversion of one row-major FP32 block (plan store) into its B tiles.
+struct TileJob {
+    int64_t src_off, dst_off;
+    int32_t src_ld, m, k, n_pad, nchunks, k_split, k_gap, src_store;
+};
+
+struct TcLaunch {
+    std::vector<TcTask> tasks;
+    std::vector<TcSlab> slabs;
+    TcTask* d_tasks = nullptr;
+    TcSlab* d_slabs = nullptr;
+    int stage = 0;
+};
+
+struct TcPrec {
+    int mode = 0, kc = 0, es = 0;
+    bool split = false;
+    std::vector<TcLaunch> launches;
+    int64_t wt_chunks = 0, sk_chunks = 0;
+    int64_t* d_chunk_pos = nullptr;    // WT chunk -> tree position of its first row
+    int32_t* d_chunk_valid = nullptr;  // WT chunk -> valid rows
+    uint8_t* b_hi = nullptr;
+    uint8_t* b_lo = nullptr;
+    int64_t b_bytes = 0;
+    int64_t r_cap = 0;  // right-hand sides the RT buffers hold (multiple of 128)
+    uint8_t* rt_hi[3] = {nullptr, nullptr, nullptr};
+    uint8_t* rt_lo[3] = {nullptr, nullptr, nullptr};
+    int* d_err = nullptr;
+    int* h_err = nullptr;  // pinned
+};
+
+struct TcState {
+    TcPrec* prec[3] = {nullptr, nullptr, nullptr};
+};
+
+static int mode_of(int precision) {
+    return precision == GOFMM_PREC_TF32 ? TC_TF32 : precision == GOFMM_PREC_BF16 ? TC_BF16 : TC_BF16X3;
 }
-bool tc_ready(const DeviceState&, int64_t, int) { return false; }
-int tc_run(Handle&, DeviceState&, const float*, int64_t, float*, int64_t, int, int, cudaStream_t) {
-    fail(GOFMM_ERR_UNSUPPORTED, "tensor-core precisions are not built in this library version");
+
+namespace {
+
+constexpr int kTileBytes = 128 * 128;  // one 128-row x 128-byte operand tile
+constexpr int kMaxN = 256;
+constexpr long long kSpinLimit = 4000000000LL;  // clock cycles (~2 s) before a wait gives up
+constexpr int kErrProducer = 1, kErrMma = 2, kErrEpilogue = 3;
+
+template <int MODE>
+struct Cfg {
+    static constexpr bool kSplit = MODE == TC_BF16X3;
+    static constexpr int kStages = kSplit ? 2 : 4;
+    static constexpr int kStageBytes = (kSplit ? 2 : 1) * (kTileBytes + kMaxN * 128);
+    static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+    static constexpr int kKc = MODE == TC_TF32 ? 32 : 64;
+    static constexpr int kEs = MODE == TC_TF32 ? 4 : 2;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait on an mbarrier phase; false (and an error code recorded) on
+// timeout or when another thread of the grid already failed.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*reinterpret_cast<volatile int*>(err) != 0) return false;
+        if (clock64() - t0 > kSpinLimit) {
+            atomicCAS(err, 0, code);
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (tile rows at a 128-byte stride).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= uint64_t((saddr & 0x3FFFFu) >> 4);  // start address
+    d |= uint64_t(1) << 16;                   // leading byte offset (unused when swizzled)
+    d |= uint64_t(1024 >> 4) << 32;           // stride byte offset
+    d |= uint64_t(1) << 46;                   // descriptor version
+    d |= uint64_t(2) << 61;                   // 128-byte swizzle
+    return d;
+}
+// Instruction descriptor (kind::tf32 / kind::f16): FP32 accumulator, both
+// operands K-major, M = 128.
+__device__ __forceinline__ uint32_t make_idesc(int fmt, int n) {
+    return (1u << 4) | (uint32_t(fmt) << 7) | (uint32_t(fmt) << 10) | (uint32_t(n >> 3) << 17) |
+           (uint32_t(128 >> 4) << 24);
+}
+template <int MODE>
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    if constexpr (MODE == TC_TF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc));
+    }
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ float round_tf32(float x) {
+    uint32_t y;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+    return __uint_as_float(y);
+}
+// byte position of (row, byte-in-row) inside a 128-byte-swizzled tile
+__device__ __forceinline__ uint32_t swz(uint32_t row, uint32_t byte) {
+    return row * 128u + ((((byte >> 4) ^ (row & 7u)) << 4) | (byte & 15u));
+}
+
+struct TcParams {
+    const TcTask* tasks;
+    const TcSlab* slabs;
+    int n_rtiles;
+    const uint8_t* b_hi;
+    const uint8_t* b_lo;
+    uint8_t* rt_hi[3];
+    uint8_t* rt_lo[3];
+    int64_t rt_chunks[3];
+    float* U;
+    int64_t ldu;
+    const int64_t* perm;
+    int r;
+    int* err;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const TcParams p) {
+    using C = Cfg<MODE>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + C::kStages * C::kStageBytes);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::kStages + 1);
+    const uint32_t s_base = smem_u32(base);
+    auto full_bar = [&](int s) { return smem_u32(&bars[s]); };
+    auto empty_bar = [&](int s) { return smem_u32(&bars[C::kStages + s]); };
+    const uint32_t done_bar = smem_u32(&bars[2 * C::kStages]);
+    // stage s: A_hi | B_hi | (A_lo | B_lo)
+    auto sA = [&](int s, int lo) { return s_base + s * C::kStageBytes + lo * (kTileBytes + kMaxN * 128); };
+    auto sB = [&](int s, int lo) { return sA(s, lo) + kTileBytes; };
+
+    const int rt = blockIdx.x % p.n_rtiles;
+    const TcTask tk = p.tasks[blockIdx.x / p.n_rtiles];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t b_bytes = uint32_t(tk.n_pad) * 128u;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::kStages; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        mbar_init(done_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(256)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- producer: stream chunk tiles into the stage ring
+            int stage = 0, issued = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int si = tk.slab0; si < tk.slab1 && ok; ++si) {
+                const TcSlab sl = p.slabs[si];
+                const int64_t a_off = (int64_t(rt) * p.rt_chunks[sl.a_buf] + sl.a_chunk0) * kTileBytes;
+                const uint8_t* a_hi = p.rt_hi[sl.a_buf] + a_off;
+                const uint8_t* b_hi = p.b_hi + sl.b_off;
+                for (int c = 0; c < sl.nchunks; ++c) {
+                    if (!mbar_wait(empty_bar(stage), phase ^ 1u, p.err, kErrProducer)) { ok = false; break; }
+                    mbar_expect_tx(full_bar(stage), (C::kSplit ? 2u : 1u) * (kTileBytes + b_bytes));
+                    bulk_g2s(sA(stage, 0), a_hi + int64_t(c) * kTileBytes, kTileBytes, full_bar(stage));
+                    bulk_g2s(sB(stage, 0), b_hi + int64_t(c) * b_bytes, b_bytes, full_bar(stage));
+                    if constexpr (C::kSplit) {
+                        bulk_g2s(sA(stage, 1), p.rt_lo[sl.a_buf] + a_off + int64_t(c) * kTileBytes, kTileBytes,
+                                 full_bar(stage));
+                        bulk_g2s(sB(stage, 1), p.b_lo + sl.b_off + int64_t(c) * b_bytes, b_bytes, full_bar(stage));
+                    }
+                    ++issued;
+                    if (++stage == C::kStages) { stage = 0; phase ^= 1u; }
+                }
+            }
+            if (!ok) {
+                // drain: wait (bounded) for the copies of the last issued stages
+                const int outstanding = issued < C::kStages ? issued : C::kStages;
+                for (int q = 1; q <= outstanding; ++q) {
+                    const int idx = issued - q;
+                    const int s = idx % C::kStages;
+                    const uint32_t ph = uint32_t((idx / C::kStages) & 1);
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(full_bar(s), ph) && clock64() - t0 < kSpinLimit) {
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer (one thread)
+            const uint32_t idesc = make_idesc(MODE == TC_TF32 ? 2 : 1, tk.n_pad);
+            int stage = 0;
+            uint32_t phase = 0;
+            for (int q = 0; q < tk.nchunks; ++q) {
+                if (!mbar_wait(full_bar(stage), phase, p.err, kErrMma)) break;
+                tc_fence_after();
+                const uint64_t da = sw128_desc(sA(stage, 0)), db = sw128_desc(sB(stage, 0));
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint64_t off = uint64_t(kk * 2);  // 32 bytes per MMA K step, in 16-byte units
+                    mma<MODE>(tmem, da + off, db + off, idesc, (q > 0 || kk > 0) ? 1u : 0u);
+                    if constexpr (C::kSplit) {
+                        const uint64_t dal = sw128_desc(sA(stage, 1)), dbl = sw128_desc(sB(stage, 1));
+                        mma<MODE>(tmem, da + off, dbl + off, idesc, 1u);
+                        mma<MODE>(tmem, dal + off, db + off, idesc, 1u);
+                    }
+                }
+                mma_commit(empty_bar(stage));
+                if (++stage == C::kStages) { stage = 0; phase ^= 1u; }
+            }
+            mma_commit(done_bar);
+        }
+    } else {
+        // ---- epilogue: warps 2..5 own TMEM lane quarters (warp % 4)
+        const int q4 = warp & 3;
+        const int row = q4 * 32 + lane;  // row of the MMA tile = column of r
+        const int j = rt * 128 + row;
+        bool ok = true;
+        if (tk.nchunks > 0) ok = mbar_wait(done_bar, 0, p.err, kErrEpilogue);
+        ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
+        tc_fence_after();
+        const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16);
+        for (int n0 = 0; n0 < tk.n_pad; n0 += 32) {
+            float v[32];
+            if (tk.nchunks > 0 && ok) {
+                tmem_ld32(taddr + uint32_t(n0), v);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) v[i] = 0.f;
+            }
+            if (!ok || j >= p.r) continue;
+            if (tk.out_kind == OUT_U) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int n = n0 + i;
+                    if (n < tk.m) p.U[p.perm[tk.out_pos + n] * p.ldu + j] = v[i];
+                }
+                continue;
+            }
+            // RT output: 32 consecutive k of this row, inside one chunk.  Only
+            // pieces below n_pad are stored: columns in [m, n_pad) are exact
+            // zeros (zero rows of the B tiles), TMEM columns from n_pad on were
+            // never written by this task and must not reach the zero padding.
+            const int buf = tk.out_kind == OUT_WTIL ? 1 : 2;
+            const int64_t chunk = tk.out_pos + n0 / C::kKc;
+            const uint32_t byte0 = uint32_t((n0 % C::kKc) * C::kEs);
+            uint8_t* thi = p.rt_hi[buf] + (int64_t(rt) * p.rt_chunks[buf] + chunk) * kTileBytes;
+            if constexpr (MODE == TC_TF32) {
+#pragma unroll
+                for (int piece = 0; piece < 8; ++piece) {
+                    if (n0 + 4 * piece >= tk.n_pad) break;
+                    float4* dst = reinterpret_cast<float4*>(thi + swz(row, byte0 + piece * 16));
+                    float4 o = make_float4(v[4 * piece], v[4 * piece + 1], v[4 * piece + 2], v[4 * piece + 3]);
+                    if (tk.accumulate) {
+                        const float4 e = *dst;
+                        o.x += e.x; o.y += e.y; o.z += e.z; o.w += e.w;
+                    }
+                    *dst = make_float4(round_tf32(o.x), round_tf32(o.y), round_tf32(o.z), round_tf32(o.w));
+                }
+            } else {
+                uint8_t* tlo = C::kSplit ? p.rt_lo[buf] + (int64_t(rt) * p.rt_chunks[buf] + chunk) * kTileBytes
+                                         : nullptr;
+#pragma unroll
+                for (int piece = 0; piece < 4; ++piece) {
+                    if (n0 + 8 * piece >= tk.n_pad) break;
+                    const uint32_t pos = swz(row, byte0 + piece * 16);
+                    float x[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) x[e] = v[8 * piece + e];
+                    if (tk.accumulate) {
+                        const uint4 eh = *reinterpret_cast<const uint4*>(thi + pos);
+                        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&eh);
+                        uint4 el = make_uint4(0, 0, 0, 0);
+                        if constexpr (C::kSplit) el = *reinterpret_cast<const uint4*>(tlo + pos);
+                        const __nv_bfloat16* l = reinterpret_cast<const __nv_bfloat16*>(&el);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            x[e] += __bfloat162float(h[e]) + (C::kSplit ? __bfloat162float(l[e]) : 0.f);
+                    }
+                    uint4 oh, ol;
+                    __nv_bfloat16* hh = reinterpret_cast<__nv_bfloat16*>(&oh);
+                    __nv_bfloat16* ll = reinterpret_cast<__nv_bfloat16*>(&ol);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        hh[e] = __float2bfloat16_rn(x[e]);
+                        ll[e] = __float2bfloat16_rn(x[e] - __bfloat162float(hh[e]));
+                    }
+                    *reinterpret_cast<uint4*>(thi + pos) = oh;
+                    if constexpr (C::kSplit) *reinterpret_cast<uint4*>(tlo + pos) = ol;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+    }
+}
+
+// W (original order, FP32) -> WT in RT layout, one 128 x KC tile per CTA.
+template <int MODE>
+__global__ void __launch_bounds__(256) tc_gather_kernel(const float* __restrict__ W, int64_t ldw,
+                                                        const int64_t* __restrict__ perm,
+                                                        const int64_t* __restrict__ chunk_pos,
+                                                        const int32_t* __restrict__ chunk_valid, uint8_t* wt_hi,
+                                                        uint8_t* wt_lo, int64_t wt_chunks, int r) {
+    using C = Cfg<MODE>;
+    __shared__ __align__(16) uint8_t hi[kTileBytes];
+    __shared__ __align__(16) uint8_t lo[C::kSplit ? kTileBytes : 16];
+    const int64_t c = blockIdx.x;
+    const int rt = blockIdx.y;
+    const int64_t pos = chunk_pos[c];
+    const int valid = chunk_valid[c];
+    for (int e = threadIdx.x; e < 128 * C::kKc; e += blockDim.x) {
+        const int k = e / 128, jj = e % 128, j = rt * 128 + jj;
+        float x = 0.f;
+        if (k < valid && j < r) x = W[perm[pos + k] * ldw + j];
+        const uint32_t at = swz(uint32_t(jj), uint32_t(k * C::kEs));
+        if constexpr (MODE == TC_TF32) {
+            *reinterpret_cast<float*>(hi + at) = round_tf32(x);
+        } else {
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            *reinterpret_cast<__nv_bfloat16*>(hi + at) = h;
+            if constexpr (C::kSplit)
+                *reinterpret_cast<__nv_bfloat16*>(lo + at) = __float2bfloat16_rn(x - __bfloat162float(h));
+        }
+    }
+    __syncthreads();
+    const int64_t off = (int64_t(rt) * wt_chunks + c) * kTileBytes;
+    for (int e = threadIdx.x; e < kTileBytes / 16; e += blockDim.x) {
+        reinterpret_cast<uint4*>(wt_hi + off)[e] = reinterpret_cast<const uint4*>(hi)[e];
+        if constexpr (C::kSplit) reinterpret_cast<uint4*>(wt_lo + off)[e] = reinterpret_cast<const uint4*>(lo)[e];
+    }
+}
+
+// Plan store blocks (row-major FP32) -> B tiles (prepare time).
+template <int MODE>
+__global__ void tc_tile_kernel(const TileJob* __restrict__ jobs, const float* __restrict__ kstore,
+                               const float* __restrict__ pstore, uint8_t* b_hi, uint8_t* b_lo) {
+    using C = Cfg<MODE>;
+    const TileJob jb = jobs[blockIdx.x];
+    const float* src = (jb.src_store == A_KSTORE ? kstore : pstore) + jb.src_off;
+    const int64_t per_chunk = int64_t(jb.n_pad) * C::kKc;
+    for (int64_t e = threadIdx.x; e < per_chunk * jb.nchunks; e += blockDim.x) {
+        const int ch = int(e / per_chunk);
+        const int rem = int(e % per_chunk);
+        const int n = rem / C::kKc, kk = rem % C::kKc;
+        const int col = ch * C::kKc + kk;
+        int sc = -1;
+        if (col < jb.k_split) sc = col;
+        else if (col >= jb.k_split + jb.k_gap) sc = col - jb.k_gap;
+        float x = 0.f;
+        if (n < jb.m && sc >= 0 && sc < jb.k) x = src[int64_t(n) * jb.src_ld + sc];
+        const int64_t at = jb.dst_off + int64_t(ch) * jb.n_pad * 128 + swz(uint32_t(n), uint32_t(kk * C::kEs));
+        if constexpr (MODE == TC_TF32) {
+            *reinterpret_cast<float*>(b_hi + at) = round_tf32(x);
+        } else {
+            const __nv_bfloat16 h = __float2bfloat16_rn(x);
+            *reinterpret_cast<__nv_bfloat16*>(b_hi + at) = h;
+            if constexpr (C::kSplit)
+                *reinterpret_cast<__nv_bfloat16*>(b_lo + at) = __float2bfloat16_rn(x - __bfloat162float(h));
+        }
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host --
+static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::vector<TileJob>& jobs) {
+    const int64_t nn = st.n_nodes(), nl = st.n_leaves();
+    const int kc = T.kc;
+    auto padk = [&](int64_t x) { return (x + kc - 1) / kc * kc; };
+    std::vector<int64_t> leaf_chunk(nl), node_chunk(nn, -1);
+    std::map<int64_t, int64_t> leaf_at_pos, node_at_skel;
+    int64_t c = 0;
+    std::vector<int64_t> chunk_pos;
+    std::vector<int32_t> chunk_valid;
+    for (int64_t b = 0; b < nl; ++b) {
+        const int64_t h = st.leaf_node(b);
+        leaf_chunk[b] = c;
+        leaf_at_pos[st.node_off[h]] = b;
+        for (int64_t i = 0; i < st.node_size[h]; i += kc) {
+            chunk_pos.push_back(st.node_off[h] + i);
+            chunk_valid.push_back(int32_t(std::min<int64_t>(kc, st.node_size[h] - i)));
+        }
+        c += padk(st.node_size[h]) / kc;
+    }
+    T.wt_chunks = c;
+    c = 0;
+    for (int64_t h = 1; h < nn; ++h) {
+        node_chunk[h] = c;
+        node_at_skel[D.skel_off[h]] = h;
+        c += padk(int64_t(st.skel[h].size())) / kc;
+    }
+    T.sk_chunks = std::max<int64_t>(c, 1);
+    T.d_chunk_pos = dupload(chunk_pos);
+    T.d_chunk_valid = dupload(chunk_valid);
+
+    int64_t bbytes = 0;
+    T.launches.clear();
+    for (const Launch& l : D.launches) {
+        TcLaunch tl;
+        tl.stage = l.stage;
+        for (const Task& t : l.tasks) {
+            int64_t out_base;
+            if (l.out_buf == OUT_U) out_base = t.out_row;
+            else out_base = node_chunk.at(node_at_skel.at(t.out_row));
+            for (int64_t q = 0; q * kMaxN < std::max<int64_t>(t.m, 1); ++q) {
+                const int32_t mq = int32_t(std::min<int64_t>(kMaxN, t.m - q * kMaxN));
+                TcTask tt{};
+                tt.out_pos = l.out_buf == OUT_U ? out_base + q * kMaxN : out_base + q * kMaxN / kc;
+                tt.m = mq;
+                tt.n_pad = std::max(16, (mq + 15) / 16 * 16);
+                tt.slab0 = int32_t(tl.slabs.size());
+                tt.out_kind = l.out_buf;
+                tt.accumulate = l.accumulate;
+                for (int si = t.slab0; si < t.slab1; ++si) {
+                    const Slab& s = l.slabs[si];
+                    if (s.a_src == A_GEN)
+                        fail(GOFMM_ERR_UNSUPPORTED, "tensor-core precisions need cached K blocks (GOFMM_CACHE_BLOCKS)");
+                    TcSlab ts{};
+                    ts.a_buf = s.b_src;
+                    int64_t ksplit = s.k, kgap = 0, kpad;
+                    if (s.b_src == B_WT) {
+                        const int64_t a = leaf_at_pos.at(s.b_row);
+                        ts.a_chunk0 = int32_t(leaf_chunk[a]);
+                        kpad = padk(s.k);
+                    } else {
+                        const int64_t a = node_at_skel.at(s.b_row);
+                        const int64_t sa = int64_t(st.skel[a].size());
+                        ts.a_chunk0 = int32_t(node_chunk[a]);
+                        if (s.k == sa) {
+                            kpad = padk(sa);
+                        } else {  // [w~_l; w~_r]: two adjacent sibling segments
+                            const int64_t sb = int64_t(st.skel[a + 1].size());
+                            if (s.k != sa + sb || node_chunk[a + 1] != node_chunk[a] + padk(sa) / kc)
+                                fail(GOFMM_ERR_ARG, "unexpected slab layout in the tensor-core plan");
+                            ksplit = sa;
+                            kgap = padk(sa) - sa;
+                            kpad = padk(sa) + padk(sb);
+                        }
+                    }
+                    ts.nchunks = int32_t(kpad / kc);
+                    ts.b_off = bbytes;
+                    TileJob jb{};
+                    jb.src_off = s.a_off + q * kMaxN * int64_t(s.lda);
+                    jb.dst_off = bbytes;
+                    jb.src_ld = s.lda;
+                    jb.m = mq;
+                    jb.k = s.k;
+                    jb.n_pad = tt.n_pad;
+                    jb.nchunks = ts.nchunks;
+                    jb.k_split = int32_t(ksplit);
+                    jb.k_gap = int32_t(kgap);
+                    jb.src_store = s.a_src;
+                    jobs.push_back(jb);
+                    bbytes += int64_t(ts.nchunks) * tt.n_pad * 128;
+                    tt.nchunks += ts.nchunks;
+                    tl.slabs.push_back(ts);
+                }
+                tt.slab1 = int32_t(tl.slabs.size());
+                tl.tasks.push_back(tt);
+            }
+        }
+        T.launches.push_back(std::move(tl));
+    }
+    T.b_bytes = bbytes;
+    // every range a kernel will touch, checked on the host before upload
+    auto check = [](bool ok, const char* what) {
+        if (!ok) fail(GOFMM_ERR_ARG, std::string("tensor-core plan out of range: ") + what);
+    };
+    const int64_t chunks[3] = {T.wt_chunks, T.sk_chunks, T.sk_chunks};
+    for (const TcLaunch& l : T.launches)
+        for (const TcTask& t : l.tasks) {
+            check(t.m >= 1 && t.m <= kMaxN && t.n_pad % 16 == 0 && t.n_pad >= t.m && t.n_pad <= kMaxN, "task shape");
+            check(t.slab0 >= 0 && t.slab0 <= t.slab1 && t.slab1 <= int32_t(l.slabs.size()), "task slabs");
+            if (t.out_kind == OUT_U)
+                check(t.out_pos >= 0 && t.out_pos + t.m <= st.n, "output rows");
+            else
+                check(t.out_pos >= 0 && t.out_pos + (t.n_pad + kc - 1) / kc <= T.sk_chunks, "output chunks");
+            int64_t total = 0;
+            for (int si = t.slab0; si < t.slab1; ++si) {
+                const TcSlab& sl = l.slabs[si];
+                check(sl.a_buf >= 0 && sl.a_buf < 3, "operand buffer");
+                check(sl.a_chunk0 >= 0 && sl.a_chunk0 + sl.nchunks <= chunks[sl.a_buf], "operand chunks");
+                check(sl.b_off % 16 == 0 && sl.b_off + int64_t(sl.nchunks) * t.n_pad * 128 <= T.b_bytes, "B tiles");
+                total += sl.nchunks;
+            }
+            check(total == t.nchunks, "chunk count");
+        }
+    for (const TileJob& j : jobs) {
+        const int64_t lim = j.src_store == A_KSTORE ? D.kstore_elems : D.pstore_elems;
+        check(j.m >= 1 && j.k >= 1 && j.k <= j.src_ld, "tile job shape");
+        check(j.src_off >= 0 && j.src_off + int64_t(j.m - 1) * j.src_ld + j.k <= lim, "tile job source");
+        check(j.dst_off + int64_t(j.nchunks) * j.n_pad * 128 <= T.b_bytes, "tile job destination");
+        check(int64_t(j.nchunks) * T.kc >= int64_t(j.k_split) + j.k_gap + (j.k - j.k_split), "tile job columns");
+    }
+    for (TcLaunch& l : T.launches) {
+        l.d_tasks = dupload(l.tasks);
+        l.d_slabs = dupload(l.slabs);
+    }
+}
+
+template <int MODE>
+static void set_smem_attr() {
+    CUDA_OK(cudaFuncSetAttribute(tc_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<MODE>::kSmem));
+}
+
+void tc_prepare(Handle& H, DeviceState& D, int64_t r_max, int precision) {
+    if (!D.tc) D.tc = new TcState();
+    const int mode = mode_of(precision);
+    TcPrec*& T = D.tc->prec[mode];
+    if (!T) {
+        auto t = std::make_unique<TcPrec>();
+        t->mode = mode;
+        t->kc = mode == TC_TF32 ? 32 : 64;
+        t->es = mode == TC_TF32 ? 4 : 2;
+        t->split = mode == TC_BF16X3;
+        std::vector<TileJob> jobs;
+        build_tc_plan(H.st, D, *t, jobs);
+        t->b_hi = dalloc<uint8_t>(size_t(std::max<int64_t>(t->b_bytes, 16)));
+        if (t->split) t->b_lo = dalloc<uint8_t>(size_t(std::max<int64_t>(t->b_bytes, 16)));
+        if (!jobs.empty()) {
+            TileJob* dj = dupload(jobs);
+            const float* ks = static_cast<const float*>(D.fam[1].kstore);
+            const float* ps = static_cast<const float*>(D.fam[1].pstore);
+            const unsigned nj = unsigned(jobs.size());
+            if (mode == TC_TF32) tc_tile_kernel<TC_TF32><<<nj, 256>>>(dj, ks, ps, t->b_hi, t->b_lo);
+            else if (mode == TC_BF16) tc_tile_kernel<TC_BF16><<<nj, 256>>>(dj, ks, ps, t->b_hi, t->b_lo);
+            else tc_tile_kernel<TC_BF16X3><<<nj, 256>>>(dj, ks, ps, t->b_hi, t->b_lo);
+            CUDA_OK(cudaGetLastError());
+            CUDA_OK(cudaDeviceSynchronize());
+            dfree(dj);
+        }
+        t->d_err = dalloc<int>(1);
+        CUDA_OK(cudaMemset(t->d_err, 0, sizeof(int)));
+        CUDA_OK(cudaMallocHost(&t->h_err, sizeof(int)));
+        *t->h_err = 0;
+        set_smem_attr<TC_TF32>();
+        set_smem_attr<TC_BF16>();
+        set_smem_attr<TC_BF16X3>();
+        T = t.release();
+    }
+    const int64_t r_pad = (r_max + 127) / 128 * 128;
+    if (T->r_cap < r_pad) {
+        for (int i = 0; i < 3; ++i) {
+            dfree(T->rt_hi[i]);
+            dfree(T->rt_lo[i]);
+            T->rt_hi[i] = T->rt_lo[i] = nullptr;
+        }
+        T->r_cap = 0;
+        const int64_t chunks[3] = {T->wt_chunks, T->sk_chunks, T->sk_chunks};
+        for (int i = 0; i < 3; ++i) {
+            const size_t bytes = size_t(r_pad / 128) * size_t(chunks[i]) * kTileBytes;
+            T->rt_hi[i] = dalloc<uint8_t>(bytes);
+            CUDA_OK(cudaMemset(T->rt_hi[i], 0, bytes));
+            if (T->split) {
+                T->rt_lo[i] = dalloc<uint8_t>(bytes);
+                CUDA_OK(cudaMemset(T->rt_lo[i], 0, bytes));
+            }
+        }
+        T->r_cap = r_pad;
+    }
+}
+
+bool tc_ready(const DeviceState& D, int64_t r, int precision) {
+    if (!D.tc) return false;
+    const TcPrec* T = D.tc->prec[mode_of(precision)];
+    return T && T->r_cap >= r;
+}
+
+template <int MODE>
+static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, int64_t ldw, float* U, int64_t ldu,
+                         int r, cudaStream_t s) {
+    const int n_rtiles = (r + 127) / 128;
+    int launches = 0;
+    const bool timing = H.timing && D.ev_ok;
+    if (timing) CUDA_OK(cudaEventRecord(D.ev[0], s));
+    {
+        dim3 grid(unsigned(T.wt_chunks), unsigned(n_rtiles));
+        tc_gather_kernel<MODE><<<grid, 256, 0, s>>>(W, ldw, D.d_idx, T.d_chunk_pos, T.d_chunk_valid, T.rt_hi[0],
+                                                    T.rt_lo[0], T.wt_chunks, r);
+        CUDA_OK(cudaGetLastError());
+        ++launches;
+    }
+    if (timing) CUDA_OK(cudaEventRecord(D.ev[1], s));
+    TcParams p{};
+    p.n_rtiles = n_rtiles;
+    p.b_hi = T.b_hi;
+    p.b_lo = T.b_lo;
+    for (int i = 0; i < 3; ++i) { p.rt_hi[i] = T.rt_hi[i]; p.rt_lo[i] = T.rt_lo[i]; }
+    p.rt_chunks[0] = T.wt_chunks;
+    p.rt_chunks[1] = p.rt_chunks[2] = T.sk_chunks;
+    p.U = U;
+    p.ldu = ldu;
+    p.perm = D.d_idx;
+    p.r = r;
+    p.err = T.d_err;
+    int stage_done = 1;
+    for (const TcLaunch& l : T.launches) {
+        while (timing && stage_done < l.stage) CUDA_OK(cudaEventRecord(D.ev[++stage_done], s));
+        if (l.tasks.empty()) continue;
+        p.tasks = l.d_tasks;
+        p.slabs = l.d_slabs;
+        tc_gemm_kernel<MODE><<<unsigned(l.tasks.size()) * unsigned(n_rtiles), 192, Cfg<MODE>::kSmem, s>>>(p);
+        CUDA_OK(cudaGetLastError());
+        ++launches;
+    }
+    while (timing && stage_done < 4) CUDA_OK(cudaEventRecord(D.ev[++stage_done], s));
+    CUDA_OK(cudaMemcpyAsync(T.h_err, T.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    return launches;
+}
+
+int tc_run(Handle& H, DeviceState& D, const float* W, int64_t ldw, float* U, int64_t ldu, int r, int precision,
+           cudaStream_t s) {
+    TcPrec& T = *D.tc->prec[mode_of(precision)];
+    if (*reinterpret_cast<volatile int*>(T.h_err) != 0)
+        fail(GOFMM_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait (code " + std::to_string(*T.h_err) + ")");
+    if (T.mode == TC_TF32) return tc_launch_all<TC_TF32>(H, D, T, W, ldw, U, ldu, r, s);
+    if (T.mode == TC_BF16) return tc_launch_all<TC_BF16>(H, D, T, W, ldw, U, ldu, r, s);
+    return tc_launch_all<TC_BF16X3>(H, D, T, W, ldw, U, ldu, r, s);
+}
+
+int tc_error(const DeviceState& D) {
+    if (!D.tc) return 0;
+    for (const TcPrec* T : D.tc->prec)
+        if (T && T->h_err && *T->h_err) return *T->h_err;
+    return 0;
+}
+
 void tc_destroy(DeviceState& D) {
+    if (!D.tc) return;
+    for (TcPrec*& T : D.tc->prec) {
+        if (!T) continue;
+        for (TcLaunch& l : T->launches) { dfree(l.d_tasks); dfree(l.d_slabs); }
+        dfree(T->d_chunk_pos); dfree(T->d_chunk_valid); dfree(T->b_hi); dfree(T->b_lo); dfree(T->d_err);
+        for (int i = 0; i < 3; ++i) { dfree(T->rt_hi[i]); dfree(T->rt_lo[i]); }
+        if (T->h_err) cudaFreeHost(T->h_err);
+        delete T;
+        T = nullptr;
+    }
     delete D.tc;
     D.tc = nullptr;
 }

@@ -142,6 +142,7 @@ void device_evaluate(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu
 void device_evaluate_static(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu, int64_t r, int dtype,
                             int precision, void* stream);
 void device_destroy(Handle& H);
+void device_synchronize(Handle& H, void* stream);
 void device_stage_times(Handle& H, float* ms, int n);
 
 }  // namespace gofmm

@@ -74,6 +74,7 @@ def _load():
                                           C.c_int64, C.c_int, C.c_int, C.c_void_p]),
         "gofmm_evaluate_static": (C.c_int, [H, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                             C.c_int64, C.c_int, C.c_int, C.c_void_p]),
+        "gofmm_synchronize": (C.c_int, [H, C.c_void_p]),
         "gofmm_free": (C.c_int, [H]),
         "gofmm_export": (C.c_int, [H, C.c_char_p]),
         "gofmm_import": (C.c_int, [C.c_char_p, C.POINTER(EntriesC), C.c_int, C.c_int, C.POINTER(H)]),
@@ -239,6 +240,14 @@ def evaluate_host(h: Handle, W: np.ndarray, U: np.ndarray, precision: int, strea
     _check(LIB.gofmm_evaluate_host(h.ptr, C.c_void_p(W.ctypes.data), W.strides[0] // W.itemsize,
                                    C.c_void_p(U.ctypes.data), U.strides[0] // U.itemsize,
                                    W.shape[1], _dtype_code(W), int(precision), sp))
+
+
+def synchronize(h: Handle, stream=None):
+    """Wait for the stream; raise on errors the kernels recorded (bounded
+    waits that gave up: ERR_TIMEOUT)."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(LIB.gofmm_synchronize(h.ptr, C.c_void_p(s.cuda_stream)))
 
 
 def free(h: Handle):

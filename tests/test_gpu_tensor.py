@@ -1,0 +1,90 @@
+"""Tensor-core evaluation (tcgen05: TF32, BF16, split BF16x3 with FP32
+accumulation) against the FP64 oracle on the same structure.
+
+Tolerances follow the operand rounding: each MMA input is rounded to the
+mode's format (unit roundoff u: TF32 2^-11, BF16 2^-9; split BF16 keeps
+about 2^-16 of the FP32 value) and the result passes through up to four
+rounded stages (N2S, S2S, S2N, L2L), so the relative Frobenius error is a
+few u: TF32 <= 5e-3, BF16 <= 2e-2, BF16x3 <= 1e-4."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1707_00164_b300 as G
+import workloads as wl
+from common import assert_same_structure, both
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {G.PREC_TF32: 5e-3, G.PREC_BF16: 2e-2, G.PREC_BF16X3: 1e-4}
+PRECS = [G.PREC_TF32, G.PREC_BF16, G.PREC_BF16X3]
+NAMES = {G.PREC_TF32: "tf32", G.PREC_BF16: "bf16", G.PREC_BF16X3: "bf16x3"}
+
+
+def run(h, W, prec):
+    Wt = torch.from_numpy(W.astype(np.float32)).cuda()
+    Ut = torch.full_like(Wt, float("nan"))
+    G.evaluate(h, Wt, Ut, prec)
+    G.synchronize(h)
+    return Ut.double().cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+CASES = [
+    ("c2_recipe_n8192_r300", wl.scaled(wl.C2, 8192), 300, dict(knn_exact_max=20000)),
+    ("ragged_n1000_r37", wl.scaled(wl.C1, 1000), 37, dict(leaf_size=32, callback=False)),
+    ("paper_far_n1024_r130", wl.scaled(wl.C1, 1024), 130, dict(leaf_size=32, far=O.FAR_PAPER, budget=0.05,
+                                                               callback=False)),
+    ("hss_n512_r5", wl.scaled(wl.C1, 512), 5, dict(leaf_size=32, budget=0.0, callback=False)),
+    ("tall_blocks_n3000_m400", wl.scaled(wl.C3, 3000), 64, dict(leaf_size=400, max_rank=300, tau=1e-6)),
+]
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=[NAMES[p] for p in PRECS])
+@pytest.mark.parametrize("name,w,r,over", CASES, ids=[c[0] for c in CASES])
+def test_tensor_core_evaluate_matches_oracle(name, w, r, over, prec):
+    over = dict(over)
+    cb = over.pop("callback", None)
+    h, st, K = both(w, callback=cb, **over)
+    assert_same_structure(h, st)
+    W = w.rhs(r)
+    ref = O.evaluate(st, K, W)
+    U = run(h, W, prec)
+    assert np.all(np.isfinite(U))
+    assert rel(U, ref) <= TOL[prec], rel(U, ref)
+
+
+def test_tensor_core_is_deterministic_and_r_independent():
+    w = wl.scaled(wl.C1, 2000)
+    h, st, K = both(w, leaf_size=64, callback=False)
+    W = w.rhs(200)
+    a = run(h, W, G.PREC_BF16X3)
+    b = run(h, W, G.PREC_BF16X3)
+    assert np.array_equal(a, b)
+    c = run(h, W[:, :70], G.PREC_BF16X3)   # fewer columns after more: same values
+    assert np.array_equal(c, a[:, :70])
+
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "c2_rows.npz")
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(not os.path.exists(GOLDEN), reason="oracle rows not generated")
+@pytest.mark.parametrize("prec", PRECS, ids=[NAMES[p] for p in PRECS])
+def test_full_size_tensor_core_against_oracle_rows(prec):
+    g = np.load(GOLDEN)
+    w = wl.C2
+    K = w.matrix()
+    h = G.compress(G.Entries.gaussian(K.points, w.bandwidth, w.shift), G.default_params(**w.params()))
+    W = torch.from_numpy(w.rhs(512).astype(np.float32)).cuda()
+    U = torch.empty_like(W)
+    G.evaluate(h, W, U, prec)
+    G.synchronize(h)
+    got = U[torch.from_numpy(g["rows"]).cuda()][:, : g["u_oracle"].shape[1]].double().cpu().numpy()
+    assert rel(got, g["u_oracle"]) <= TOL[prec]
