@@ -45,6 +45,8 @@ TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.json")
 SMS, FP32_LANES = 148, 128
 # tensor-core dense rate relative to BF16 (nominal: TF32 1.1 / BF16 2.25 PFLOP/s)
 NOMINAL_RATIO = {"tf32": 1.1 / 2.25, "bf16": 1.0, "bf16x3": 1.0 / 3.0}
+DTYPE_NAME = {"fp64": "f64", "fp32": "f32", "tf32": "tf32 (fp32 accumulate)", "bf16": "bf16 (fp32 accumulate)",
+              "bf16x3": "bf16x3 split (hi*hi+hi*lo+lo*hi, fp32 accumulate)"}
 
 
 def parse():
@@ -52,7 +54,9 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="fp32")
+    ap.add_argument("--precision", default="bf16x3",
+                    help="headline mode: fp32 (CUDA cores) or tf32 / bf16 / bf16x3 (tensor cores)")
+    ap.add_argument("--no-modes", action="store_true", help="skip timing the other precision modes")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dense", action="store_true")
@@ -254,7 +258,7 @@ def native_arm(args):
 
     for _ in range(args.warmup):
         G.evaluate(h, W, U, prec, stream)
-    torch.cuda.synchronize(dev)
+    G.synchronize(h, stream)
     barrier()
     torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -264,7 +268,7 @@ def native_arm(args):
         for _ in range(args.steps):
             G.evaluate(h, W, U, prec, stream)
         e1.record(stream)
-        torch.cuda.synchronize(dev)
+        G.synchronize(h, stream)
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
     ms_max = ms
@@ -276,7 +280,7 @@ def native_arm(args):
 
     # per-stage CUDA-event timing of the same evaluation, on its stream
     G.set_timing(h, True)
-    stages = {"gather": [], "upward": [], "downward": [], "leaf": [], "total": []}
+    stages = {"gather": [], "upward": [], "s2s": [], "s2n": [], "leaf": [], "total": []}
     launches = 0
     for _ in range(args.steps):
         G.evaluate(h, W, U, prec, stream)
@@ -301,20 +305,49 @@ def native_arm(args):
            "d2h_bytes_per_step": Wn.nbytes}
 
     # accuracy against the oracle's rows (FP64 K~W, same structure) and the exact rows
-    acc = None
-    if os.path.exists(GOLDEN) and rank == 0 and w is WORKLOAD:
-        g = np.load(GOLDEN)
-        G.evaluate(h, W, U, prec, stream)
+    golden = np.load(GOLDEN) if (os.path.exists(GOLDEN) and w is WORKLOAD and rank == 0) else None
+
+    def accuracy(pr):
+        if golden is None:
+            return None
+        G.evaluate(h, W, U, pr, stream)
+        G.synchronize(h, stream)
+        g = golden
         got = U[torch.from_numpy(g["rows"]).to(dev)][:, : g["u_oracle"].shape[1]].double().cpu().numpy()
-        acc = {"eps2_vs_oracle_fp64": float(np.linalg.norm(got - g["u_oracle"]) / np.linalg.norm(g["u_oracle"])),
-               "eps2_vs_exact_KW": float(np.linalg.norm(got - g["u_exact"]) / np.linalg.norm(g["u_exact"])),
-               "rows": int(g["rows"].size), "cols": int(g["u_oracle"].shape[1])}
+        return {"eps2_vs_oracle_fp64": float(np.linalg.norm(got - g["u_oracle"]) / np.linalg.norm(g["u_oracle"])),
+                "eps2_vs_exact_KW": float(np.linalg.norm(got - g["u_exact"]) / np.linalg.norm(g["u_exact"])),
+                "rows": int(g["rows"].size), "cols": int(g["u_oracle"].shape[1])}
+
+    acc = accuracy(prec)
+
+    # every precision mode on the same matrix and W (context for the headline)
+    modes = None
+    if rank == 0 and not args.no_modes:
+        modes = {}
+        for name in ("fp32", "tf32", "bf16", "bf16x3"):
+            pr = G.PRECISIONS[name]
+            G.prepare(h, r, pr)
+            for _ in range(3):
+                G.evaluate(h, W, U, pr, stream)
+            torch.cuda.synchronize(dev)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            nst = max(3, min(args.steps, 10))
+            a.record(stream)
+            for _ in range(nst):
+                G.evaluate(h, W, U, pr, stream)
+            b.record(stream)
+            G.synchronize(h, stream)
+            mms = a.elapsed_time(b) / nst
+            modes[name] = {"ms": mms, "value": w.n * r / (mms / 1e3), "accuracy": accuracy(pr)}
 
     # roofline of the grouped-GEMM kernel (all its launches in one evaluation)
     peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
-    flops = r * (st["flops_n2s"] + st["flops_s2s"] + st["flops_s2n"] + st["flops_l2l"])
-    gemm_ms = st_ms["upward"] + st_ms["downward"] + st_ms["leaf"]
-    achieved = flops / (gemm_ms / 1e3) / 1e12
+    # dominant kernel launch: the S2S grouped GEMM (all far pairs, all levels)
+    flops_all = r * (st["flops_n2s"] + st["flops_s2s"] + st["flops_s2n"] + st["flops_l2l"])
+    flops = r * st["flops_s2s"]
+    achieved = flops / (st_ms["s2s"] / 1e3) / 1e12
+    gemm_ms = st_ms["upward"] + st_ms["s2s"] + st_ms["s2n"] + st_ms["leaf"]
     if prec_name in ("fp32", "fp64"):
         mhz = peaks.get("sm_max_mhz", 2032.0)
         per_lane = 2.0 if prec_name == "fp32" else 2.0 / 64.0
@@ -323,7 +356,8 @@ def native_arm(args):
     else:
         bf16 = peaks.get("bf16_tflops", 1800.0)
         peak = bf16 * NOMINAL_RATIO[prec_name]
-        bound, peak_src = "tensor", "of measured bf16 burst x nominal ratio"
+        bound, peak_src = "tensor", (f"of measured bf16 burst ({bf16:.0f} TFLOP/s) x nominal ratio "
+                                     f"{NOMINAL_RATIO[prec_name]:.3f} for {prec_name}")
     traffic = None
     if os.path.exists(TRAFFIC_PATH):
         tr = json.load(open(TRAFFIC_PATH))
@@ -331,11 +365,14 @@ def native_arm(args):
         src_sha = hashlib.sha256(open(os.path.join(ROOT, "paper_1707_00164_b300", "csrc", ent["source"]),
                                       "rb").read()).hexdigest() if ent else None
         if ent and ent.get("sha256") == src_sha:
-            traffic = ent["dram_bytes_per_step"]
-    roofline = {"kernel": "grouped GEMM (all launches of one evaluation)", "bound": bound,
+            traffic = ent["dram_bytes_per_launch"]
+    kname = ("gemm_simt_kernel" if prec_name in ("fp32", "fp64") else f"tc_gemm_kernel<{prec_name}>")
+    roofline = {"kernel": f"{kname}, S2S launch (every far pair of every level, one launch per evaluation)",
+                "bound": bound,
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": peak_src, "traffic": traffic, "flops_per_step": flops,
-                "gemm_ms_per_step": gemm_ms,
+                "peak_source": peak_src, "traffic": traffic, "flops_per_launch": flops,
+                "launch_ms": st_ms["s2s"], "all_gemm_flops_per_step": flops_all, "all_gemm_ms_per_step": gemm_ms,
+                "all_gemm_achieved": flops_all / (gemm_ms / 1e3) / 1e12,
                 "stages_ms": {k: round(v, 4) for k, v in st_ms.items()}}
 
     dense = None
@@ -350,11 +387,11 @@ def native_arm(args):
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if prec_name == "fp64" else "f32",
+            "vs_baseline": None, "dtype": DTYPE_NAME[prec_name],
             "data": "synthetic: seeded 6-D standard-normal points, Gaussian kernel; seeded N(0,1) W",
             "config": config_dict(w, prec_name), "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches * args.steps,
-            "accuracy": acc, "dense_cublas": dense, "compress_seconds": round(compress_s, 2),
+            "accuracy": acc, "modes": modes, "dense_cublas": dense, "compress_seconds": round(compress_s, 2),
             "structure": {k: st[k] for k in ("depth", "mean_rank", "max_rank", "near_pairs", "far_pairs",
                                               "near_entries", "far_entries")},
         }))

@@ -243,10 +243,10 @@ int gofmm_stats(const gofmm_handle* h, gofmm_stats_t* s);
 /*
  * Stage timing: when enabled, gofmm_evaluate records CUDA events on its
  * stream around each stage.  gofmm_stage_times then synchronises on the last
- * event and fills ms[0..4] with the milliseconds of the last call's stages
- * (0 gather of W into tree order, 1 N2S upward pass, 2 S2S+S2N levels,
- * 3 leaf S2N+L2L with scatter, 4 whole call) and, if n > 5, ms[5] with the
- * number of kernels the call launched.
+ * event and fills ms[0..5] with the milliseconds of the last call's stages
+ * (0 gather of W into tree order, 1 N2S upward pass, 2 S2S (one launch),
+ * 3 S2N pushes level by level, 4 leaf S2N+L2L with scatter, 5 whole call)
+ * and, if n > 6, ms[6] with the number of kernels the call launched.
  */
 int gofmm_set_timing(gofmm_handle* h, int enable);
 int gofmm_stage_times(gofmm_handle* h, float* ms, int n);

@@ -7,9 +7,9 @@
 //            w~_a = P_{a~[l~r~]} [w~_l; w~_r]                  (N2S, POST)
 //   stage 2  one grouped launch over all levels:
 //            u~_b = sum_{a in Far(b)} K_{b~a~} w~_a            (S2S)
-//            then one launch per level, top-down, accumulating in place
+//   stage 3  one launch per level, top-down, accumulating in place
 //            u~_b += (P^T_{p~[l~r~]} u~_p)[rows of b]          (S2N, PRE)
-//   stage 3  one grouped launch over the leaves, scattered to the original
+//   stage 4  one grouped launch over the leaves, scattered to the original
 //            order:  U[b] = P^T_{b~b} u~_b + sum_{a in Near(b)} K_{ba} WT[a]
 //                                                              (S2N leaf + L2L)
 // Every launch is a grouped GEMM (eval_plan.hpp) whose tasks own disjoint
@@ -248,7 +248,7 @@ static void build_plan(const Structure& st, bool cached, DeviceState& D) {
     };
     if (L == 0) {
         // a single leaf: U = K W
-        Launch& lo = add_launch(OUT_U, 3);
+        Launch& lo = add_launch(OUT_U, 4);
         Task t{0, int32_t(N), 0, 0, 0};
         lo.slabs.push_back(cached ? slab(A_KSTORE, 0, 0, int(N), int(N), B_WT, 0)
                                   : slab(A_GEN, 0, 0, 0, int(N), B_WT, 0));
@@ -301,7 +301,7 @@ static void build_plan(const Structure& st, bool cached, DeviceState& D) {
     // ... then the S2N pushes level by level, top-down, accumulated in place:
     // u~_h += (P^T_{p~[l~r~]} u~_p)[rows of h]
     for (int lvl = 2; lvl <= L; ++lvl) {
-        Launch& l = add_launch(OUT_UTIL, 2);
+        Launch& l = add_launch(OUT_UTIL, 3);
         l.accumulate = 1;
         for (int64_t h = (int64_t(1) << lvl) - 1; h < (int64_t(2) << lvl) - 1; ++h) {
             const int64_t p = (h - 1) / 2;
@@ -317,7 +317,7 @@ static void build_plan(const Structure& st, bool cached, DeviceState& D) {
     }
     // stage 3: leaf S2N + L2L, scattered to the original order
     {
-        Launch& l = add_launch(OUT_U, 3);
+        Launch& l = add_launch(OUT_U, 4);
         for (int64_t b = 0; b < nl; ++b) {
             const int64_t h = st.leaf_node(b);
             Task t{st.node_off[h], int32_t(st.node_size[h]), int32_t(l.slabs.size()), 0, 0};
@@ -382,7 +382,7 @@ static void ensure_base(Handle& H) {
         std::vector<float> p32(H.K.pts.begin(), H.K.pts.end());
         D->d_pts32 = dupload(p32);
     }
-    for (int i = 0; i < 5; ++i) CUDA_OK(cudaEventCreate(&D->ev[i]));
+    for (int i = 0; i < 6; ++i) CUDA_OK(cudaEventCreate(&D->ev[i]));
     D->ev_ok = true;
     H.dev = D.release();
 }
@@ -515,7 +515,7 @@ static int run_simt(Handle& H, const T* W, int64_t ldw, T* U, int64_t ldu, int r
         CUDA_OK(cudaGetLastError());
         ++launches;
     }
-    while (timing && stage_done < 4) { CUDA_OK(cudaEventRecord(D.ev[++stage_done], s)); }
+    while (timing && stage_done < 5) { CUDA_OK(cudaEventRecord(D.ev[++stage_done], s)); }
     return launches;
 }
 
@@ -645,12 +645,12 @@ void device_stage_times(Handle& H, float* ms, int n) {
     if (!H.dev || !H.dev->ev_ok) fail(GOFMM_ERR_ARG, "no evaluation recorded");
     DeviceState& D = *H.dev;
     DeviceGuard g(H.st.prm.device);
-    CUDA_OK(cudaEventSynchronize(D.ev[4]));
-    float t[5] = {0, 0, 0, 0, 0};
-    for (int i = 0; i < 4; ++i) CUDA_OK(cudaEventElapsedTime(&t[i], D.ev[i], D.ev[i + 1]));
-    CUDA_OK(cudaEventElapsedTime(&t[4], D.ev[0], D.ev[4]));
-    for (int i = 0; i < n && i < 5; ++i) ms[i] = t[i];
-    if (n > 5) ms[5] = float(D.last_launches);
+    CUDA_OK(cudaEventSynchronize(D.ev[5]));
+    float t[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < 5; ++i) CUDA_OK(cudaEventElapsedTime(&t[i], D.ev[i], D.ev[i + 1]));
+    CUDA_OK(cudaEventElapsedTime(&t[5], D.ev[0], D.ev[5]));
+    for (int i = 0; i < n && i < 6; ++i) ms[i] = t[i];
+    if (n > 6) ms[6] = float(D.last_launches);
 }
 
 void device_destroy(Handle& H) {

@@ -96,7 +96,7 @@ struct DeviceState {
     std::vector<double> pstore_host;  // P and P^T of every node, FP64
     Family fam[2];                    // 0: double, 1: float
     struct TcState* tc = nullptr;     // tensor-core path (eval_tc.cu)
-    cudaEvent_t ev[5] = {};
+    cudaEvent_t ev[6] = {};
     bool ev_ok = false;
     int last_launches = 0;
 };

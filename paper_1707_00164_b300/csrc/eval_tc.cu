@@ -733,7 +733,7 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
         CUDA_OK(cudaGetLastError());
         ++launches;
     }
-    while (timing && stage_done < 4) CUDA_OK(cudaEventRecord(D.ev[++stage_done], s));
+    while (timing && stage_done < 5) CUDA_OK(cudaEventRecord(D.ev[++stage_done], s));
     CUDA_OK(cudaMemcpyAsync(T.h_err, T.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     return launches;
 }

@@ -279,10 +279,10 @@ def set_timing(h: Handle, enable: bool):
 
 
 def stage_times(h: Handle) -> dict:
-    ms = (C.c_float * 6)()
-    _check(LIB.gofmm_stage_times(h.ptr, ms, 6))
-    return dict(gather=ms[0], upward=ms[1], downward=ms[2], leaf=ms[3], total=ms[4],
-                launches=int(ms[5]))
+    ms = (C.c_float * 7)()
+    _check(LIB.gofmm_stage_times(h.ptr, ms, 7))
+    return dict(gather=ms[0], upward=ms[1], s2s=ms[2], s2n=ms[3], leaf=ms[4], total=ms[5],
+                launches=int(ms[6]))
 
 
 def view(h: Handle, what: int) -> np.ndarray:
