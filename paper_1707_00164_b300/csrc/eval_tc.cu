@@ -18,11 +18,12 @@
 // Every tile sits in HBM exactly as the MMA reads it from shared memory, so
 // a single linear cp.async.bulk stages it (no tensor maps).
 //
-// Kernel: one CTA per (task, 128-column tile of r), 6 warps.  Warp 0 streams
-// A/B chunk tiles into a ring of shared-memory stages (mbarrier
-// complete_tx); warp 1 allocates TMEM and one thread issues the MMAs (4 per
-// chunk, 12 for BF16x3) and commits each stage back to the producer; warps
-// 2-5 read the accumulator (tcgen05.ld) and write the outputs: the next
+// Kernel: persistent, one CTA per SM looping over (task, 128-column tile of
+// r) tiles, 6 warps.  Warp 0 streams A/B chunk tiles into a ring of
+// shared-memory stages (mbarrier complete_tx); warp 1 allocates TMEM (two
+// 256-column accumulators) and one thread issues the MMAs (4 per chunk, 12
+// for BF16x3) and commits each stage back to the producer; warps 2-5 read
+// the other accumulator (tcgen05.ld) meanwhile and write the outputs: the next
 // stage's RT operand (rounded to TF32 / BF16 / BF16 hi+lo) or, for the
 // leaves, U scattered to the original order in FP32.  Every wait is bounded;
 // on timeout the kernel records an error code, drains what it issued and
@@ -88,6 +89,7 @@ struct TcPrec {
     uint8_t* rt_lo[3] = {nullptr, nullptr, nullptr};
     int* d_err = nullptr;
     int* h_err = nullptr;  // pinned
+    int num_sms = 148;     // persistent grid size
 };
 
 struct TcState {
@@ -110,7 +112,7 @@ struct Cfg {
     static constexpr bool kSplit = MODE == TC_BF16X3;
     static constexpr int kStages = kSplit ? 2 : 4;
     static constexpr int kStageBytes = (kSplit ? 2 : 1) * (kTileBytes + kMaxN * 128);
-    static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+    static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;  // + alignment slack, barriers
     static constexpr int kKc = MODE == TC_TF32 ? 32 : 64;
     static constexpr int kEs = MODE == TC_TF32 ? 4 : 2;
 };
@@ -220,6 +222,7 @@ struct TcParams {
     const TcTask* tasks;
     const TcSlab* slabs;
     int n_rtiles;
+    int ntiles;
     const uint8_t* b_hi;
     const uint8_t* b_lo;
     uint8_t* rt_hi[3];
@@ -232,37 +235,50 @@ struct TcParams {
     int* err;
 };
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Persistent grouped GEMM: CTA b processes tiles b, b + gridDim.x, ... (tile
+// = task * n_rtiles + r-tile; tasks are sorted heaviest first).  The stage
+// ring runs on across tiles and the accumulator is double-buffered in TMEM
+// (2 x 256 columns), so the epilogue of one tile overlaps the MMAs of the
+// next.
 template <int MODE>
 __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const TcParams p) {
     using C = Cfg<MODE>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + C::kStages * C::kStageBytes);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::kStages + 1);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::kStages + 5);
     const uint32_t s_base = smem_u32(base);
     auto full_bar = [&](int s) { return smem_u32(&bars[s]); };
     auto empty_bar = [&](int s) { return smem_u32(&bars[C::kStages + s]); };
-    const uint32_t done_bar = smem_u32(&bars[2 * C::kStages]);
+    auto tfull_bar = [&](int a) { return smem_u32(&bars[2 * C::kStages + a]); };
+    auto tempty_bar = [&](int a) { return smem_u32(&bars[2 * C::kStages + 2 + a]); };
+    const uint32_t drain_bar = smem_u32(&bars[2 * C::kStages + 4]);
     // stage s: A_hi | B_hi | (A_lo | B_lo)
     auto sA = [&](int s, int lo) { return s_base + s * C::kStageBytes + lo * (kTileBytes + kMaxN * 128); };
     auto sB = [&](int s, int lo) { return sA(s, lo) + kTileBytes; };
 
-    const int rt = blockIdx.x % p.n_rtiles;
-    const TcTask tk = p.tasks[blockIdx.x / p.n_rtiles];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t b_bytes = uint32_t(tk.n_pad) * 128u;
+    const int ntiles = p.ntiles;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::kStages; ++s) {
             mbar_init(full_bar(s), 1);
             mbar_init(empty_bar(s), 1);
         }
-        mbar_init(done_bar, 1);
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(tfull_bar(a), 1);
+            mbar_init(tempty_bar(a), 4);  // one arrival per epilogue warp
+        }
+        mbar_init(drain_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(256)
+                     "r"(512)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -273,27 +289,33 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const TcParams p) {
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---- producer: stream chunk tiles into the stage ring
+            // ---- producer: stream chunk tiles of every tile of this CTA
             int stage = 0, issued = 0;
             uint32_t phase = 0;
             bool ok = true;
-            for (int si = tk.slab0; si < tk.slab1 && ok; ++si) {
-                const TcSlab sl = p.slabs[si];
-                const int64_t a_off = (int64_t(rt) * p.rt_chunks[sl.a_buf] + sl.a_chunk0) * kTileBytes;
-                const uint8_t* a_hi = p.rt_hi[sl.a_buf] + a_off;
-                const uint8_t* b_hi = p.b_hi + sl.b_off;
-                for (int c = 0; c < sl.nchunks; ++c) {
-                    if (!mbar_wait(empty_bar(stage), phase ^ 1u, p.err, kErrProducer)) { ok = false; break; }
-                    mbar_expect_tx(full_bar(stage), (C::kSplit ? 2u : 1u) * (kTileBytes + b_bytes));
-                    bulk_g2s(sA(stage, 0), a_hi + int64_t(c) * kTileBytes, kTileBytes, full_bar(stage));
-                    bulk_g2s(sB(stage, 0), b_hi + int64_t(c) * b_bytes, b_bytes, full_bar(stage));
-                    if constexpr (C::kSplit) {
-                        bulk_g2s(sA(stage, 1), p.rt_lo[sl.a_buf] + a_off + int64_t(c) * kTileBytes, kTileBytes,
-                                 full_bar(stage));
-                        bulk_g2s(sB(stage, 1), p.b_lo + sl.b_off + int64_t(c) * b_bytes, b_bytes, full_bar(stage));
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const TcTask tk = p.tasks[t / p.n_rtiles];
+                const int rt = t % p.n_rtiles;
+                const uint32_t b_bytes = uint32_t(tk.n_pad) * 128u;
+                for (int si = tk.slab0; si < tk.slab1 && ok; ++si) {
+                    const TcSlab sl = p.slabs[si];
+                    const int64_t a_off = (int64_t(rt) * p.rt_chunks[sl.a_buf] + sl.a_chunk0) * kTileBytes;
+                    const uint8_t* a_hi = p.rt_hi[sl.a_buf] + a_off;
+                    const uint8_t* b_hi = p.b_hi + sl.b_off;
+                    for (int c = 0; c < sl.nchunks; ++c) {
+                        if (!mbar_wait(empty_bar(stage), phase ^ 1u, p.err, kErrProducer)) { ok = false; break; }
+                        mbar_expect_tx(full_bar(stage), (C::kSplit ? 2u : 1u) * (kTileBytes + b_bytes));
+                        bulk_g2s(sA(stage, 0), a_hi + int64_t(c) * kTileBytes, kTileBytes, full_bar(stage));
+                        bulk_g2s(sB(stage, 0), b_hi + int64_t(c) * b_bytes, b_bytes, full_bar(stage));
+                        if constexpr (C::kSplit) {
+                            bulk_g2s(sA(stage, 1), p.rt_lo[sl.a_buf] + a_off + int64_t(c) * kTileBytes, kTileBytes,
+                                     full_bar(stage));
+                            bulk_g2s(sB(stage, 1), p.b_lo + sl.b_off + int64_t(c) * b_bytes, b_bytes,
+                                     full_bar(stage));
+                        }
+                        ++issued;
+                        if (++stage == C::kStages) { stage = 0; phase ^= 1u; }
                     }
-                    ++issued;
-                    if (++stage == C::kStages) { stage = 0; phase ^= 1u; }
                 }
             }
             if (!ok) {
@@ -301,10 +323,9 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const TcParams p) {
                 const int outstanding = issued < C::kStages ? issued : C::kStages;
                 for (int q = 1; q <= outstanding; ++q) {
                     const int idx = issued - q;
-                    const int s = idx % C::kStages;
-                    const uint32_t ph = uint32_t((idx / C::kStages) & 1);
                     const long long t0 = clock64();
-                    while (!mbar_try_wait(full_bar(s), ph) && clock64() - t0 < kSpinLimit) {
+                    while (!mbar_try_wait(full_bar(idx % C::kStages), uint32_t((idx / C::kStages) & 1)) &&
+                           clock64() - t0 < kSpinLimit) {
                     }
                 }
             }
@@ -312,107 +333,131 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const TcParams p) {
     } else if (warp == 1) {
         if (lane == 0) {
             // ---- MMA issuer (one thread)
-            const uint32_t idesc = make_idesc(MODE == TC_TF32 ? 2 : 1, tk.n_pad);
-            int stage = 0;
+            int stage = 0, i = 0;
             uint32_t phase = 0;
-            for (int q = 0; q < tk.nchunks; ++q) {
-                if (!mbar_wait(full_bar(stage), phase, p.err, kErrMma)) break;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+                const TcTask tk = p.tasks[t / p.n_rtiles];
+                const int acc = i & 1;
+                if (!mbar_wait(tempty_bar(acc), uint32_t(((i >> 1) & 1) ^ 1), p.err, kErrMma)) break;
                 tc_fence_after();
-                const uint64_t da = sw128_desc(sA(stage, 0)), db = sw128_desc(sB(stage, 0));
+                const uint32_t tacc = tmem + uint32_t(acc * 256);
+                const uint32_t idesc = make_idesc(MODE == TC_TF32 ? 2 : 1, tk.n_pad);
+                for (int q = 0; q < tk.nchunks; ++q) {
+                    if (!mbar_wait(full_bar(stage), phase, p.err, kErrMma)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint64_t da = sw128_desc(sA(stage, 0)), db = sw128_desc(sB(stage, 0));
 #pragma unroll
-                for (int kk = 0; kk < 4; ++kk) {
-                    const uint64_t off = uint64_t(kk * 2);  // 32 bytes per MMA K step, in 16-byte units
-                    mma<MODE>(tmem, da + off, db + off, idesc, (q > 0 || kk > 0) ? 1u : 0u);
-                    if constexpr (C::kSplit) {
-                        const uint64_t dal = sw128_desc(sA(stage, 1)), dbl = sw128_desc(sB(stage, 1));
-                        mma<MODE>(tmem, da + off, dbl + off, idesc, 1u);
-                        mma<MODE>(tmem, dal + off, db + off, idesc, 1u);
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t off = uint64_t(kk * 2);  // 32 bytes per MMA K step, in 16-byte units
+                        mma<MODE>(tacc, da + off, db + off, idesc, (q > 0 || kk > 0) ? 1u : 0u);
+                        if constexpr (C::kSplit) {
+                            const uint64_t dal = sw128_desc(sA(stage, 1)), dbl = sw128_desc(sB(stage, 1));
+                            mma<MODE>(tacc, da + off, dbl + off, idesc, 1u);
+                            mma<MODE>(tacc, dal + off, db + off, idesc, 1u);
+                        }
                     }
+                    mma_commit(empty_bar(stage));
+                    if (++stage == C::kStages) { stage = 0; phase ^= 1u; }
                 }
-                mma_commit(empty_bar(stage));
-                if (++stage == C::kStages) { stage = 0; phase ^= 1u; }
+                mma_commit(tfull_bar(acc));
             }
-            mma_commit(done_bar);
+            // no MMA may still be running when TMEM is freed
+            mma_commit(drain_bar);
+            const long long t0 = clock64();
+            while (!mbar_try_wait(drain_bar, 0) && clock64() - t0 < kSpinLimit) {
+            }
         }
     } else {
         // ---- epilogue: warps 2..5 own TMEM lane quarters (warp % 4)
         const int q4 = warp & 3;
         const int row = q4 * 32 + lane;  // row of the MMA tile = column of r
-        const int j = rt * 128 + row;
-        bool ok = true;
-        if (tk.nchunks > 0) ok = mbar_wait(done_bar, 0, p.err, kErrEpilogue);
-        ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
-        tc_fence_after();
-        const uint32_t taddr = tmem + (uint32_t(q4 * 32) << 16);
-        for (int n0 = 0; n0 < tk.n_pad; n0 += 32) {
-            float v[32];
-            if (tk.nchunks > 0 && ok) {
-                tmem_ld32(taddr + uint32_t(n0), v);
-            } else {
+        int i = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+            const TcTask tk = p.tasks[t / p.n_rtiles];
+            const int rt = t % p.n_rtiles;
+            const int j = rt * 128 + row;
+            const int acc = i & 1;
+            bool ok = mbar_wait(tfull_bar(acc), uint32_t((i >> 1) & 1), p.err, kErrEpilogue);
+            ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t taddr = tmem + uint32_t(acc * 256) + (uint32_t(q4 * 32) << 16);
+            for (int n0 = 0; n0 < tk.n_pad; n0 += 32) {
+                float v[32];
+                if (tk.nchunks > 0) {
+                    tmem_ld32(taddr + uint32_t(n0), v);
+                } else {
 #pragma unroll
-                for (int i = 0; i < 32; ++i) v[i] = 0.f;
-            }
-            if (!ok || j >= p.r) continue;
-            if (tk.out_kind == OUT_U) {
-#pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int n = n0 + i;
-                    if (n < tk.m) p.U[p.perm[tk.out_pos + n] * p.ldu + j] = v[i];
+                    for (int e = 0; e < 32; ++e) v[e] = 0.f;
                 }
-                continue;
-            }
-            // RT output: 32 consecutive k of this row, inside one chunk.  Only
-            // pieces below n_pad are stored: columns in [m, n_pad) are exact
-            // zeros (zero rows of the B tiles), TMEM columns from n_pad on were
-            // never written by this task and must not reach the zero padding.
-            const int buf = tk.out_kind == OUT_WTIL ? 1 : 2;
-            const int64_t chunk = tk.out_pos + n0 / C::kKc;
-            const uint32_t byte0 = uint32_t((n0 % C::kKc) * C::kEs);
-            uint8_t* thi = p.rt_hi[buf] + (int64_t(rt) * p.rt_chunks[buf] + chunk) * kTileBytes;
-            if constexpr (MODE == TC_TF32) {
+                if (j >= p.r) continue;
+                if (tk.out_kind == OUT_U) {
 #pragma unroll
-                for (int piece = 0; piece < 8; ++piece) {
-                    if (n0 + 4 * piece >= tk.n_pad) break;
-                    float4* dst = reinterpret_cast<float4*>(thi + swz(row, byte0 + piece * 16));
-                    float4 o = make_float4(v[4 * piece], v[4 * piece + 1], v[4 * piece + 2], v[4 * piece + 3]);
-                    if (tk.accumulate) {
-                        const float4 e = *dst;
-                        o.x += e.x; o.y += e.y; o.z += e.z; o.w += e.w;
+                    for (int e = 0; e < 32; ++e) {
+                        const int n = n0 + e;
+                        if (n < tk.m) p.U[p.perm[tk.out_pos + n] * p.ldu + j] = v[e];
                     }
-                    *dst = make_float4(round_tf32(o.x), round_tf32(o.y), round_tf32(o.z), round_tf32(o.w));
+                    continue;
                 }
-            } else {
-                uint8_t* tlo = C::kSplit ? p.rt_lo[buf] + (int64_t(rt) * p.rt_chunks[buf] + chunk) * kTileBytes
-                                         : nullptr;
+                // RT output: 32 consecutive k of this row, inside one chunk.
+                // Only pieces below n_pad are stored: columns in [m, n_pad)
+                // are exact zeros (zero rows of the B tiles); TMEM columns
+                // from n_pad on were not written for this tile and must not
+                // reach the zero padding of the segment.
+                const int buf = tk.out_kind == OUT_WTIL ? 1 : 2;
+                const int64_t chunk = tk.out_pos + n0 / C::kKc;
+                const uint32_t byte0 = uint32_t((n0 % C::kKc) * C::kEs);
+                uint8_t* thi = p.rt_hi[buf] + (int64_t(rt) * p.rt_chunks[buf] + chunk) * kTileBytes;
+                if constexpr (MODE == TC_TF32) {
 #pragma unroll
-                for (int piece = 0; piece < 4; ++piece) {
-                    if (n0 + 8 * piece >= tk.n_pad) break;
-                    const uint32_t pos = swz(row, byte0 + piece * 16);
-                    float x[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) x[e] = v[8 * piece + e];
-                    if (tk.accumulate) {
-                        const uint4 eh = *reinterpret_cast<const uint4*>(thi + pos);
-                        const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&eh);
-                        uint4 el = make_uint4(0, 0, 0, 0);
-                        if constexpr (C::kSplit) el = *reinterpret_cast<const uint4*>(tlo + pos);
-                        const __nv_bfloat16* l = reinterpret_cast<const __nv_bfloat16*>(&el);
-#pragma unroll
-                        for (int e = 0; e < 8; ++e)
-                            x[e] += __bfloat162float(h[e]) + (C::kSplit ? __bfloat162float(l[e]) : 0.f);
+                    for (int piece = 0; piece < 8; ++piece) {
+                        if (n0 + 4 * piece >= tk.n_pad) break;
+                        float4* dst = reinterpret_cast<float4*>(thi + swz(row, byte0 + piece * 16));
+                        float4 o = make_float4(v[4 * piece], v[4 * piece + 1], v[4 * piece + 2], v[4 * piece + 3]);
+                        if (tk.accumulate) {
+                            const float4 e = *dst;
+                            o.x += e.x; o.y += e.y; o.z += e.z; o.w += e.w;
+                        }
+                        *dst = make_float4(round_tf32(o.x), round_tf32(o.y), round_tf32(o.z), round_tf32(o.w));
                     }
-                    uint4 oh, ol;
-                    __nv_bfloat16* hh = reinterpret_cast<__nv_bfloat16*>(&oh);
-                    __nv_bfloat16* ll = reinterpret_cast<__nv_bfloat16*>(&ol);
+                } else {
+                    uint8_t* tlo = C::kSplit ? p.rt_lo[buf] + (int64_t(rt) * p.rt_chunks[buf] + chunk) * kTileBytes
+                                             : nullptr;
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        hh[e] = __float2bfloat16_rn(x[e]);
-                        ll[e] = __float2bfloat16_rn(x[e] - __bfloat162float(hh[e]));
+                    for (int piece = 0; piece < 4; ++piece) {
+                        if (n0 + 8 * piece >= tk.n_pad) break;
+                        const uint32_t pos = swz(row, byte0 + piece * 16);
+                        float x[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) x[e] = v[8 * piece + e];
+                        if (tk.accumulate) {
+                            const uint4 eh = *reinterpret_cast<const uint4*>(thi + pos);
+                            const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&eh);
+                            uint4 el = make_uint4(0, 0, 0, 0);
+                            if constexpr (C::kSplit) el = *reinterpret_cast<const uint4*>(tlo + pos);
+                            const __nv_bfloat16* l = reinterpret_cast<const __nv_bfloat16*>(&el);
+#pragma unroll
+                            for (int e = 0; e < 8; ++e)
+                                x[e] += __bfloat162float(h[e]) + (C::kSplit ? __bfloat162float(l[e]) : 0.f);
+                        }
+                        uint4 oh, ol;
+                        __nv_bfloat16* hh = reinterpret_cast<__nv_bfloat16*>(&oh);
+                        __nv_bfloat16* ll = reinterpret_cast<__nv_bfloat16*>(&ol);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            hh[e] = __float2bfloat16_rn(x[e]);
+                            ll[e] = __float2bfloat16_rn(x[e] - __bfloat162float(hh[e]));
+                        }
+                        *reinterpret_cast<uint4*>(thi + pos) = oh;
+                        if constexpr (C::kSplit) *reinterpret_cast<uint4*>(tlo + pos) = ol;
                     }
-                    *reinterpret_cast<uint4*>(thi + pos) = oh;
-                    if constexpr (C::kSplit) *reinterpret_cast<uint4*>(tlo + pos) = ol;
                 }
             }
+            // accumulator buffer free for the MMA of the tile after next
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty_bar(acc));
         }
     }
     tc_fence_before();
@@ -420,7 +465,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const TcParams p) {
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
     }
 }
 
@@ -663,6 +708,9 @@ void tc_prepare(Handle& H, DeviceState& D, int64_t r_max, int precision) {
         CUDA_OK(cudaMemset(t->d_err, 0, sizeof(int)));
         CUDA_OK(cudaMallocHost(&t->h_err, sizeof(int)));
         *t->h_err = 0;
+        int dev = 0;
+        CUDA_OK(cudaGetDevice(&dev));
+        CUDA_OK(cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, dev));
         set_smem_attr<TC_TF32>();
         set_smem_attr<TC_BF16>();
         set_smem_attr<TC_BF16X3>();
@@ -729,7 +777,9 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
         if (l.tasks.empty()) continue;
         p.tasks = l.d_tasks;
         p.slabs = l.d_slabs;
-        tc_gemm_kernel<MODE><<<unsigned(l.tasks.size()) * unsigned(n_rtiles), 192, Cfg<MODE>::kSmem, s>>>(p);
+        p.ntiles = int(l.tasks.size()) * n_rtiles;
+        const int grid = std::min(p.ntiles, T.num_sms);
+        tc_gemm_kernel<MODE><<<unsigned(grid), 192, Cfg<MODE>::kSmem, s>>>(p);
         CUDA_OK(cudaGetLastError());
         ++launches;
     }
