@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <map>
+#include <tuple>
 #include <string>
 #include <utility>
 #include <vector>
@@ -97,6 +98,16 @@ struct DeviceState {
     Family fam[2];                    // 0: double, 1: float
     struct TcState* tc = nullptr;     // tensor-core path (eval_tc.cu)
     cudaEvent_t ev[6] = {};
+    // CUDA graphs of the launch sequence, keyed by (precision, r, W, ldw, U,
+    // ldu): captured on `capture_stream` once a key repeats, replayed on the
+    // caller's stream; cleared whenever device buffers are (re)allocated.
+    struct GraphEntry {
+        int calls = 0;
+        int launches = 0;
+        cudaGraphExec_t exec = nullptr;
+    };
+    std::map<std::tuple<int, int64_t, const void*, int64_t, void*, int64_t>, GraphEntry> graphs;
+    cudaStream_t capture_stream = nullptr;
     bool ev_ok = false;
     int last_launches = 0;
 };

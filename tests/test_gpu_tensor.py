@@ -88,3 +88,23 @@ def test_full_size_tensor_core_against_oracle_rows(prec):
     G.synchronize(h)
     got = U[torch.from_numpy(g["rows"]).cuda()][:, : g["u_oracle"].shape[1]].double().cpu().numpy()
     assert rel(got, g["u_oracle"]) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [G.PREC_FP32, G.PREC_BF16X3], ids=["fp32", "bf16x3"])
+def test_graph_replay_matches_direct_launches(prec):
+    """Repeated calls with the same buffers are replayed from a CUDA graph;
+    the result must equal the directly launched sequence bit for bit."""
+    w = wl.scaled(wl.C1, 1500)
+    h, st, K = both(w, leaf_size=64, callback=False)
+    W = torch.from_numpy(w.rhs(96).astype(np.float32)).cuda()
+    U = torch.empty_like(W)
+    G.set_timing(h, True)  # timing forces direct launches
+    G.evaluate(h, W, U, prec)
+    G.synchronize(h)
+    ref = U.clone()
+    G.set_timing(h, False)
+    for _ in range(4):  # calls 2.. replay the captured graph
+        U.fill_(float("nan"))
+        G.evaluate(h, W, U, prec)
+        G.synchronize(h)
+        assert torch.equal(U, ref)
