@@ -215,6 +215,33 @@ def config_dict(w, precision):
             "l2": "inputs larger than L2: the cached K blocks (>= 4 GB in FP32) are read every step"}
 
 
+# ------------------------------------------------------------ multi-rank --
+def shared_handle(G, entries, params, rank, world, barrier, path, device=0):
+    """Rank 0 compresses and writes a checkpoint, the other ranks import it:
+    every rank evaluates the same compressed matrix."""
+    if world == 1:
+        return G.compress(entries, params)
+    h = None
+    if rank == 0:
+        h = G.compress(entries, params)
+        G.export(h, path)
+    barrier()
+    if rank != 0:
+        h = G.import_(path, entries, G.CACHE_BLOCKS, device)
+    return h
+
+
+def rank_rhs_seed(w, rank):
+    """Every rank multiplies its own right-hand sides (weak scaling)."""
+    return w.w_seed + rank
+
+
+def whole_job_value(n, r, world, ms_per_rank, reduce_max):
+    """Units of all ranks over the slowest rank's time: (value, max ms)."""
+    ms_max = reduce_max(ms_per_rank)
+    return n * r * world / (ms_max / 1e3), ms_max
+
+
 # ------------------------------------------------------------------ native --
 def native_arm(args):
     import torch
@@ -233,21 +260,14 @@ def native_arm(args):
     entries = G.Entries.gaussian(K.points, w.bandwidth, w.shift)
     params = G.default_params(**w.params(), device=local)
     t0 = time.perf_counter()
-    if world > 1:
-        path = os.path.join(tempfile.gettempdir(), f"gofmm_bench_{w.name}.bin")
-        if rank == 0:
-            h = G.compress(entries, params)
-            G.export(h, path)
-        torch.distributed.barrier()
-        if rank != 0:
-            h = G.import_(path, entries, G.CACHE_BLOCKS, local)
-    else:
-        h = G.compress(entries, params)
+    h = shared_handle(G, entries, params, rank, world,
+                      (lambda: torch.distributed.barrier()) if world > 1 else (lambda: None),
+                      os.path.join(tempfile.gettempdir(), f"gofmm_bench_{w.name}.bin"), local)
     compress_s = time.perf_counter() - t0
     st = G.stats(h)
     r = w.r
     G.prepare(h, r, prec)
-    Wn = wl.scaled(w, w.n, w_seed=w.w_seed + rank).rhs(r).astype(np.float32)
+    Wn = wl.scaled(w, w.n, w_seed=rank_rhs_seed(w, rank)).rhs(r).astype(np.float32)
     W = torch.from_numpy(Wn).to(dev)
     U = torch.empty_like(W)
     stream = torch.cuda.current_stream(dev)
@@ -271,12 +291,15 @@ def native_arm(args):
         G.synchronize(h, stream)
     barrier()
     ms = e0.elapsed_time(e1) / args.steps
-    ms_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
+
+    def reduce_max(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = w.n * r * world / (ms_max / 1e3)
+        return float(t.item())
+
+    value, ms_max = whole_job_value(w.n, r, world, ms, reduce_max)
 
     # per-stage CUDA-event timing of the same evaluation, on its stream
     G.set_timing(h, True)
