@@ -218,6 +218,58 @@ int gofmm_evaluate_static(gofmm_handle* h, const void* W, int64_t ldw, void* U, 
  */
 int gofmm_synchronize(gofmm_handle* h, void* stream);
 
+/*
+ * ---- Batching and serving engine ------------------------------------------
+ * Many evaluations in flight at once over any mix of resident compressed
+ * matrices and right-hand-side counts (the paper batches up to 8 GPU tasks
+ * over streams, §2.3 CPU-GPU hybrid; here every step is one grouped launch).
+ * Each evaluation advances one stage per step (gather, N2S levels, S2S, S2N
+ * levels, leaf); a step packs the current stage of every admitted evaluation
+ * into one persistent tensor-core launch.  Evaluations submitted between
+ * steps join at the next step.  A result is bitwise identical alone or in
+ * any mix (tasks never share accumulation).
+ */
+typedef struct gofmm_engine gofmm_engine;
+
+/*
+ * Create an engine on `device` for precision TF32, BF16 or BF16X3, with a
+ * workspace pool of pool_bytes allocated now (each running evaluation takes
+ * its right-hand-side workspace, (N + 2 S) * 128-column tiles in the RT
+ * layout, from the pool; admission waits until it fits).  Errors: ERR_ARG,
+ * ERR_UNSUPPORTED (other precisions), ERR_NOMEM, ERR_CUDA.
+ */
+int gofmm_engine_create(int device, int precision, int64_t pool_bytes, gofmm_engine** out);
+
+/*
+ * Queue U = K~ W for handle h (prepared for the engine's precision).  W and
+ * U are device pointers (FP32, N x r, original order, ld >= r) that must stay
+ * valid until the request is done.  *id receives the request id.  Nothing
+ * runs until gofmm_engine_step / gofmm_engine_drain.  Errors: ERR_ARG
+ * (unprepared handle, bad sizes), ERR_NOMEM (workspace larger than the pool).
+ */
+int gofmm_engine_submit(gofmm_engine* e, gofmm_handle* h, const void* W, int64_t ldw, void* U, int64_t ldu,
+                        int64_t r, int64_t* id);
+
+/*
+ * One step on `stream`: admit queued requests whose workspace fits (FIFO),
+ * then advance every admitted request by one stage.  Asynchronous; *pending
+ * receives the number of requests not yet known to be finished.
+ */
+int gofmm_engine_step(gofmm_engine* e, void* stream, int64_t* pending);
+
+/* *state = 0 queued, 1 running, 2 done (its U is complete). */
+int gofmm_engine_poll(gofmm_engine* e, int64_t id, int* state);
+
+/* Step until every submitted request is done; synchronises `stream`. */
+int gofmm_engine_drain(gofmm_engine* e, void* stream);
+
+/* out[0..6] = steps, kernel launches, most requests in one step, completed,
+ * queued, running, finishing. */
+int gofmm_engine_stats(const gofmm_engine* e, int64_t* out, int n);
+
+/* Synchronise the device and free the engine and its pool. */
+int gofmm_engine_free(gofmm_engine* e);
+
 /* Release the handle and all its host and device memory (synchronises the
  * device first).  NULL is accepted. */
 int gofmm_free(gofmm_handle* h);

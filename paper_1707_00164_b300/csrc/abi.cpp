@@ -14,6 +14,10 @@ struct gofmm_handle {
     gofmm::Handle h;
 };
 
+struct gofmm_engine {
+    gofmm::Engine* e = nullptr;
+};
+
 namespace {
 thread_local std::string g_last_error;
 
@@ -290,6 +294,60 @@ int gofmm_synchronize(gofmm_handle* h, void* stream) {
         if (!h) gofmm::fail(GOFMM_ERR_ARG, "handle is NULL");
         gofmm::device_synchronize(h->h, stream);
     });
+}
+
+int gofmm_engine_create(int device, int precision, int64_t pool_bytes, gofmm_engine** out) {
+    if (out) *out = nullptr;
+    return guarded([&] {
+        if (!out) gofmm::fail(GOFMM_ERR_ARG, "out is NULL");
+        auto w = std::make_unique<gofmm_engine>();
+        w->e = gofmm::engine_create(device, precision, pool_bytes);
+        *out = w.release();
+    });
+}
+
+int gofmm_engine_submit(gofmm_engine* e, gofmm_handle* h, const void* W, int64_t ldw, void* U, int64_t ldu,
+                        int64_t r, int64_t* id) {
+    return guarded([&] {
+        if (!e || !h || !id) gofmm::fail(GOFMM_ERR_ARG, "engine, handle and id must not be NULL");
+        *id = gofmm::engine_submit(*e->e, h->h, static_cast<const float*>(W), ldw, static_cast<float*>(U), ldu, r);
+    });
+}
+
+int gofmm_engine_step(gofmm_engine* e, void* stream, int64_t* pending) {
+    return guarded([&] {
+        if (!e) gofmm::fail(GOFMM_ERR_ARG, "engine is NULL");
+        const int64_t n = gofmm::engine_step(*e->e, static_cast<cudaStream_t>(stream));
+        if (pending) *pending = n;
+    });
+}
+
+int gofmm_engine_poll(gofmm_engine* e, int64_t id, int* state) {
+    return guarded([&] {
+        if (!e || !state) gofmm::fail(GOFMM_ERR_ARG, "engine and state must not be NULL");
+        *state = gofmm::engine_poll(*e->e, id);
+    });
+}
+
+int gofmm_engine_drain(gofmm_engine* e, void* stream) {
+    return guarded([&] {
+        if (!e) gofmm::fail(GOFMM_ERR_ARG, "engine is NULL");
+        gofmm::engine_drain(*e->e, static_cast<cudaStream_t>(stream));
+    });
+}
+
+int gofmm_engine_stats(const gofmm_engine* e, int64_t* out, int n) {
+    return guarded([&] {
+        if (!e || !out || n < 1) gofmm::fail(GOFMM_ERR_ARG, "bad arguments");
+        gofmm::engine_stats(*e->e, out, n);
+    });
+}
+
+int gofmm_engine_free(gofmm_engine* e) {
+    if (!e) return GOFMM_OK;
+    int rc = guarded([&] { gofmm::engine_destroy(e->e); });
+    delete e;
+    return rc;
 }
 
 int gofmm_free(gofmm_handle* h) {

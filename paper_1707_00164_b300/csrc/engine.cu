@@ -1,0 +1,354 @@
+// Batching and serving engine: many evaluations U_i = K~_i W_i in flight at
+// once on one GPU, over any mix of resident compressed matrices and r.
+//
+// Every evaluation is the same sequence of stages as a single one (gather,
+// then the tensor-core launches of its matrix's plan: N2S levels, S2S, S2N
+// levels, leaf).  A step advances every admitted evaluation by one stage in
+// ONE persistent grouped-GEMM launch whose tiles come from all of them (plus
+// one gather launch per evaluation that starts), so uneven trees, ranks and
+// right-hand-side counts are packed into the same kernel.  Evaluations
+// arriving between steps join at the next step (continuous batching).  A
+// task's arithmetic never depends on what else shares the launch (no
+// split-K, fixed summation order), so a result is bitwise the same alone and
+// in any mix.
+//
+// Admission is by memory: each evaluation needs its own right-hand-side
+// workspace (tree-ordered W, skeleton weights and potentials in the RT
+// layout), carved first-fit out of one pool allocated at creation; a request
+// waits in FIFO order until its workspace fits.  A finished evaluation's
+// workspace returns to the pool once the GPU has passed the step that
+// completed it.
+#include <algorithm>
+#include <deque>
+#include <memory>
+#include <unordered_map>
+
+#include "eval_tc.hpp"
+
+namespace gofmm {
+
+struct EngineRequest {
+    int64_t id = 0;
+    Handle* H = nullptr;
+    TcPrec* T = nullptr;
+    const float* W = nullptr;
+    int64_t ldw = 0;
+    float* U = nullptr;
+    int64_t ldu = 0;
+    int r = 0, n_rtiles = 0;
+    int next = 0;  // 0: gather; 1 + k: launch k of the plan
+    size_t ws_off = 0, ws_bytes = 0;
+    uint8_t* rt_hi[3] = {nullptr, nullptr, nullptr};
+    uint8_t* rt_lo[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t done_ev = nullptr;
+};
+
+struct Engine {
+    int device = 0, precision = 0, mode = 0;
+    int num_sms = 148;
+    uint8_t* pool = nullptr;
+    size_t pool_bytes = 0;
+    std::map<size_t, size_t> free_blocks;  // offset -> size
+    std::deque<EngineRequest*> queue;
+    std::vector<EngineRequest*> active;
+    std::vector<EngineRequest*> finishing;  // completed on the host side, waiting for their event
+    std::unordered_map<int64_t, int> state;  // 0 queued, 1 running, 2 done
+    int64_t next_id = 1;
+    // tile upload ring
+    static constexpr int kRing = 4;
+    TcTile* h_tiles[kRing] = {};
+    TcTile* d_tiles[kRing] = {};
+    size_t tile_cap[kRing] = {};
+    cudaEvent_t ring_ev[kRing] = {};
+    bool ring_used[kRing] = {};
+    int ring_pos = 0;
+    int* d_err = nullptr;
+    int* h_err = nullptr;
+    // statistics
+    int64_t steps = 0, launches = 0, max_active = 0, completed = 0;
+};
+
+namespace {
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+bool pool_alloc(Engine& E, size_t bytes, size_t& off) {
+    for (auto it = E.free_blocks.begin(); it != E.free_blocks.end(); ++it) {
+        if (it->second < bytes) continue;
+        off = it->first;
+        const size_t rest = it->second - bytes;
+        E.free_blocks.erase(it);
+        if (rest) E.free_blocks[off + bytes] = rest;
+        return true;
+    }
+    return false;
+}
+
+void pool_free(Engine& E, size_t off, size_t bytes) {
+    auto it = E.free_blocks.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != E.free_blocks.end() && it->first + it->second == nx->first) {
+        it->second += nx->second;
+        E.free_blocks.erase(nx);
+    }
+    if (it != E.free_blocks.begin()) {
+        auto pv = std::prev(it);
+        if (pv->first + pv->second == it->first) {
+            pv->second += it->second;
+            E.free_blocks.erase(it);
+        }
+    }
+}
+
+size_t workspace_bytes(const TcPrec& T, int n_rtiles) {
+    const size_t per = size_t(n_rtiles) * kTileBytes;
+    const size_t chunks[3] = {size_t(T.wt_chunks), size_t(T.sk_chunks), size_t(T.sk_chunks)};
+    size_t total = 0;
+    for (size_t c : chunks) total += align_up(c * per, 256) * (T.split ? 2 : 1);
+    return total;
+}
+
+void carve(EngineRequest& q, uint8_t* base) {
+    const size_t per = size_t(q.n_rtiles) * kTileBytes;
+    const size_t chunks[3] = {size_t(q.T->wt_chunks), size_t(q.T->sk_chunks), size_t(q.T->sk_chunks)};
+    uint8_t* p = base + q.ws_off;
+    for (int i = 0; i < 3; ++i) {
+        q.rt_hi[i] = p;
+        p += align_up(chunks[i] * per, 256);
+        if (q.T->split) {
+            q.rt_lo[i] = p;
+            p += align_up(chunks[i] * per, 256);
+        }
+    }
+}
+
+// Requests whose final step the GPU has finished: release their workspace.
+void retire(Engine& E) {
+    for (size_t i = 0; i < E.finishing.size();) {
+        EngineRequest* q = E.finishing[i];
+        const cudaError_t e = cudaEventQuery(q->done_ev);
+        if (e == cudaErrorNotReady) { ++i; continue; }
+        if (e != cudaSuccess) fail(GOFMM_ERR_CUDA, std::string("engine event: ") + cudaGetErrorString(e));
+        pool_free(E, q->ws_off, q->ws_bytes);
+        cudaEventDestroy(q->done_ev);
+        E.state[q->id] = 2;
+        ++E.completed;
+        delete q;
+        E.finishing[i] = E.finishing.back();
+        E.finishing.pop_back();
+    }
+}
+
+}  // namespace
+
+Engine* engine_create(int device, int precision, int64_t pool_bytes) {
+    if (precision != GOFMM_PREC_TF32 && precision != GOFMM_PREC_BF16 && precision != GOFMM_PREC_BF16X3)
+        fail(GOFMM_ERR_UNSUPPORTED, "the engine runs the tensor-core precisions (TF32, BF16, BF16X3)");
+    if (pool_bytes < (int64_t(1) << 20)) fail(GOFMM_ERR_ARG, "pool_bytes must be at least 1 MiB");
+    DeviceGuard g(device);
+    auto E = std::make_unique<Engine>();
+    E->device = device;
+    E->precision = precision;
+    E->mode = mode_of(precision);
+    CUDA_OK(cudaDeviceGetAttribute(&E->num_sms, cudaDevAttrMultiProcessorCount, device));
+    E->pool_bytes = size_t(pool_bytes) / 256 * 256;
+    E->pool = dalloc<uint8_t>(E->pool_bytes);
+    E->free_blocks[0] = E->pool_bytes;
+    for (int i = 0; i < Engine::kRing; ++i) {
+        E->tile_cap[i] = 1 << 16;
+        CUDA_OK(cudaMallocHost(&E->h_tiles[i], E->tile_cap[i] * sizeof(TcTile)));
+        E->d_tiles[i] = dalloc<TcTile>(E->tile_cap[i]);
+        CUDA_OK(cudaEventCreateWithFlags(&E->ring_ev[i], cudaEventDisableTiming));
+    }
+    E->d_err = dalloc<int>(1);
+    CUDA_OK(cudaMemset(E->d_err, 0, sizeof(int)));
+    CUDA_OK(cudaMallocHost(&E->h_err, sizeof(int)));
+    *E->h_err = 0;
+    return E.release();
+}
+
+int64_t engine_submit(Engine& E, Handle& H, const float* W, int64_t ldw, float* U, int64_t ldu, int64_t r) {
+    if (!W || !U) fail(GOFMM_ERR_ARG, "W and U must not be NULL");
+    if (r < 1 || r > (int64_t(1) << 24) || ldw < r || ldu < r) fail(GOFMM_ERR_ARG, "need 1 <= r <= ld");
+    if (H.st.prm.device != E.device) fail(GOFMM_ERR_ARG, "handle lives on another device than the engine");
+    if (!H.dev || !H.dev->tc || !H.dev->tc->prec[E.mode])
+        fail(GOFMM_ERR_ARG, "handle not prepared for the engine's precision: call gofmm_prepare first");
+    auto q = std::make_unique<EngineRequest>();
+    q->id = E.next_id++;
+    q->H = &H;
+    q->T = H.dev->tc->prec[E.mode];
+    q->W = W;
+    q->ldw = ldw;
+    q->U = U;
+    q->ldu = ldu;
+    q->r = int(r);
+    q->n_rtiles = int((r + 127) / 128);
+    q->ws_bytes = workspace_bytes(*q->T, q->n_rtiles);
+    if (q->ws_bytes > E.pool_bytes)
+        fail(GOFMM_ERR_NOMEM, "request needs " + std::to_string(q->ws_bytes) + " bytes of workspace; the pool has " +
+                                  std::to_string(E.pool_bytes));
+    E.state[q->id] = 0;
+    E.queue.push_back(q.release());
+    return E.queue.back()->id;
+}
+
+int64_t engine_step(Engine& E, cudaStream_t s) {
+    DeviceGuard g(E.device);
+    if (*reinterpret_cast<volatile int*>(E.h_err) != 0)
+        fail(GOFMM_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait (code " + std::to_string(*E.h_err) + ")");
+    retire(E);
+    // admission, first come first served, by workspace memory
+    while (!E.queue.empty()) {
+        EngineRequest* q = E.queue.front();
+        size_t off = 0;
+        if (!pool_alloc(E, q->ws_bytes, off)) break;
+        q->ws_off = off;
+        carve(*q, E.pool);
+        q->next = 0;
+        E.queue.pop_front();
+        E.active.push_back(q);
+        E.state[q->id] = 1;
+    }
+    if (E.active.empty()) return int64_t(E.queue.size() + E.finishing.size());
+    E.max_active = std::max<int64_t>(E.max_active, int64_t(E.active.size()));
+
+    // skip empty launches so every step does work for every request
+    for (EngineRequest* q : E.active)
+        while (q->next >= 1 && q->next <= int(q->T->launches.size()) && q->T->launches[q->next - 1].tasks.empty())
+            ++q->next;
+
+    // gathers of the requests that start now
+    for (EngineRequest* q : E.active)
+        if (q->next == 0) {
+            launch_gather(E.mode, *q->T, q->W, q->ldw, q->H->dev->d_idx, q->rt_hi[0], q->rt_lo[0], q->r, s);
+            ++E.launches;
+        }
+
+    // one grouped launch for everybody else (chunks of kMaxSegs requests)
+    std::vector<EngineRequest*> gemm;
+    for (EngineRequest* q : E.active)
+        if (q->next >= 1 && q->next <= int(q->T->launches.size())) gemm.push_back(q);
+    for (size_t b0 = 0; b0 < gemm.size(); b0 += kMaxSegs) {
+        const size_t nb = std::min<size_t>(kMaxSegs, gemm.size() - b0);
+        TcParams p{};
+        p.nsegs = int(nb);
+        p.err = E.d_err;
+        struct W8 {
+            int64_t w;
+            TcTile t;
+        };
+        std::vector<W8> tiles;
+        for (size_t k = 0; k < nb; ++k) {
+            EngineRequest* q = gemm[b0 + k];
+            const TcLaunch& l = q->T->launches[q->next - 1];
+            p.segs[k] = make_seg(*q->T, l, q->rt_hi, q->rt_lo, q->U, q->ldu, q->H->dev->d_idx, q->r);
+            for (size_t t = 0; t < l.tasks.size(); ++t) {
+                const int64_t w = int64_t(l.tasks[t].nchunks) * l.tasks[t].n_pad + 1;
+                for (int rt = 0; rt < q->n_rtiles; ++rt) tiles.push_back(W8{w, TcTile{int32_t(k), int32_t(t), rt, 0}});
+            }
+        }
+        // heaviest tiles first over the whole mix; r-tiles of a task stay adjacent
+        std::stable_sort(tiles.begin(), tiles.end(), [](const W8& a, const W8& b) { return a.w > b.w; });
+        const int slot = E.ring_pos;
+        E.ring_pos = (E.ring_pos + 1) % Engine::kRing;
+        if (E.ring_used[slot]) CUDA_OK(cudaEventSynchronize(E.ring_ev[slot]));  // staging slot free again
+        if (tiles.size() > E.tile_cap[slot]) {
+            CUDA_OK(cudaFreeHost(E.h_tiles[slot]));
+            dfree(E.d_tiles[slot]);
+            E.tile_cap[slot] = tiles.size() * 2;
+            CUDA_OK(cudaMallocHost(&E.h_tiles[slot], E.tile_cap[slot] * sizeof(TcTile)));
+            E.d_tiles[slot] = dalloc<TcTile>(E.tile_cap[slot]);
+        }
+        for (size_t i = 0; i < tiles.size(); ++i) E.h_tiles[slot][i] = tiles[i].t;
+        CUDA_OK(cudaMemcpyAsync(E.d_tiles[slot], E.h_tiles[slot], tiles.size() * sizeof(TcTile),
+                                cudaMemcpyHostToDevice, s));
+        p.tiles = E.d_tiles[slot];
+        p.ntiles = int(tiles.size());
+        launch_gemm_mode(E.mode, p, E.num_sms, s);
+        CUDA_OK(cudaEventRecord(E.ring_ev[slot], s));
+        E.ring_used[slot] = true;
+        ++E.launches;
+    }
+    CUDA_OK(cudaMemcpyAsync(E.h_err, E.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+
+    // advance; requests past their last launch are complete once this step is
+    std::vector<EngineRequest*> still;
+    cudaEvent_t ev = nullptr;
+    for (EngineRequest* q : E.active) {
+        ++q->next;
+        if (q->next > int(q->T->launches.size())) {
+            if (!ev) {
+                CUDA_OK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+                CUDA_OK(cudaEventRecord(ev, s));
+                q->done_ev = ev;
+            } else {
+                CUDA_OK(cudaEventCreateWithFlags(&q->done_ev, cudaEventDisableTiming));
+                CUDA_OK(cudaEventRecord(q->done_ev, s));
+            }
+            E.finishing.push_back(q);
+        } else {
+            still.push_back(q);
+        }
+    }
+    E.active.swap(still);
+    ++E.steps;
+    return int64_t(E.queue.size() + E.active.size() + E.finishing.size());
+}
+
+int engine_poll(Engine& E, int64_t id) {
+    retire(E);
+    auto it = E.state.find(id);
+    if (it == E.state.end()) fail(GOFMM_ERR_ARG, "unknown request id");
+    return it->second;
+}
+
+void engine_drain(Engine& E, cudaStream_t s) {
+    DeviceGuard g(E.device);
+    while (!E.queue.empty() || !E.active.empty()) {
+        const size_t before = E.queue.size() + E.active.size();
+        engine_step(E, s);
+        if (E.active.empty() && !E.queue.empty() && E.queue.size() + E.active.size() == before) {
+            // nothing admitted: wait for finishing requests to free memory
+            CUDA_OK(cudaStreamSynchronize(s));
+            retire(E);
+            if (E.finishing.empty() && E.active.empty() && !E.queue.empty())
+                fail(GOFMM_ERR_NOMEM, "queued request does not fit the pool");
+        }
+    }
+    CUDA_OK(cudaStreamSynchronize(s));
+    retire(E);
+    if (*reinterpret_cast<volatile int*>(E.h_err) != 0)
+        fail(GOFMM_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait (code " + std::to_string(*E.h_err) + ")");
+}
+
+void engine_stats(const Engine& E, int64_t* out, int n) {
+    const int64_t v[7] = {E.steps, E.launches, E.max_active, E.completed, int64_t(E.queue.size()),
+                          int64_t(E.active.size()), int64_t(E.finishing.size())};
+    for (int i = 0; i < n && i < 7; ++i) out[i] = v[i];
+}
+
+void engine_destroy(Engine* E) {
+    if (!E) return;
+    int old = -1;
+    cudaGetDevice(&old);
+    cudaSetDevice(E->device);
+    cudaDeviceSynchronize();
+    for (EngineRequest* q : E->queue) delete q;
+    for (EngineRequest* q : E->active) delete q;
+    for (EngineRequest* q : E->finishing) {
+        if (q->done_ev) cudaEventDestroy(q->done_ev);
+        delete q;
+    }
+    for (int i = 0; i < Engine::kRing; ++i) {
+        if (E->h_tiles[i]) cudaFreeHost(E->h_tiles[i]);
+        dfree(E->d_tiles[i]);
+        if (E->ring_ev[i]) cudaEventDestroy(E->ring_ev[i]);
+    }
+    dfree(E->pool);
+    dfree(E->d_err);
+    if (E->h_err) cudaFreeHost(E->h_err);
+    delete E;
+    if (old >= 0) cudaSetDevice(old);
+}
+
+}  // namespace gofmm

@@ -35,75 +35,16 @@
 #include <map>
 #include <memory>
 
-#include "eval_state.hpp"
+#include "eval_tc.hpp"
 
 namespace gofmm {
 
-enum TcMode : int { TC_TF32 = 0, TC_BF16 = 1, TC_BF16X3 = 2 };
-
-struct TcSlab {
-    int64_t b_off;     // byte offset of the slab's first chunk tile in the B store
-    int32_t a_buf;     // 0 WT, 1 WTIL, 2 UTIL
-    int32_t a_chunk0;  // first chunk of the slab's K range in that RT buffer
-    int32_t nchunks;
-    int32_t pad;
-};
-
-struct TcTask {
-    int64_t out_pos;  // OUT_U: tree position of row 0; else first chunk of the output segment
-    int32_t m;        // valid output rows (<= 256)
-    int32_t n_pad;    // MMA N: m rounded up to 16
-    int32_t slab0, slab1;
-    int32_t out_kind;  // OUT_WTIL, OUT_UTIL, OUT_U
-    int32_t accumulate;
-    int32_t nchunks;   // chunks over all slabs
-    int32_t pad;
-};
-
-// Conversion of one row-major FP32 block (plan store) into its B tiles.
-struct TileJob {
-    int64_t src_off, dst_off;
-    int32_t src_ld, m, k, n_pad, nchunks, k_split, k_gap, src_store;
-};
-
-struct TcLaunch {
-    std::vector<TcTask> tasks;
-    std::vector<TcSlab> slabs;
-    TcTask* d_tasks = nullptr;
-    TcSlab* d_slabs = nullptr;
-    int stage = 0;
-};
-
-struct TcPrec {
-    int mode = 0, kc = 0, es = 0;
-    bool split = false;
-    std::vector<TcLaunch> launches;
-    int64_t wt_chunks = 0, sk_chunks = 0;
-    int64_t* d_chunk_pos = nullptr;    // WT chunk -> tree position of its first row
-    int32_t* d_chunk_valid = nullptr;  // WT chunk -> valid rows
-    uint8_t* b_hi = nullptr;
-    uint8_t* b_lo = nullptr;
-    int64_t b_bytes = 0;
-    int64_t r_cap = 0;  // right-hand sides the RT buffers hold (multiple of 128)
-    uint8_t* rt_hi[3] = {nullptr, nullptr, nullptr};
-    uint8_t* rt_lo[3] = {nullptr, nullptr, nullptr};
-    int* d_err = nullptr;
-    int* h_err = nullptr;  // pinned
-    int num_sms = 148;     // persistent grid size
-};
-
-struct TcState {
-    TcPrec* prec[3] = {nullptr, nullptr, nullptr};
-};
-
-static int mode_of(int precision) {
+int mode_of(int precision) {
     return precision == GOFMM_PREC_TF32 ? TC_TF32 : precision == GOFMM_PREC_BF16 ? TC_BF16 : TC_BF16X3;
 }
 
 namespace {
 
-constexpr int kTileBytes = 128 * 128;  // one 128-row x 128-byte operand tile
-constexpr int kMaxN = 256;
 constexpr long long kSpinLimit = 4000000000LL;  // clock cycles (~2 s) before a wait gives up
 constexpr int kErrProducer = 1, kErrMma = 2, kErrEpilogue = 3;
 
@@ -218,22 +159,6 @@ __device__ __forceinline__ uint32_t swz(uint32_t row, uint32_t byte) {
     return row * 128u + ((((byte >> 4) ^ (row & 7u)) << 4) | (byte & 15u));
 }
 
-struct TcParams {
-    const TcTask* tasks;
-    const TcSlab* slabs;
-    int n_rtiles;
-    int ntiles;
-    const uint8_t* b_hi;
-    const uint8_t* b_lo;
-    uint8_t* rt_hi[3];
-    uint8_t* rt_lo[3];
-    int64_t rt_chunks[3];
-    float* U;
-    int64_t ldu;
-    const int64_t* perm;
-    int r;
-    int* err;
-};
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
@@ -245,7 +170,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // (2 x 256 columns), so the epilogue of one tile overlaps the MMAs of the
 // next.
 template <int MODE>
-__global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const TcParams p) {
+__global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
     using C = Cfg<MODE>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -294,23 +219,25 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const TcParams p) {
             uint32_t phase = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                const TcTask tk = p.tasks[t / p.n_rtiles];
-                const int rt = t % p.n_rtiles;
+                const TcTile tt = p.tiles[t];
+                const TcSeg& sg = p.segs[tt.seg];
+                const TcTask tk = sg.tasks[tt.task];
+                const int rt = tt.rt;
                 const uint32_t b_bytes = uint32_t(tk.n_pad) * 128u;
                 for (int si = tk.slab0; si < tk.slab1 && ok; ++si) {
-                    const TcSlab sl = p.slabs[si];
-                    const int64_t a_off = (int64_t(rt) * p.rt_chunks[sl.a_buf] + sl.a_chunk0) * kTileBytes;
-                    const uint8_t* a_hi = p.rt_hi[sl.a_buf] + a_off;
-                    const uint8_t* b_hi = p.b_hi + sl.b_off;
+                    const TcSlab sl = sg.slabs[si];
+                    const int64_t a_off = (int64_t(rt) * sg.rt_chunks[sl.a_buf] + sl.a_chunk0) * kTileBytes;
+                    const uint8_t* a_hi = sg.rt_hi[sl.a_buf] + a_off;
+                    const uint8_t* b_hi = sg.b_hi + sl.b_off;
                     for (int c = 0; c < sl.nchunks; ++c) {
                         if (!mbar_wait(empty_bar(stage), phase ^ 1u, p.err, kErrProducer)) { ok = false; break; }
                         mbar_expect_tx(full_bar(stage), (C::kSplit ? 2u : 1u) * (kTileBytes + b_bytes));
                         bulk_g2s(sA(stage, 0), a_hi + int64_t(c) * kTileBytes, kTileBytes, full_bar(stage));
                         bulk_g2s(sB(stage, 0), b_hi + int64_t(c) * b_bytes, b_bytes, full_bar(stage));
                         if constexpr (C::kSplit) {
-                            bulk_g2s(sA(stage, 1), p.rt_lo[sl.a_buf] + a_off + int64_t(c) * kTileBytes, kTileBytes,
+                            bulk_g2s(sA(stage, 1), sg.rt_lo[sl.a_buf] + a_off + int64_t(c) * kTileBytes, kTileBytes,
                                      full_bar(stage));
-                            bulk_g2s(sB(stage, 1), p.b_lo + sl.b_off + int64_t(c) * b_bytes, b_bytes,
+                            bulk_g2s(sB(stage, 1), sg.b_lo + sl.b_off + int64_t(c) * b_bytes, b_bytes,
                                      full_bar(stage));
                         }
                         ++issued;
@@ -337,7 +264,8 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const TcParams p) {
             uint32_t phase = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
-                const TcTask tk = p.tasks[t / p.n_rtiles];
+                const TcTile tt = p.tiles[t];
+                const TcTask tk = p.segs[tt.seg].tasks[tt.task];
                 const int acc = i & 1;
                 if (!mbar_wait(tempty_bar(acc), uint32_t(((i >> 1) & 1) ^ 1), p.err, kErrMma)) break;
                 tc_fence_after();
@@ -374,45 +302,53 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const TcParams p) {
         const int row = q4 * 32 + lane;  // row of the MMA tile = column of r
         int i = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
-            const TcTask tk = p.tasks[t / p.n_rtiles];
-            const int rt = t % p.n_rtiles;
+            const TcTile tt = p.tiles[t];
+            const TcSeg& sg = p.segs[tt.seg];
+            const TcTask tk = sg.tasks[tt.task];
+            const int rt = tt.rt;
             const int j = rt * 128 + row;
+            const bool jv = j < sg.r;
             const int acc = i & 1;
             bool ok = mbar_wait(tfull_bar(acc), uint32_t((i >> 1) & 1), p.err, kErrEpilogue);
             ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
             if (!ok) break;
             tc_fence_after();
             const uint32_t taddr = tmem + uint32_t(acc * 256) + (uint32_t(q4 * 32) << 16);
-            for (int n0 = 0; n0 < tk.n_pad; n0 += 32) {
+            // RT outputs write the whole output segment of the task (zeros in the
+            // padding columns and in rows j >= r), so every RT element a later
+            // stage reads was written earlier in the same evaluation; only the
+            // in-place S2N pushes touch valid elements alone.
+            const int ncols = tk.out_kind == OUT_U ? tk.n_pad : (tk.accumulate ? tk.n_pad : tk.out_cols);
+            for (int n0 = 0; n0 < ncols; n0 += 32) {
                 float v[32];
-                if (tk.nchunks > 0) {
+                if (tk.nchunks > 0 && n0 < tk.n_pad) {
                     tmem_ld32(taddr + uint32_t(n0), v);
+#pragma unroll
+                    for (int e = 0; e < 32; ++e)
+                        if (n0 + e >= tk.n_pad || !jv) v[e] = 0.f;  // TMEM past n_pad is not this tile's
                 } else {
 #pragma unroll
                     for (int e = 0; e < 32; ++e) v[e] = 0.f;
                 }
-                if (j >= p.r) continue;
                 if (tk.out_kind == OUT_U) {
+                    if (!jv) continue;
 #pragma unroll
                     for (int e = 0; e < 32; ++e) {
                         const int n = n0 + e;
-                        if (n < tk.m) p.U[p.perm[tk.out_pos + n] * p.ldu + j] = v[e];
+                        if (n < tk.m) sg.U[sg.perm[tk.out_pos + n] * sg.ldu + j] = v[e];
                     }
                     continue;
                 }
-                // RT output: 32 consecutive k of this row, inside one chunk.
-                // Only pieces below n_pad are stored: columns in [m, n_pad)
-                // are exact zeros (zero rows of the B tiles); TMEM columns
-                // from n_pad on were not written for this tile and must not
-                // reach the zero padding of the segment.
+                if (tk.accumulate && !jv) continue;
+                // RT output: 32 consecutive k of this row, inside one chunk
                 const int buf = tk.out_kind == OUT_WTIL ? 1 : 2;
                 const int64_t chunk = tk.out_pos + n0 / C::kKc;
                 const uint32_t byte0 = uint32_t((n0 % C::kKc) * C::kEs);
-                uint8_t* thi = p.rt_hi[buf] + (int64_t(rt) * p.rt_chunks[buf] + chunk) * kTileBytes;
+                uint8_t* thi = sg.rt_hi[buf] + (int64_t(rt) * sg.rt_chunks[buf] + chunk) * kTileBytes;
                 if constexpr (MODE == TC_TF32) {
 #pragma unroll
                     for (int piece = 0; piece < 8; ++piece) {
-                        if (n0 + 4 * piece >= tk.n_pad) break;
+                        if (tk.accumulate && n0 + 4 * piece >= tk.n_pad) break;
                         float4* dst = reinterpret_cast<float4*>(thi + swz(row, byte0 + piece * 16));
                         float4 o = make_float4(v[4 * piece], v[4 * piece + 1], v[4 * piece + 2], v[4 * piece + 3]);
                         if (tk.accumulate) {
@@ -422,11 +358,11 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const TcParams p) {
                         *dst = make_float4(round_tf32(o.x), round_tf32(o.y), round_tf32(o.z), round_tf32(o.w));
                     }
                 } else {
-                    uint8_t* tlo = C::kSplit ? p.rt_lo[buf] + (int64_t(rt) * p.rt_chunks[buf] + chunk) * kTileBytes
+                    uint8_t* tlo = C::kSplit ? sg.rt_lo[buf] + (int64_t(rt) * sg.rt_chunks[buf] + chunk) * kTileBytes
                                              : nullptr;
 #pragma unroll
                     for (int piece = 0; piece < 4; ++piece) {
-                        if (n0 + 8 * piece >= tk.n_pad) break;
+                        if (tk.accumulate && n0 + 8 * piece >= tk.n_pad) break;
                         const uint32_t pos = swz(row, byte0 + piece * 16);
                         float x[8];
 #pragma unroll
@@ -586,6 +522,7 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
                 tt.slab0 = int32_t(tl.slabs.size());
                 tt.out_kind = l.out_buf;
                 tt.accumulate = l.accumulate;
+                tt.out_cols = l.out_buf == OUT_U ? tt.n_pad : int32_t(std::min<int64_t>(kMaxN, padk(t.m) - q * kMaxN));
                 for (int si = t.slab0; si < t.slab1; ++si) {
                     const Slab& s = l.slabs[si];
                     if (s.a_src == A_GEN)
@@ -649,7 +586,8 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
             if (t.out_kind == OUT_U)
                 check(t.out_pos >= 0 && t.out_pos + t.m <= st.n, "output rows");
             else
-                check(t.out_pos >= 0 && t.out_pos + (t.n_pad + kc - 1) / kc <= T.sk_chunks, "output chunks");
+                check(t.out_pos >= 0 && t.out_cols % 32 == 0 && t.out_cols >= t.n_pad &&
+                          t.out_pos + t.out_cols / kc <= T.sk_chunks, "output chunks");
             int64_t total = 0;
             for (int si = t.slab0; si < t.slab1; ++si) {
                 const TcSlab& sl = l.slabs[si];
@@ -678,7 +616,20 @@ static void set_smem_attr() {
     CUDA_OK(cudaFuncSetAttribute(tc_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<MODE>::kSmem));
 }
 
-void tc_prepare(Handle& H, DeviceState& D, int64_t r_max, int precision) {
+// Tile list of one launch alone: tasks in plan order (heaviest first), the
+// r-tiles of a task adjacent so they share the task's B tiles through L2.
+static std::pair<TcTile*, int> launch_tiles(TcLaunch& l, int n_rtiles) {
+    auto it = l.tiles.find(n_rtiles);
+    if (it != l.tiles.end()) return it->second;
+    std::vector<TcTile> t;
+    for (size_t k = 0; k < l.tasks.size(); ++k)
+        for (int rt = 0; rt < n_rtiles; ++rt) t.push_back(TcTile{0, int32_t(k), rt, 0});
+    auto v = std::make_pair(dupload(t), int(t.size()));
+    l.tiles[n_rtiles] = v;
+    return v;
+}
+
+TcPrec& tc_plan(Handle& H, DeviceState& D, int precision) {
     if (!D.tc) D.tc = new TcState();
     const int mode = mode_of(precision);
     TcPrec*& T = D.tc->prec[mode];
@@ -716,7 +667,13 @@ void tc_prepare(Handle& H, DeviceState& D, int64_t r_max, int precision) {
         set_smem_attr<TC_BF16X3>();
         T = t.release();
     }
+    return *T;
+}
+
+void tc_prepare(Handle& H, DeviceState& D, int64_t r_max, int precision) {
+    TcPrec* T = &tc_plan(H, D, precision);
     const int64_t r_pad = (r_max + 127) / 128 * 128;
+    for (TcLaunch& l : T->launches) launch_tiles(l, int(r_pad / 128));
     if (T->r_cap < r_pad) {
         for (int i = 0; i < 3; ++i) {
             dfree(T->rt_hi[i]);
@@ -744,43 +701,77 @@ bool tc_ready(const DeviceState& D, int64_t r, int precision) {
     return T && T->r_cap >= r;
 }
 
+// Segment of one launch of one compressed matrix evaluated into the given
+// RT buffers and output.
+TcSeg make_seg(const TcPrec& T, const TcLaunch& l, uint8_t* const* rt_hi, uint8_t* const* rt_lo, float* U,
+                      int64_t ldu, const int64_t* perm, int r) {
+    TcSeg g{};
+    g.tasks = l.d_tasks;
+    g.slabs = l.d_slabs;
+    g.b_hi = T.b_hi;
+    g.b_lo = T.b_lo;
+    for (int i = 0; i < 3; ++i) {
+        g.rt_hi[i] = rt_hi[i];
+        g.rt_lo[i] = rt_lo[i];
+    }
+    g.rt_chunks[0] = T.wt_chunks;
+    g.rt_chunks[1] = g.rt_chunks[2] = T.sk_chunks;
+    g.U = U;
+    g.ldu = ldu;
+    g.perm = perm;
+    g.r = r;
+    return g;
+}
+
 template <int MODE>
+static void launch_gemm(const TcParams& p, int num_sms, cudaStream_t s) {
+    const int grid = std::min(p.ntiles, num_sms);
+    tc_gemm_kernel<MODE><<<unsigned(grid), 192, Cfg<MODE>::kSmem, s>>>(p);
+    CUDA_OK(cudaGetLastError());
+}
+
+void launch_gemm_mode(int mode, const TcParams& p, int num_sms, cudaStream_t s) {
+    if (mode == TC_TF32) launch_gemm<TC_TF32>(p, num_sms, s);
+    else if (mode == TC_BF16) launch_gemm<TC_BF16>(p, num_sms, s);
+    else launch_gemm<TC_BF16X3>(p, num_sms, s);
+}
+
+void launch_gather(int mode, const TcPrec& T, const float* W, int64_t ldw, const int64_t* perm,
+                          uint8_t* wt_hi, uint8_t* wt_lo, int r, cudaStream_t s) {
+    dim3 grid(unsigned(T.wt_chunks), unsigned((r + 127) / 128));
+    if (mode == TC_TF32)
+        tc_gather_kernel<TC_TF32><<<grid, 256, 0, s>>>(W, ldw, perm, T.d_chunk_pos, T.d_chunk_valid, wt_hi, wt_lo,
+                                                       T.wt_chunks, r);
+    else if (mode == TC_BF16)
+        tc_gather_kernel<TC_BF16><<<grid, 256, 0, s>>>(W, ldw, perm, T.d_chunk_pos, T.d_chunk_valid, wt_hi, wt_lo,
+                                                       T.wt_chunks, r);
+    else
+        tc_gather_kernel<TC_BF16X3><<<grid, 256, 0, s>>>(W, ldw, perm, T.d_chunk_pos, T.d_chunk_valid, wt_hi,
+                                                         wt_lo, T.wt_chunks, r);
+    CUDA_OK(cudaGetLastError());
+}
+
 static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, int64_t ldw, float* U, int64_t ldu,
                          int r, cudaStream_t s) {
     const int n_rtiles = (r + 127) / 128;
     int launches = 0;
     const bool timing = H.timing && D.ev_ok;
     if (timing) CUDA_OK(cudaEventRecord(D.ev[0], s));
-    {
-        dim3 grid(unsigned(T.wt_chunks), unsigned(n_rtiles));
-        tc_gather_kernel<MODE><<<grid, 256, 0, s>>>(W, ldw, D.d_idx, T.d_chunk_pos, T.d_chunk_valid, T.rt_hi[0],
-                                                    T.rt_lo[0], T.wt_chunks, r);
-        CUDA_OK(cudaGetLastError());
-        ++launches;
-    }
+    launch_gather(T.mode, T, W, ldw, D.d_idx, T.rt_hi[0], T.rt_lo[0], r, s);
+    ++launches;
     if (timing) CUDA_OK(cudaEventRecord(D.ev[1], s));
     TcParams p{};
-    p.n_rtiles = n_rtiles;
-    p.b_hi = T.b_hi;
-    p.b_lo = T.b_lo;
-    for (int i = 0; i < 3; ++i) { p.rt_hi[i] = T.rt_hi[i]; p.rt_lo[i] = T.rt_lo[i]; }
-    p.rt_chunks[0] = T.wt_chunks;
-    p.rt_chunks[1] = p.rt_chunks[2] = T.sk_chunks;
-    p.U = U;
-    p.ldu = ldu;
-    p.perm = D.d_idx;
-    p.r = r;
+    p.nsegs = 1;
     p.err = T.d_err;
     int stage_done = 1;
-    for (const TcLaunch& l : T.launches) {
+    for (TcLaunch& l : T.launches) {
         while (timing && stage_done < l.stage) CUDA_OK(cudaEventRecord(D.ev[++stage_done], s));
         if (l.tasks.empty()) continue;
-        p.tasks = l.d_tasks;
-        p.slabs = l.d_slabs;
-        p.ntiles = int(l.tasks.size()) * n_rtiles;
-        const int grid = std::min(p.ntiles, T.num_sms);
-        tc_gemm_kernel<MODE><<<unsigned(grid), 192, Cfg<MODE>::kSmem, s>>>(p);
-        CUDA_OK(cudaGetLastError());
+        const auto tl = launch_tiles(l, n_rtiles);
+        p.tiles = tl.first;
+        p.ntiles = tl.second;
+        p.segs[0] = make_seg(T, l, T.rt_hi, T.rt_lo, U, ldu, D.d_idx, r);
+        launch_gemm_mode(T.mode, p, T.num_sms, s);
         ++launches;
     }
     while (timing && stage_done < 5) CUDA_OK(cudaEventRecord(D.ev[++stage_done], s));
@@ -793,9 +784,7 @@ int tc_run(Handle& H, DeviceState& D, const float* W, int64_t ldw, float* U, int
     TcPrec& T = *D.tc->prec[mode_of(precision)];
     if (*reinterpret_cast<volatile int*>(T.h_err) != 0)
         fail(GOFMM_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait (code " + std::to_string(*T.h_err) + ")");
-    if (T.mode == TC_TF32) return tc_launch_all<TC_TF32>(H, D, T, W, ldw, U, ldu, r, s);
-    if (T.mode == TC_BF16) return tc_launch_all<TC_BF16>(H, D, T, W, ldw, U, ldu, r, s);
-    return tc_launch_all<TC_BF16X3>(H, D, T, W, ldw, U, ldu, r, s);
+    return tc_launch_all(H, D, T, W, ldw, U, ldu, r, s);
 }
 
 int tc_error(const DeviceState& D) {
@@ -809,7 +798,11 @@ void tc_destroy(DeviceState& D) {
     if (!D.tc) return;
     for (TcPrec*& T : D.tc->prec) {
         if (!T) continue;
-        for (TcLaunch& l : T->launches) { dfree(l.d_tasks); dfree(l.d_slabs); }
+        for (TcLaunch& l : T->launches) {
+            dfree(l.d_tasks);
+            dfree(l.d_slabs);
+            for (auto& kv : l.tiles) dfree(kv.second.first);
+        }
         dfree(T->d_chunk_pos); dfree(T->d_chunk_valid); dfree(T->b_hi); dfree(T->b_lo); dfree(T->d_err);
         for (int i = 0; i < 3; ++i) { dfree(T->rt_hi[i]); dfree(T->rt_lo[i]); }
         if (T->h_err) cudaFreeHost(T->h_err);

@@ -1,0 +1,115 @@
+// Tensor-core path: plan, stores and launch interface shared by the
+// single-evaluation path (eval_tc.cu) and the batching/serving engine
+// (engine.cu).
+#pragma once
+#include <map>
+#include <utility>
+#include <vector>
+
+#include "eval_state.hpp"
+
+namespace gofmm {
+
+constexpr int kMaxN = 256;              // MMA N per task (taller tasks are split)
+constexpr int kTileBytes = 128 * 128;  // one 128-row x 128-byte operand tile
+
+enum TcMode : int { TC_TF32 = 0, TC_BF16 = 1, TC_BF16X3 = 2 };
+
+
+struct TcSlab {
+    int64_t b_off;     // byte offset of the slab's first chunk tile in the B store
+    int32_t a_buf;     // 0 WT, 1 WTIL, 2 UTIL
+    int32_t a_chunk0;  // first chunk of the slab's K range in that RT buffer
+    int32_t nchunks;
+    int32_t pad;
+};
+
+struct TcTask {
+    int64_t out_pos;  // OUT_U: tree position of row 0; else first chunk of the output segment
+    int32_t m;        // valid output rows (<= 256)
+    int32_t n_pad;    // MMA N: m rounded up to 16
+    int32_t slab0, slab1;
+    int32_t out_kind;  // OUT_WTIL, OUT_UTIL, OUT_U
+    int32_t accumulate;
+    int32_t nchunks;   // chunks over all slabs
+    int32_t out_cols;  // RT outputs: columns of the output segment this task writes (zeros past m)
+};
+
+// One (evaluation, launch) pair inside a tensor-core launch: the tasks and
+// slabs of that launch of one compressed matrix, its B tiles, the RT buffers
+// of that evaluation, and its output.
+struct TcSeg {
+    const TcTask* tasks;
+    const TcSlab* slabs;
+    const uint8_t* b_hi;
+    const uint8_t* b_lo;
+    uint8_t* rt_hi[3];
+    uint8_t* rt_lo[3];
+    int64_t rt_chunks[3];
+    float* U;
+    int64_t ldu;
+    const int64_t* perm;
+    int32_t r;
+    int32_t pad;
+};
+constexpr int kMaxSegs = 64;  // segments per launch (kernel parameters, by value)
+
+struct TcTile {
+    int32_t seg, task, rt, pad;
+};
+
+struct TcParams {
+    const TcTile* tiles;
+    int ntiles;
+    int nsegs;
+    int* err;
+    TcSeg segs[kMaxSegs];
+};
+
+// Conversion of one row-major FP32 block (plan store) into its B tiles.
+struct TileJob {
+    int64_t src_off, dst_off;
+    int32_t src_ld, m, k, n_pad, nchunks, k_split, k_gap, src_store;
+};
+
+struct TcLaunch {
+    std::vector<TcTask> tasks;
+    std::vector<TcSlab> slabs;
+    TcTask* d_tasks = nullptr;
+    TcSlab* d_slabs = nullptr;
+    int stage = 0;
+    std::map<int, std::pair<TcTile*, int>> tiles;  // r-tiles -> tile list of this launch alone
+};
+
+struct TcPrec {
+    int mode = 0, kc = 0, es = 0;
+    bool split = false;
+    std::vector<TcLaunch> launches;
+    int64_t wt_chunks = 0, sk_chunks = 0;
+    int64_t* d_chunk_pos = nullptr;    // WT chunk -> tree position of its first row
+    int32_t* d_chunk_valid = nullptr;  // WT chunk -> valid rows
+    uint8_t* b_hi = nullptr;
+    uint8_t* b_lo = nullptr;
+    int64_t b_bytes = 0;
+    int64_t r_cap = 0;  // right-hand sides the RT buffers hold (multiple of 128)
+    uint8_t* rt_hi[3] = {nullptr, nullptr, nullptr};
+    uint8_t* rt_lo[3] = {nullptr, nullptr, nullptr};
+    int* d_err = nullptr;
+    int* h_err = nullptr;  // pinned
+    int num_sms = 148;     // persistent grid size
+};
+
+struct TcState {
+    TcPrec* prec[3] = {nullptr, nullptr, nullptr};
+};
+
+
+int mode_of(int precision);
+TcPrec& tc_plan(Handle& H, DeviceState& D, int precision);  // plan + B tiles (allocates, synchronises)
+TcSeg make_seg(const TcPrec& T, const TcLaunch& l, uint8_t* const* rt_hi, uint8_t* const* rt_lo, float* U,
+               int64_t ldu, const int64_t* perm, int r);
+void launch_gemm_mode(int mode, const TcParams& p, int num_sms, cudaStream_t s);
+void launch_gather(int mode, const TcPrec& T, const float* W, int64_t ldw, const int64_t* perm, uint8_t* wt_hi,
+                   uint8_t* wt_lo, int r, cudaStream_t s);
+
+}  // namespace gofmm

@@ -8,6 +8,8 @@
 
 #include "gofmm.h"
 
+typedef struct CUstream_st* cudaStream_t;
+
 namespace gofmm {
 
 // Failure carried to the ABI boundary, where it becomes a return code plus
@@ -143,6 +145,16 @@ void device_evaluate_static(Handle& H, const void* W, int64_t ldw, void* U, int6
                             int precision, void* stream);
 void device_destroy(Handle& H);
 void device_synchronize(Handle& H, void* stream);
+
+// Batching / serving engine (engine.cu).
+struct Engine;
+Engine* engine_create(int device, int precision, int64_t pool_bytes);
+int64_t engine_submit(Engine& E, Handle& H, const float* W, int64_t ldw, float* U, int64_t ldu, int64_t r);
+int64_t engine_step(Engine& E, cudaStream_t s);
+int engine_poll(Engine& E, int64_t id);
+void engine_drain(Engine& E, cudaStream_t s);
+void engine_stats(const Engine& E, int64_t* out, int n);
+void engine_destroy(Engine* E);
 void device_stage_times(Handle& H, float* ms, int n);
 
 }  // namespace gofmm

@@ -75,6 +75,14 @@ def _load():
         "gofmm_evaluate_static": (C.c_int, [H, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                             C.c_int64, C.c_int, C.c_int, C.c_void_p]),
         "gofmm_synchronize": (C.c_int, [H, C.c_void_p]),
+        "gofmm_engine_create": (C.c_int, [C.c_int, C.c_int, C.c_int64, C.POINTER(H)]),
+        "gofmm_engine_submit": (C.c_int, [H, H, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int64,
+                                          C.POINTER(C.c_int64)]),
+        "gofmm_engine_step": (C.c_int, [H, C.c_void_p, C.POINTER(C.c_int64)]),
+        "gofmm_engine_poll": (C.c_int, [H, C.c_int64, C.POINTER(C.c_int)]),
+        "gofmm_engine_drain": (C.c_int, [H, C.c_void_p]),
+        "gofmm_engine_stats": (C.c_int, [H, C.POINTER(C.c_int64), C.c_int]),
+        "gofmm_engine_free": (C.c_int, [H]),
         "gofmm_free": (C.c_int, [H]),
         "gofmm_export": (C.c_int, [H, C.c_char_p]),
         "gofmm_import": (C.c_int, [C.c_char_p, C.POINTER(EntriesC), C.c_int, C.c_int, C.POINTER(H)]),
@@ -322,3 +330,62 @@ def structure(h: Handle) -> dict:
         P[node] = pvals[pos:pos + s * nc].reshape(s, nc)
         pos += s * nc
     return dict(depth=L, perm=perm, leaf_off=leaf_off, near=near, far=far, skel=skel, P=P)
+
+
+class Engine:
+    """gofmm_engine: many evaluations in flight, one grouped launch per step."""
+
+    QUEUED, RUNNING, DONE = 0, 1, 2
+
+    def __init__(self, precision: int, pool_bytes: int, device: int = 0):
+        self.ptr = C.c_void_p()
+        _check(LIB.gofmm_engine_create(int(device), int(precision), int(pool_bytes), C.byref(self.ptr)))
+        self._keep = {}
+
+    def submit(self, h: Handle, W, U) -> int:
+        """Queue U = K~ W (torch CUDA float32 tensors, N x r); both must stay
+        alive until the request is done."""
+        if W.stride(1) != 1 or U.stride(1) != 1 or W.shape != U.shape:
+            raise ValueError("W and U: same shape, unit column stride")
+        rid = C.c_int64()
+        _check(LIB.gofmm_engine_submit(self.ptr, h.ptr, C.c_void_p(W.data_ptr()), W.stride(0),
+                                       C.c_void_p(U.data_ptr()), U.stride(0), W.shape[1], C.byref(rid)))
+        self._keep[rid.value] = (h, W, U)
+        return rid.value
+
+    def step(self, stream=None) -> int:
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        n = C.c_int64()
+        _check(LIB.gofmm_engine_step(self.ptr, C.c_void_p(s.cuda_stream), C.byref(n)))
+        return n.value
+
+    def poll(self, rid: int) -> int:
+        st = C.c_int()
+        _check(LIB.gofmm_engine_poll(self.ptr, int(rid), C.byref(st)))
+        if st.value == self.DONE:
+            self._keep.pop(rid, None)
+        return st.value
+
+    def drain(self, stream=None):
+        import torch
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(LIB.gofmm_engine_drain(self.ptr, C.c_void_p(s.cuda_stream)))
+        self._keep.clear()
+
+    def stats(self) -> dict:
+        out = (C.c_int64 * 7)()
+        _check(LIB.gofmm_engine_stats(self.ptr, out, 7))
+        return dict(steps=out[0], launches=out[1], max_active=out[2], completed=out[3], queued=out[4],
+                    running=out[5], finishing=out[6])
+
+    def free(self):
+        if self.ptr:
+            rc = LIB.gofmm_engine_free(self.ptr)
+            self.ptr = None
+            _check(rc)
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            LIB.gofmm_engine_free(self.ptr)
+            self.ptr = None
