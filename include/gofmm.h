@@ -257,6 +257,9 @@ int gofmm_engine_submit(gofmm_engine* e, gofmm_handle* h, const void* W, int64_t
  */
 int gofmm_engine_step(gofmm_engine* e, void* stream, int64_t* pending);
 
+/* *bytes = pool workspace one request of h with r right-hand sides takes. */
+int gofmm_engine_workspace(const gofmm_engine* e, gofmm_handle* h, int64_t r, int64_t* bytes);
+
 /* *state = 0 queued, 1 running, 2 done (its U is complete). */
 int gofmm_engine_poll(gofmm_engine* e, int64_t id, int* state);
 

@@ -322,6 +322,13 @@ int gofmm_engine_step(gofmm_engine* e, void* stream, int64_t* pending) {
     });
 }
 
+int gofmm_engine_workspace(const gofmm_engine* e, gofmm_handle* h, int64_t r, int64_t* bytes) {
+    return guarded([&] {
+        if (!e || !h || !bytes) gofmm::fail(GOFMM_ERR_ARG, "engine, handle and bytes must not be NULL");
+        *bytes = gofmm::engine_workspace(*e->e, h->h, r);
+    });
+}
+
 int gofmm_engine_poll(gofmm_engine* e, int64_t id, int* state) {
     return guarded([&] {
         if (!e || !state) gofmm::fail(GOFMM_ERR_ARG, "engine and state must not be NULL");

@@ -295,6 +295,13 @@ int64_t engine_step(Engine& E, cudaStream_t s) {
     return int64_t(E.queue.size() + E.active.size() + E.finishing.size());
 }
 
+int64_t engine_workspace(const Engine& E, Handle& H, int64_t r) {
+    if (r < 1) fail(GOFMM_ERR_ARG, "r must be >= 1");
+    if (!H.dev || !H.dev->tc || !H.dev->tc->prec[E.mode])
+        fail(GOFMM_ERR_ARG, "handle not prepared for the engine's precision: call gofmm_prepare first");
+    return int64_t(workspace_bytes(*H.dev->tc->prec[E.mode], int((r + 127) / 128)));
+}
+
 int engine_poll(Engine& E, int64_t id) {
     retire(E);
     auto it = E.state.find(id);
@@ -305,14 +312,14 @@ int engine_poll(Engine& E, int64_t id) {
 void engine_drain(Engine& E, cudaStream_t s) {
     DeviceGuard g(E.device);
     while (!E.queue.empty() || !E.active.empty()) {
-        const size_t before = E.queue.size() + E.active.size();
         engine_step(E, s);
-        if (E.active.empty() && !E.queue.empty() && E.queue.size() + E.active.size() == before) {
-            // nothing admitted: wait for finishing requests to free memory
+        // A step that leaves nothing running admitted nothing: the pool is
+        // held by finished requests the GPU may still be completing.
+        if (E.active.empty() && !E.queue.empty()) {
+            if (E.finishing.empty())
+                fail(GOFMM_ERR_NOMEM, "queued request does not fit the pool");  // cannot happen: submit checks
             CUDA_OK(cudaStreamSynchronize(s));
             retire(E);
-            if (E.finishing.empty() && E.active.empty() && !E.queue.empty())
-                fail(GOFMM_ERR_NOMEM, "queued request does not fit the pool");
         }
     }
     CUDA_OK(cudaStreamSynchronize(s));

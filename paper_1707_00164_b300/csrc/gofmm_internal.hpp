@@ -152,6 +152,7 @@ Engine* engine_create(int device, int precision, int64_t pool_bytes);
 int64_t engine_submit(Engine& E, Handle& H, const float* W, int64_t ldw, float* U, int64_t ldu, int64_t r);
 int64_t engine_step(Engine& E, cudaStream_t s);
 int engine_poll(Engine& E, int64_t id);
+int64_t engine_workspace(const Engine& E, Handle& H, int64_t r);
 void engine_drain(Engine& E, cudaStream_t s);
 void engine_stats(const Engine& E, int64_t* out, int n);
 void engine_destroy(Engine* E);

@@ -80,6 +80,7 @@ def _load():
                                           C.POINTER(C.c_int64)]),
         "gofmm_engine_step": (C.c_int, [H, C.c_void_p, C.POINTER(C.c_int64)]),
         "gofmm_engine_poll": (C.c_int, [H, C.c_int64, C.POINTER(C.c_int)]),
+        "gofmm_engine_workspace": (C.c_int, [H, H, C.c_int64, C.POINTER(C.c_int64)]),
         "gofmm_engine_drain": (C.c_int, [H, C.c_void_p]),
         "gofmm_engine_stats": (C.c_int, [H, C.POINTER(C.c_int64), C.c_int]),
         "gofmm_engine_free": (C.c_int, [H]),
@@ -352,6 +353,12 @@ class Engine:
                                        C.c_void_p(U.data_ptr()), U.stride(0), W.shape[1], C.byref(rid)))
         self._keep[rid.value] = (h, W, U)
         return rid.value
+
+    def workspace(self, h: Handle, r: int) -> int:
+        """Pool bytes one request of h with r right-hand sides takes."""
+        b = C.c_int64()
+        _check(LIB.gofmm_engine_workspace(self.ptr, h.ptr, int(r), C.byref(b)))
+        return b.value
 
     def step(self, stream=None) -> int:
         import torch
