@@ -487,6 +487,26 @@ static void far_paper(Structure& st) {
 }
 
 // -------------------------------------------------------- skeletonization --
+// y -= c * x (element-wise; the same rounding on every instruction set, no
+// contraction into FMA)
+__attribute__((target_clones("avx512f", "avx2", "default"))) static void axpy_sub(double* y, const double* x,
+                                                                                double c, int64_t n) {
+    for (int64_t i = 0; i < n; ++i) y[i] -= x[i] * c;
+}
+
+// Dot product with eight independent partial sums (lets the compiler keep
+// several vector lanes busy without reassociating a single sum).
+__attribute__((target_clones("avx512f", "avx2", "default"))) static double dot8(const double* a, const double* b,
+                                                                              int64_t n) {
+    double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int64_t i = 0;
+    for (; i + 8 <= n; i += 8)
+        for (int u = 0; u < 8; ++u) s[u] += a[i + u] * b[i + u];
+    double t = ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+    for (; i < n; ++i) t += a[i] * b[i];
+    return t;
+}
+
 IdResult interpolative_decomposition(std::vector<double>& A, int64_t m, int64_t n,
                                      int64_t max_rank, double tau) {
     IdResult res;
@@ -503,10 +523,8 @@ IdResult interpolative_decomposition(std::vector<double>& A, int64_t m, int64_t 
         double mx = -1.0;
         int64_t jb = k;
         for (int64_t j = k; j < n; ++j) {
-            const double* a = &A[size_t(j * m)];
-            double acc = 0.0;
-            for (int64_t i = k; i < m; ++i) acc += a[i] * a[i];
-            const double nrm = std::sqrt(acc);
+            const double* a = &A[size_t(j * m)] + k;
+            const double nrm = std::sqrt(dot8(a, a, m - k));
             if (nrm > mx || (nrm == mx && perm[j] < perm[jb])) { mx = nrm; jb = j; }
         }
         if (jb != k) {
@@ -525,10 +543,9 @@ IdResult interpolative_decomposition(std::vector<double>& A, int64_t m, int64_t 
         if (vn2 > 0.0) {
             for (int64_t j = k + 1; j < n; ++j) {
                 double* aj = &A[size_t(j * m)];
-                double dot = 0.0;
-                for (int64_t i = k; i < m; ++i) dot += v[i] * aj[i];
+                const double dot = dot8(&v[k], aj + k, m - k);
                 const double coef = (2.0 / vn2) * dot;
-                for (int64_t i = k; i < m; ++i) aj[i] -= v[i] * coef;
+                axpy_sub(aj + k, &v[k], coef, m - k);
             }
         }
         ak[k] = alpha;
