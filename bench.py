@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-dense", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched form")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
     ap.add_argument("--n", type=int, default=0,
                     help="profiling only: the same recipe at another N (not a bench line)")
     return ap.parse_args()
@@ -242,6 +244,133 @@ def whole_job_value(n, r, world, ms_per_rank, reduce_max):
     return n * r * world / (ms_max / 1e3), ms_max
 
 
+# -------------------------------------------------------- batching/serving --
+def compress_many(G, works, device):
+    """Native host compression of several workloads (no GPU work)."""
+    out = []
+    for w in works:
+        pts = w.points()
+        ent = (G.Entries.gaussian(pts, w.bandwidth, w.shift) if w.kernel == wl.GAUSSIAN
+               else G.Entries.imq(pts, w.bandwidth, w.shift))
+        out.append(G.compress(ent, G.default_params(**w.params(), device=device)))
+    return out
+
+
+def batching_bench(G, torch, dev, works, handles, steps, warmup):
+    """64 uneven instances (N log-uniform in [2048, 65536], r in {16..256})
+    as one static batch: one persistent grouped launch per step for all of
+    them, replayed as a CUDA graph; compared with the same 64 evaluations
+    issued one after another."""
+    prec = G.PREC_BF16X3
+    for w, h in zip(works, handles):
+        G.prepare(h, w.r, prec)
+    Ws = [torch.from_numpy(w.rhs().astype(np.float32)).to(dev) for w in works]
+    Us = [torch.empty_like(W) for W in Ws]
+    B = G.Batch(handles, [w.r for w in works], prec)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(warmup, 2)):
+        B.evaluate(Ws, Us, stream)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        B.evaluate(Ws, Us, stream)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    if B.info()["error"]:
+        raise RuntimeError("batched evaluation reported a kernel error")
+    ms = a.elapsed_time(b) / steps
+    # the same evaluations one by one (each replayed from its own graph)
+    seq_ref = [torch.empty_like(W) for W in Ws]
+    for _ in range(2):
+        for h, W, U in zip(handles, Ws, seq_ref):
+            G.evaluate(h, W, U, prec, stream)
+    torch.cuda.synchronize(dev)
+    a.record(stream)
+    for _ in range(max(1, steps // 2)):
+        for h, W, U in zip(handles, Ws, seq_ref):
+            G.evaluate(h, W, U, prec, stream)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    seq_ms = a.elapsed_time(b) / max(1, steps // 2)
+    same = all(torch.equal(U, R) for U, R in zip(Us, seq_ref))
+    nr = sum(w.n * w.r for w in works)
+    info = B.info()
+    B.free()
+    return {"workload": "64 Gaussian instances, N log-uniform [2048, 65536], d U{2..8}, h U[0.3, 1], "
+                        "r U{16..256}, m 256, s 256, tau 1e-5; split BF16x3",
+            "instances": len(works), "sum_N_r": nr, "ms_per_batch": ms, "value": nr / (ms / 1e3),
+            "unit": UNIT, "launches_per_batch": info["launches"], "graph": True,
+            "sequential_ms": seq_ms, "sequential_value": nr / (seq_ms / 1e3),
+            "bitwise_equal_to_sequential": bool(same)}
+
+
+def serving_bench(G, torch, dev, works, handles, loads=(0.5, 0.8, 1.0)):
+    """Continuous batching over 8 resident matrices: seeded Poisson arrivals,
+    matrix uniform, r uniform in [1, 512], BF16 tensor cores; admission by
+    a workspace pool sized from free HBM.  Saturation throughput from a
+    closed run (all requests at t = 0), then open-loop runs at fractions of
+    it with p50/p99 latency (arrival to completion, host clock)."""
+    import time as _t
+    prec = G.PREC_BF16
+    for h in handles:
+        G.prepare(h, 512, prec)
+    Wfull = [torch.from_numpy(w.rhs(512).astype(np.float32)).to(dev) for w in works]
+    free, _ = torch.cuda.mem_get_info(dev)
+    pool = int(max(4 << 30, min(free - (24 << 30), 96 << 30)))
+    eng = G.Engine(prec, pool, dev.index or 0)
+    mats, rs, gaps = wl.serving_requests()
+    stream = torch.cuda.current_stream(dev)
+    units = np.array([works[m].n * int(r) for m, r in zip(mats, rs)], dtype=np.float64)
+
+    def run(arrivals):
+        pending = {}
+        lat = np.zeros(len(mats))
+        i = done = 0
+        t0 = _t.perf_counter()
+        first_done = None
+        while done < len(mats):
+            now = _t.perf_counter() - t0
+            while i < len(mats) and arrivals[i] <= now:
+                m, r = int(mats[i]), int(rs[i])
+                W = Wfull[m][:, :r]
+                U = torch.empty((works[m].n, r), dtype=torch.float32, device=dev)
+                rid = eng.submit(handles[m], W, U)
+                pending[rid] = (i, U)
+                i += 1
+            if pending:
+                eng.step(stream)
+                stream.synchronize()
+                tnow = _t.perf_counter() - t0
+                for rid in list(pending):
+                    if eng.poll(rid) == G.Engine.DONE:
+                        k, _U = pending.pop(rid)
+                        lat[k] = tnow - arrivals[k]
+                        done += 1
+            elif i < len(mats):
+                _t.sleep(max(0.0, min(1e-3, arrivals[i] - now)))
+        return lat, _t.perf_counter() - t0
+
+    run(np.zeros(len(mats)))  # warm-up (graphs, caches, allocator)
+    lat0, t_sat = run(np.zeros(len(mats)))
+    sat_rate = len(mats) / t_sat
+    out = {"workload": "8 resident matrices (N 16384..262144, Gaussian h 0.8 / IMQ l 0.5, d 3..6, m 256, "
+                       "s 256, tau 1e-5); 2000 seeded requests, matrix uniform, r U[1, 512]; BF16",
+           "pool_bytes": pool, "saturation": {"requests_per_s": sat_rate, "value": units.sum() / t_sat,
+                                               "unit": UNIT, "seconds": t_sat},
+           "loads": {}}
+    for ld in loads:
+        arrivals = np.cumsum(gaps) / (ld * sat_rate)
+        lat, tt = run(arrivals)
+        out["loads"][f"{ld:.1f}x"] = {"rate_per_s": ld * sat_rate, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                                      "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                                      "value": units.sum() / tt, "unit": UNIT}
+    st = eng.stats()
+    out["engine"] = {"steps": st["steps"], "launches": st["launches"], "max_in_flight": st["max_active"]}
+    eng.free()
+    return out
+
+
 # ------------------------------------------------------------------ native --
 def native_arm(args):
     import torch
@@ -255,6 +384,26 @@ def native_arm(args):
         dist.init_process_group("nccl", device_id=dev)
     w = WORKLOAD if not args.n else wl.scaled(WORKLOAD, args.n)
     prec_name = args.precision
+    # host-only compression of the batching and serving matrices, overlapped
+    # with the throughput measurement below
+    import threading
+    extra = {}
+    want_batch = rank == 0 and world == 1 and not args.no_batch and not args.n
+    want_serve = rank == 0 and world == 1 and not args.no_serve and not args.n
+
+    def _bg():
+        try:
+            if want_batch:
+                bw = wl.batching_instances()
+                extra["batch"] = (bw, compress_many(G, bw, local))
+            if want_serve:
+                sw = wl.serving_matrices()
+                extra["serve"] = (sw, compress_many(G, sw, local))
+        except Exception as e:  # reported in the JSON line
+            extra["error"] = repr(e)[:300]
+
+    bg = threading.Thread(target=_bg, daemon=True)
+    bg.start()
     prec = G.PRECISIONS[prec_name]
     K = w.matrix()
     entries = G.Entries.gaussian(K.points, w.bandwidth, w.shift)
@@ -402,6 +551,24 @@ def native_arm(args):
     if rank == 0 and world == 1 and not args.no_dense:
         dense = dense_reference(torch, K, W, dev)
 
+    bg.join()
+    batching = serving = None
+    if "batch" in extra:
+        try:
+            batching = batching_bench(G, torch, dev, *extra["batch"], steps=max(3, min(args.steps, 10)),
+                                      warmup=args.warmup)
+        except Exception as e:
+            batching = {"error": repr(e)[:300]}
+        extra.pop("batch")
+    if "serve" in extra:
+        try:
+            serving = serving_bench(G, torch, dev, *extra["serve"])
+        except Exception as e:
+            serving = {"error": repr(e)[:300]}
+        extra.pop("serve")
+    if "error" in extra:
+        batching = batching or {"error": extra["error"]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
@@ -414,7 +581,8 @@ def native_arm(args):
             "data": "synthetic: seeded 6-D standard-normal points, Gaussian kernel; seeded N(0,1) W",
             "config": config_dict(w, prec_name), "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches * args.steps,
-            "accuracy": acc, "modes": modes, "dense_cublas": dense, "compress_seconds": round(compress_s, 2),
+            "accuracy": acc, "modes": modes, "dense_cublas": dense, "batching": batching, "serving": serving,
+            "compress_seconds": round(compress_s, 2),
             "structure": {k: st[k] for k in ("depth", "mean_rank", "max_rank", "near_pairs", "far_pairs",
                                               "near_entries", "far_entries")},
         }))

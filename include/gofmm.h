@@ -273,6 +273,32 @@ int gofmm_engine_stats(const gofmm_engine* e, int64_t* out, int n);
 /* Synchronise the device and free the engine and its pool. */
 int gofmm_engine_free(gofmm_engine* e);
 
+/*
+ * ---- Static batch -----------------------------------------------------------
+ * A fixed list of evaluations (handle i with r[i] right-hand sides, handles
+ * may repeat) planned once: workspaces allocated, the merged step sequence
+ * (one persistent grouped launch per step for all items, plus one gather per
+ * item) built and uploaded.  gofmm_batch_evaluate runs it; calls with the
+ * same W/U pointers replay a CUDA graph of the whole sequence.
+ */
+typedef struct gofmm_batch gofmm_batch;
+
+/* Handles must be prepared for `precision` (TF32, BF16 or BF16X3) and live on
+ * one device.  Allocates the workspaces; synchronises.  Errors: ERR_ARG,
+ * ERR_UNSUPPORTED, ERR_NOMEM, ERR_CUDA. */
+int gofmm_batch_create(gofmm_handle* const* hs, const int64_t* r, int count, int precision, gofmm_batch** out);
+
+/* U[i] = K~_i W[i] for every item (device FP32 pointers, original order,
+ * ld >= r[i]), asynchronously on `stream`. */
+int gofmm_batch_evaluate(gofmm_batch* b, const void* const* W, const int64_t* ldw, void* const* U,
+                         const int64_t* ldu, void* stream);
+
+/* out[0] = kernels the last call launched, out[1] = deferred kernel error code
+ * (nonzero: a bounded wait gave up; read after synchronising). */
+int gofmm_batch_info(const gofmm_batch* b, int64_t* out, int n);
+
+int gofmm_batch_free(gofmm_batch* b);
+
 /* Release the handle and all its host and device memory (synchronises the
  * device first).  NULL is accepted. */
 int gofmm_free(gofmm_handle* h);

@@ -18,6 +18,11 @@ struct gofmm_engine {
     gofmm::Engine* e = nullptr;
 };
 
+struct gofmm_batch {
+    gofmm::Batch* b = nullptr;
+    int last_launches = 0;
+};
+
 namespace {
 thread_local std::string g_last_error;
 
@@ -354,6 +359,46 @@ int gofmm_engine_free(gofmm_engine* e) {
     if (!e) return GOFMM_OK;
     int rc = guarded([&] { gofmm::engine_destroy(e->e); });
     delete e;
+    return rc;
+}
+
+int gofmm_batch_create(gofmm_handle* const* hs, const int64_t* r, int count, int precision, gofmm_batch** out) {
+    if (out) *out = nullptr;
+    return guarded([&] {
+        if (!out || !hs || !r || count < 1) gofmm::fail(GOFMM_ERR_ARG, "bad batch arguments");
+        std::vector<gofmm::Handle*> hv;
+        for (int i = 0; i < count; ++i) {
+            if (!hs[i]) gofmm::fail(GOFMM_ERR_ARG, "NULL handle in batch");
+            hv.push_back(&hs[i]->h);
+        }
+        auto w = std::make_unique<gofmm_batch>();
+        w->b = gofmm::batch_create(hv.data(), r, count, precision);
+        *out = w.release();
+    });
+}
+
+int gofmm_batch_evaluate(gofmm_batch* b, const void* const* W, const int64_t* ldw, void* const* U,
+                         const int64_t* ldu, void* stream) {
+    return guarded([&] {
+        if (!b || !W || !ldw || !U || !ldu) gofmm::fail(GOFMM_ERR_ARG, "bad batch arguments");
+        b->last_launches = gofmm::batch_evaluate(*b->b, reinterpret_cast<const float* const*>(W), ldw,
+                                                 reinterpret_cast<float* const*>(U), ldu,
+                                                 static_cast<cudaStream_t>(stream));
+    });
+}
+
+int gofmm_batch_info(const gofmm_batch* b, int64_t* out, int n) {
+    return guarded([&] {
+        if (!b || !out || n < 1) gofmm::fail(GOFMM_ERR_ARG, "bad arguments");
+        const int64_t v[2] = {int64_t(b->last_launches), int64_t(gofmm::batch_error(*b->b))};
+        for (int i = 0; i < n && i < 2; ++i) out[i] = v[i];
+    });
+}
+
+int gofmm_batch_free(gofmm_batch* b) {
+    if (!b) return GOFMM_OK;
+    int rc = guarded([&] { gofmm::batch_destroy(b->b); });
+    delete b;
     return rc;
 }
 

@@ -359,3 +359,212 @@ void engine_destroy(Engine* E) {
 }
 
 }  // namespace gofmm
+
+// ---------------------------------------------------------------------------
+// Static batch: a fixed set of evaluations (matrix, r) whose merged step
+// sequence is planned once (tile lists uploaded once, workspaces allocated
+// once) and replayed; repeated calls with the same W/U pointers replay a
+// CUDA graph of the whole sequence.
+namespace gofmm {
+
+struct BatchItem {
+    Handle* H;
+    TcPrec* T;
+    int r, n_rtiles;
+    uint8_t* rt_hi[3];
+    uint8_t* rt_lo[3];
+};
+
+struct BatchStep {
+    std::vector<int> gathers;                   // items whose gather runs in this step
+    struct Launch {
+        std::vector<std::pair<int, int>> segs;  // (item, plan launch) per segment
+        TcTile* d_tiles = nullptr;
+        int ntiles = 0;
+    };
+    std::vector<Launch> launches;
+};
+
+struct Batch {
+    int device = 0, precision = 0, mode = 0, num_sms = 148;
+    std::vector<BatchItem> items;
+    std::vector<BatchStep> steps;
+    uint8_t* ws = nullptr;
+    int* d_err = nullptr;
+    int* h_err = nullptr;
+    int launches_per_call = 0;
+    cudaStream_t capture_stream = nullptr;
+    std::map<std::vector<const void*>, std::pair<int, cudaGraphExec_t>> graphs;  // pointers -> (calls, graph)
+};
+
+Batch* batch_create(Handle* const* hs, const int64_t* r, int count, int precision) {
+    if (count < 1) fail(GOFMM_ERR_ARG, "count must be >= 1");
+    if (precision != GOFMM_PREC_TF32 && precision != GOFMM_PREC_BF16 && precision != GOFMM_PREC_BF16X3)
+        fail(GOFMM_ERR_UNSUPPORTED, "batches run the tensor-core precisions (TF32, BF16, BF16X3)");
+    auto B = std::make_unique<Batch>();
+    B->precision = precision;
+    B->mode = mode_of(precision);
+    B->device = hs[0]->st.prm.device;
+    DeviceGuard g(B->device);
+    CUDA_OK(cudaDeviceGetAttribute(&B->num_sms, cudaDevAttrMultiProcessorCount, B->device));
+    size_t total = 0;
+    std::vector<size_t> sizes;
+    for (int i = 0; i < count; ++i) {
+        Handle& H = *hs[i];
+        if (H.st.prm.device != B->device) fail(GOFMM_ERR_ARG, "all handles of a batch must live on one device");
+        if (r[i] < 1 || r[i] > (int64_t(1) << 24)) fail(GOFMM_ERR_ARG, "r must be >= 1");
+        if (!H.dev || !H.dev->tc || !H.dev->tc->prec[B->mode])
+            fail(GOFMM_ERR_ARG, "handle not prepared for the batch precision: call gofmm_prepare first");
+        BatchItem it{};
+        it.H = &H;
+        it.T = H.dev->tc->prec[B->mode];
+        it.r = int(r[i]);
+        it.n_rtiles = int((r[i] + 127) / 128);
+        B->items.push_back(it);
+        sizes.push_back(workspace_bytes(*it.T, it.n_rtiles));
+        total += sizes.back();
+    }
+    B->ws = dalloc<uint8_t>(total);
+    size_t off = 0;
+    for (int i = 0; i < count; ++i) {
+        EngineRequest q{};
+        q.T = B->items[i].T;
+        q.n_rtiles = B->items[i].n_rtiles;
+        q.ws_off = off;
+        carve(q, B->ws);
+        for (int k = 0; k < 3; ++k) {
+            B->items[i].rt_hi[k] = q.rt_hi[k];
+            B->items[i].rt_lo[k] = q.rt_lo[k];
+        }
+        off += sizes[i];
+    }
+    // the step sequence: every item advances one stage per step
+    std::vector<int> next(count, 0);
+    for (;;) {
+        BatchStep st;
+        std::vector<int> gemm;
+        for (int i = 0; i < count; ++i) {
+            const auto& L = B->items[i].T->launches;
+            while (next[i] >= 1 && next[i] <= int(L.size()) && L[next[i] - 1].tasks.empty()) ++next[i];
+            if (next[i] == 0) st.gathers.push_back(i);
+            else if (next[i] <= int(L.size())) gemm.push_back(i);
+        }
+        if (st.gathers.empty() && gemm.empty()) break;
+        for (size_t b0 = 0; b0 < gemm.size(); b0 += kMaxSegs) {
+            BatchStep::Launch bl;
+            std::vector<std::pair<int64_t, TcTile>> tiles;
+            for (size_t k = 0; b0 + k < gemm.size() && k < size_t(kMaxSegs); ++k) {
+                const int i = gemm[b0 + k];
+                const TcLaunch& l = B->items[i].T->launches[next[i] - 1];
+                bl.segs.emplace_back(i, next[i] - 1);
+                for (size_t t = 0; t < l.tasks.size(); ++t) {
+                    const int64_t w = int64_t(l.tasks[t].nchunks) * l.tasks[t].n_pad + 1;
+                    for (int rt = 0; rt < B->items[i].n_rtiles; ++rt)
+                        tiles.emplace_back(w, TcTile{int32_t(k), int32_t(t), rt, 0});
+                }
+            }
+            std::stable_sort(tiles.begin(), tiles.end(),
+                             [](const std::pair<int64_t, TcTile>& a, const std::pair<int64_t, TcTile>& b) {
+                                 return a.first > b.first;
+                             });
+            std::vector<TcTile> tv;
+            for (auto& t : tiles) tv.push_back(t.second);
+            bl.d_tiles = dupload(tv);
+            bl.ntiles = int(tv.size());
+            st.launches.push_back(std::move(bl));
+        }
+        for (int i : st.gathers) next[i] = 1;
+        for (int i : gemm) ++next[i];
+        B->launches_per_call += int(st.gathers.size() + st.launches.size());
+        B->steps.push_back(std::move(st));
+    }
+    B->d_err = dalloc<int>(1);
+    CUDA_OK(cudaMemset(B->d_err, 0, sizeof(int)));
+    CUDA_OK(cudaMallocHost(&B->h_err, sizeof(int)));
+    *B->h_err = 0;
+    CUDA_OK(cudaStreamCreateWithFlags(&B->capture_stream, cudaStreamNonBlocking));
+    return B.release();
+}
+
+static void batch_launch(Batch& B, const float* const* W, const int64_t* ldw, float* const* U, const int64_t* ldu,
+                         cudaStream_t s) {
+    for (const BatchStep& st : B.steps) {
+        for (int i : st.gathers) {
+            const BatchItem& it = B.items[i];
+            launch_gather(B.mode, *it.T, W[i], ldw[i], it.H->dev->d_idx, it.rt_hi[0], it.rt_lo[0], it.r, s);
+        }
+        for (const BatchStep::Launch& bl : st.launches) {
+            TcParams p{};
+            p.nsegs = int(bl.segs.size());
+            p.err = B.d_err;
+            p.tiles = bl.d_tiles;
+            p.ntiles = bl.ntiles;
+            for (size_t k = 0; k < bl.segs.size(); ++k) {
+                const int i = bl.segs[k].first;
+                const BatchItem& it = B.items[i];
+                p.segs[k] = make_seg(*it.T, it.T->launches[bl.segs[k].second], it.rt_hi, it.rt_lo, U[i], ldu[i],
+                                     it.H->dev->d_idx, it.r);
+            }
+            launch_gemm_mode(B.mode, p, B.num_sms, s);
+        }
+    }
+    CUDA_OK(cudaMemcpyAsync(B.h_err, B.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+}
+
+int batch_evaluate(Batch& B, const float* const* W, const int64_t* ldw, float* const* U, const int64_t* ldu,
+                   cudaStream_t s) {
+    DeviceGuard g(B.device);
+    if (*reinterpret_cast<volatile int*>(B.h_err) != 0)
+        fail(GOFMM_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait (code " + std::to_string(*B.h_err) + ")");
+    std::vector<const void*> key;
+    for (size_t i = 0; i < B.items.size(); ++i) {
+        if (!W[i] || !U[i] || ldw[i] < B.items[i].r || ldu[i] < B.items[i].r)
+            fail(GOFMM_ERR_ARG, "bad W/U of batch item " + std::to_string(i));
+        key.push_back(W[i]);
+        key.push_back(U[i]);
+        key.push_back(reinterpret_cast<const void*>(ldw[i]));
+        key.push_back(reinterpret_cast<const void*>(ldu[i]));
+    }
+    auto& e = B.graphs[key];
+    ++e.first;
+    if (!e.second && e.first >= 2) {
+        cudaGraph_t gr = nullptr;
+        CUDA_OK(cudaStreamBeginCapture(B.capture_stream, cudaStreamCaptureModeThreadLocal));
+        try {
+            batch_launch(B, W, ldw, U, ldu, B.capture_stream);
+        } catch (...) {
+            cudaStreamEndCapture(B.capture_stream, &gr);
+            if (gr) cudaGraphDestroy(gr);
+            throw;
+        }
+        CUDA_OK(cudaStreamEndCapture(B.capture_stream, &gr));
+        const cudaError_t ie = cudaGraphInstantiate(&e.second, gr, 0);
+        cudaGraphDestroy(gr);
+        CUDA_OK(ie);
+    }
+    if (e.second) CUDA_OK(cudaGraphLaunch(e.second, s));
+    else batch_launch(B, W, ldw, U, ldu, s);
+    return B.launches_per_call;
+}
+
+int batch_error(const Batch& B) { return *B.h_err; }
+
+void batch_destroy(Batch* B) {
+    if (!B) return;
+    int old = -1;
+    cudaGetDevice(&old);
+    cudaSetDevice(B->device);
+    cudaDeviceSynchronize();
+    for (auto& kv : B->graphs)
+        if (kv.second.second) cudaGraphExecDestroy(kv.second.second);
+    for (BatchStep& st : B->steps)
+        for (auto& bl : st.launches) dfree(bl.d_tiles);
+    dfree(B->ws);
+    dfree(B->d_err);
+    if (B->h_err) cudaFreeHost(B->h_err);
+    if (B->capture_stream) cudaStreamDestroy(B->capture_stream);
+    delete B;
+    if (old >= 0) cudaSetDevice(old);
+}
+
+}  // namespace gofmm

@@ -156,6 +156,13 @@ int64_t engine_workspace(const Engine& E, Handle& H, int64_t r);
 void engine_drain(Engine& E, cudaStream_t s);
 void engine_stats(const Engine& E, int64_t* out, int n);
 void engine_destroy(Engine* E);
+
+struct Batch;
+Batch* batch_create(Handle* const* hs, const int64_t* r, int count, int precision);
+int batch_evaluate(Batch& B, const float* const* W, const int64_t* ldw, float* const* U, const int64_t* ldu,
+                   cudaStream_t s);
+int batch_error(const Batch& B);
+void batch_destroy(Batch* B);
 void device_stage_times(Handle& H, float* ms, int n);
 
 }  // namespace gofmm

@@ -84,6 +84,11 @@ def _load():
         "gofmm_engine_drain": (C.c_int, [H, C.c_void_p]),
         "gofmm_engine_stats": (C.c_int, [H, C.POINTER(C.c_int64), C.c_int]),
         "gofmm_engine_free": (C.c_int, [H]),
+        "gofmm_batch_create": (C.c_int, [C.POINTER(H), C.POINTER(C.c_int64), C.c_int, C.c_int, C.POINTER(H)]),
+        "gofmm_batch_evaluate": (C.c_int, [H, C.POINTER(C.c_void_p), C.POINTER(C.c_int64), C.POINTER(C.c_void_p),
+                                           C.POINTER(C.c_int64), C.c_void_p]),
+        "gofmm_batch_info": (C.c_int, [H, C.POINTER(C.c_int64), C.c_int]),
+        "gofmm_batch_free": (C.c_int, [H]),
         "gofmm_free": (C.c_int, [H]),
         "gofmm_export": (C.c_int, [H, C.c_char_p]),
         "gofmm_import": (C.c_int, [C.c_char_p, C.POINTER(EntriesC), C.c_int, C.c_int, C.POINTER(H)]),
@@ -395,4 +400,43 @@ class Engine:
     def __del__(self):
         if getattr(self, "ptr", None):
             LIB.gofmm_engine_free(self.ptr)
+            self.ptr = None
+
+
+class Batch:
+    """gofmm_batch: a fixed list of evaluations run as one merged step sequence."""
+
+    def __init__(self, handles, rs, precision: int):
+        n = len(handles)
+        hs = (C.c_void_p * n)(*[h.ptr.value if isinstance(h.ptr, C.c_void_p) else h.ptr for h in handles])
+        r = (C.c_int64 * n)(*[int(x) for x in rs])
+        self.ptr = C.c_void_p()
+        _check(LIB.gofmm_batch_create(hs, r, n, int(precision), C.byref(self.ptr)))
+        self.handles = list(handles)
+        self.n = n
+
+    def evaluate(self, Ws, Us, stream=None):
+        import torch
+        n = self.n
+        W = (C.c_void_p * n)(*[w.data_ptr() for w in Ws])
+        U = (C.c_void_p * n)(*[u.data_ptr() for u in Us])
+        lw = (C.c_int64 * n)(*[w.stride(0) for w in Ws])
+        lu = (C.c_int64 * n)(*[u.stride(0) for u in Us])
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _check(LIB.gofmm_batch_evaluate(self.ptr, W, lw, U, lu, C.c_void_p(s.cuda_stream)))
+
+    def info(self) -> dict:
+        out = (C.c_int64 * 2)()
+        _check(LIB.gofmm_batch_info(self.ptr, out, 2))
+        return dict(launches=out[0], error=out[1])
+
+    def free(self):
+        if self.ptr:
+            rc = LIB.gofmm_batch_free(self.ptr)
+            self.ptr = None
+            _check(rc)
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            LIB.gofmm_batch_free(self.ptr)
             self.ptr = None

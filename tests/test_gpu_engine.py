@@ -129,3 +129,20 @@ def test_engine_errors(instances):
     with pytest.raises(G.GofmmError) as e:
         small.submit(hd, W, torch.empty_like(W))
     assert e.value.code == G.ERR_NOMEM
+
+
+def test_static_batch_matches_single_evaluations_and_replays(instances):
+    rs = [16, 256, 100, 129, 37]
+    hs = [hd for _, hd in instances]
+    Ws = [torch.from_numpy(w.rhs(r).astype(np.float32)).cuda() for (w, _), r in zip(instances, rs)]
+    refs = [_single(hd, W) for hd, W in zip(hs, Ws)]
+    B = G.Batch(hs, rs, PREC)
+    Us = [torch.full_like(W, float("nan")) for W in Ws]
+    for _ in range(3):  # first call direct, later calls replay the captured graph
+        for U in Us:
+            U.fill_(float("nan"))
+        B.evaluate(Ws, Us)
+        torch.cuda.synchronize()
+        assert B.info()["error"] == 0
+        for U, ref in zip(Us, refs):
+            assert torch.equal(U, ref)

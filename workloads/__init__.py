@@ -197,3 +197,30 @@ def sample_rows(n: int, count: int = 100, seed: int = 11) -> np.ndarray:
     """Seeded row sample for the accuracy metric (§3: 100 sampled rows)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     return np.sort(rng.choice(n, size=min(count, n), replace=False)).astype(np.int64)
+
+
+def serving_matrices(seed: int = 8):
+    """Eight resident matrices for the serving workload: N in {16384, 32768,
+    65536, 131072, 262144, 32768, 65536, 131072}, Gaussian (h 0.8) and
+    inverse multiquadric (l 0.5) alternating, d ~ U{3..6}, standard-normal
+    points, shift 1e-2, tau 1e-5, m 256, s 256, kappa 32, budget 3 %."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ns = [16384, 32768, 65536, 131072, 262144, 32768, 65536, 131072]
+    out = []
+    for k, n in enumerate(ns):
+        d = int(rng.integers(3, 7))
+        kern, bw = (GAUSSIAN, 0.8) if k % 2 == 0 else (IMQ, 0.5)
+        out.append(Workload(f"serve{k}", n, d, "normal", kern, bw, 1e-2, leaf_size=256, max_rank=256,
+                            tau=1e-5, kappa=32, budget=0.03, r=512, point_seed=3000 + k, w_seed=4000 + k))
+    return out
+
+
+def serving_requests(count: int = 2000, n_matrices: int = 8, seed: int = 9):
+    """Seeded request stream: matrix uniform over the resident ones, r
+    uniform in [1, 512], unit-rate exponential inter-arrival gaps (scale by
+    the arrival rate)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    mats = rng.integers(0, n_matrices, size=count)
+    rs = rng.integers(1, 513, size=count)
+    gaps = rng.exponential(1.0, size=count)
+    return mats, rs, gaps
