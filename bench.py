@@ -264,6 +264,7 @@ def batching_bench(G, torch, dev, works, handles, steps, warmup):
     prec = G.PREC_BF16X3
     for w, h in zip(works, handles):
         G.prepare(h, w.r, prec)
+        G.trim(h)
     Ws = [torch.from_numpy(w.rhs().astype(np.float32)).to(dev) for w in works]
     Us = [torch.empty_like(W) for W in Ws]
     B = G.Batch(handles, [w.r for w in works], prec)
@@ -315,9 +316,12 @@ def serving_bench(G, torch, dev, works, handles, loads=(0.5, 0.8, 1.0)):
     prec = G.PREC_BF16
     for h in handles:
         G.prepare(h, 512, prec)
+        G.trim(h)  # keep only the BF16 tensor-core tiles resident
     Wfull = [torch.from_numpy(w.rhs(512).astype(np.float32)).to(dev) for w in works]
     free, _ = torch.cuda.mem_get_info(dev)
-    pool = int(max(4 << 30, min(free - (24 << 30), 96 << 30)))
+    reserve = 16 << 30
+    pool = int(max(4 << 30, min((free - reserve) // 2, 64 << 30)))   # request workspaces
+    out_budget = int(max(2 << 30, min((free - reserve) // 2, 64 << 30)))  # request outputs U
     eng = G.Engine(prec, pool, dev.index or 0)
     mats, rs, gaps = wl.serving_requests()
     stream = torch.cuda.current_stream(dev)
@@ -327,24 +331,33 @@ def serving_bench(G, torch, dev, works, handles, loads=(0.5, 0.8, 1.0)):
         pending = {}
         lat = np.zeros(len(mats))
         i = done = 0
+        waiting = []          # arrived, output not yet allocated (admission by free HBM)
+        used = 0
         t0 = _t.perf_counter()
-        first_done = None
         while done < len(mats):
             now = _t.perf_counter() - t0
             while i < len(mats) and arrivals[i] <= now:
-                m, r = int(mats[i]), int(rs[i])
-                W = Wfull[m][:, :r]
-                U = torch.empty((works[m].n, r), dtype=torch.float32, device=dev)
-                rid = eng.submit(handles[m], W, U)
-                pending[rid] = (i, U)
+                waiting.append(i)
                 i += 1
+            while waiting:
+                k = waiting[0]
+                m, r = int(mats[k]), int(rs[k])
+                need = works[m].n * r * 4
+                if used + need > out_budget and pending:
+                    break
+                U = torch.empty((works[m].n, r), dtype=torch.float32, device=dev)
+                rid = eng.submit(handles[m], Wfull[m][:, :r], U)
+                pending[rid] = (k, U, need)
+                used += need
+                waiting.pop(0)
             if pending:
                 eng.step(stream)
                 stream.synchronize()
                 tnow = _t.perf_counter() - t0
                 for rid in list(pending):
                     if eng.poll(rid) == G.Engine.DONE:
-                        k, _U = pending.pop(rid)
+                        k, _U, need = pending.pop(rid)
+                        used -= need
                         lat[k] = tnow - arrivals[k]
                         done += 1
             elif i < len(mats):
@@ -356,7 +369,7 @@ def serving_bench(G, torch, dev, works, handles, loads=(0.5, 0.8, 1.0)):
     sat_rate = len(mats) / t_sat
     out = {"workload": "8 resident matrices (N 16384..262144, Gaussian h 0.8 / IMQ l 0.5, d 3..6, m 256, "
                        "s 256, tau 1e-5); 2000 seeded requests, matrix uniform, r U[1, 512]; BF16",
-           "pool_bytes": pool, "saturation": {"requests_per_s": sat_rate, "value": units.sum() / t_sat,
+           "pool_bytes": pool, "output_budget_bytes": out_budget, "saturation": {"requests_per_s": sat_rate, "value": units.sum() / t_sat,
                                                "unit": UNIT, "seconds": t_sat},
            "loads": {}}
     for ld in loads:

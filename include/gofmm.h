@@ -211,6 +211,15 @@ int gofmm_evaluate_static(gofmm_handle* h, const void* W, int64_t ldw, void* U, 
                           int64_t r, int dtype, int precision, void* stream);
 
 /*
+ * Free the device copies the tensor-core precisions do not read (the
+ * row-major FP64/FP32 block and interpolation stores and the CUDA-core
+ * workspaces), keeping the tensor-core tiles of every precision prepared so
+ * far.  A later FP64/FP32 evaluation or a new tensor-core precision rebuilds
+ * what it needs.  Synchronises the device.
+ */
+int gofmm_trim(gofmm_handle* h);
+
+/*
  * Wait for `stream` and report errors the kernels recorded asynchronously:
  * GOFMM_ERR_TIMEOUT when a tensor-core kernel gave up one of its bounded
  * waits (it then returned without finishing; the outputs of that call are

@@ -485,10 +485,14 @@ static void ensure_workspace(Handle& H, int fi, int64_t r) {
 template <typename T>
 static void ensure_staging(Handle& H, int fi, int64_t r) {
     Family& F = H.dev->fam[fi];
-    if (F.dW) return;
-    F.dW = dalloc<T>(size_t(H.dev->n * F.ws_r));
-    F.dU = dalloc<T>(size_t(H.dev->n * F.ws_r));
-    (void)r;
+    if (F.dW && F.stage_r >= r) return;
+    dfree(F.dW);
+    dfree(F.dU);
+    F.dW = F.dU = nullptr;
+    F.stage_r = 0;
+    F.dW = dalloc<T>(size_t(H.dev->n * r));
+    F.dU = dalloc<T>(size_t(H.dev->n * r));
+    F.stage_r = r;
 }
 
 static int family_of(int precision) { return precision == GOFMM_PREC_FP64 ? 0 : 1; }
@@ -511,11 +515,14 @@ void device_prepare(Handle& H, int64_t r_max, int precision) {
         ensure_stores<double>(H, 0);
         ensure_workspace<double>(H, 0, r_max);
         for (Launch& l : H.dev->launches) tiles_for(l, 64);
-    } else {
+    } else if (precision == GOFMM_PREC_FP32) {
         ensure_stores<float>(H, 1);
         ensure_workspace<float>(H, 1, r_max);
         for (Launch& l : H.dev->launches) tiles_for(l, 128);
-        if (precision != GOFMM_PREC_FP32) tc_prepare(H, *H.dev, r_max, precision);
+    } else {
+        // the tensor-core tiles are built from the FP32 stores once
+        if (!tc_ready(*H.dev, 1, precision)) ensure_stores<float>(H, 1);
+        tc_prepare(H, *H.dev, r_max, precision);
     }
     CUDA_OK(cudaDeviceSynchronize());
 }
@@ -651,8 +658,8 @@ void device_evaluate(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu
     DeviceGuard g(H.st.prm.device);
     const int fi = family_of(precision);
     Family* F = H.dev ? &H.dev->fam[fi] : nullptr;
-    const bool ready = H.dev && F->stores && F->ws_r >= r &&
-                       (precision <= GOFMM_PREC_FP32 || tc_ready(*H.dev, r, precision));
+    const bool ready = precision <= GOFMM_PREC_FP32 ? (H.dev && F->stores && F->ws_r >= r)
+                                                    : (H.dev && tc_ready(*H.dev, r, precision));
     if (!ready) device_prepare(H, std::max<int64_t>(r, F ? F->ws_r : 0), precision);
     DeviceState& D = *H.dev;
     F = &D.fam[fi];
@@ -716,6 +723,23 @@ void device_evaluate(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu
         CUDA_OK(cudaMemcpy2DAsync(U, size_t(ldu) * es, F->dU, size_t(r) * es, size_t(r) * es, size_t(D.n),
                                   cudaMemcpyDeviceToHost, s));
         CUDA_OK(cudaStreamSynchronize(s));
+    }
+}
+
+void device_trim(Handle& H) {
+    if (!H.dev) return;
+    DeviceGuard g(H.st.prm.device);
+    CUDA_OK(cudaDeviceSynchronize());
+    clear_graphs(*H.dev);
+    for (Family& F : H.dev->fam) {
+        dfree(F.kstore);
+        dfree(F.pstore);
+        dfree(F.WT);
+        dfree(F.WTIL);
+        dfree(F.UTIL);
+        dfree(F.dW);
+        dfree(F.dU);
+        F = Family{};
     }
 }
 

@@ -80,6 +80,7 @@ struct Family {  // stores and workspace of one element type
     void* UTIL = nullptr;
     void* dW = nullptr;  // device staging for gofmm_evaluate_host
     void* dU = nullptr;
+    int64_t stage_r = 0;
 };
 
 struct DeviceState {

@@ -145,6 +145,7 @@ void device_evaluate_static(Handle& H, const void* W, int64_t ldw, void* U, int6
                             int precision, void* stream);
 void device_destroy(Handle& H);
 void device_synchronize(Handle& H, void* stream);
+void device_trim(Handle& H);
 
 // Batching / serving engine (engine.cu).
 struct Engine;

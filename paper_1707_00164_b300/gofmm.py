@@ -75,6 +75,7 @@ def _load():
         "gofmm_evaluate_static": (C.c_int, [H, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                             C.c_int64, C.c_int, C.c_int, C.c_void_p]),
         "gofmm_synchronize": (C.c_int, [H, C.c_void_p]),
+        "gofmm_trim": (C.c_int, [H]),
         "gofmm_engine_create": (C.c_int, [C.c_int, C.c_int, C.c_int64, C.POINTER(H)]),
         "gofmm_engine_submit": (C.c_int, [H, H, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int64,
                                           C.POINTER(C.c_int64)]),
@@ -254,6 +255,11 @@ def evaluate_host(h: Handle, W: np.ndarray, U: np.ndarray, precision: int, strea
     _check(LIB.gofmm_evaluate_host(h.ptr, C.c_void_p(W.ctypes.data), W.strides[0] // W.itemsize,
                                    C.c_void_p(U.ctypes.data), U.strides[0] // U.itemsize,
                                    W.shape[1], _dtype_code(W), int(precision), sp))
+
+
+def trim(h: Handle):
+    """gofmm_trim: drop device stores only the CUDA-core precisions use."""
+    _check(LIB.gofmm_trim(h.ptr))
 
 
 def synchronize(h: Handle, stream=None):

@@ -108,3 +108,14 @@ def test_graph_replay_matches_direct_launches(prec):
         G.evaluate(h, W, U, prec)
         G.synchronize(h)
         assert torch.equal(U, ref)
+
+
+def test_trim_keeps_tensor_core_results_and_rebuilds_cuda_core_stores():
+    w = wl.scaled(wl.C1, 1200)
+    h, st, K = both(w, leaf_size=64, callback=False)
+    W = w.rhs(40)
+    a = run(h, W, G.PREC_BF16X3)
+    b32 = run(h, W, G.PREC_FP32)
+    G.trim(h)
+    assert np.array_equal(run(h, W, G.PREC_BF16X3), a)   # tiles kept
+    assert np.array_equal(run(h, W, G.PREC_FP32), b32)   # stores rebuilt on demand
