@@ -39,6 +39,7 @@ METRIC = json.load(open(os.path.join(ROOT, "BASELINE.json")))["metric"] \
 UNIT = "N*r/s"
 WORKLOAD = wl.C2
 GOLDEN = os.path.join(ROOT, "tests", "golden", "c2_rows.npz")
+GOLDEN_C3 = os.path.join(ROOT, "tests", "golden", "imq4d_n131072_r2048_rows.npz")
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.json")
 # B300: 148 SMs x 128 FP32 lanes x 2 flop (FMA) per clock
@@ -62,6 +63,7 @@ def parse():
     ap.add_argument("--no-dense", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched form")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
+    ap.add_argument("--no-precision", action="store_true", help="skip the precision workload")
     ap.add_argument("--n", type=int, default=0,
                     help="profiling only: the same recipe at another N (not a bench line)")
     return ap.parse_args()
@@ -306,6 +308,41 @@ def batching_bench(G, torch, dev, works, handles, steps, warmup):
             "bitwise_equal_to_sequential": bool(same)}
 
 
+def precision_bench(G, torch, dev, w, h, steps):
+    """The precision workload (IMQ, 4-D uniform points, N = 131072, m 256,
+    s 512, tau 1e-6, r = 2048): every mode timed, with eps2 against the FP64
+    oracle rows of the same structure and against the exact K W rows."""
+    g = np.load(GOLDEN_C3) if os.path.exists(GOLDEN_C3) else None
+    W = torch.from_numpy(w.rhs(w.r).astype(np.float32)).to(dev)
+    U = torch.empty_like(W)
+    stream = torch.cuda.current_stream(dev)
+    st = G.stats(h)
+    flops = w.r * (st["flops_n2s"] + st["flops_s2s"] + st["flops_s2n"] + st["flops_l2l"])
+    out = {"workload": f"{w.name}: IMQ l 0.5, 4-D uniform points, N {w.n}, m {w.leaf_size}, s {w.max_rank}, "
+                       f"tau {w.tau}, r {w.r}", "flops_per_step": flops, "modes": {}}
+    for name in ("fp32", "tf32", "bf16", "bf16x3"):
+        pr = G.PRECISIONS[name]
+        G.prepare(h, w.r, pr)
+        for _ in range(2):
+            G.evaluate(h, W, U, pr, stream)
+        G.synchronize(h, stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nst = max(2, min(steps, 5))
+        a.record(stream)
+        for _ in range(nst):
+            G.evaluate(h, W, U, pr, stream)
+        b.record(stream)
+        G.synchronize(h, stream)
+        ms = a.elapsed_time(b) / nst
+        ent = {"ms": ms, "value": w.n * w.r / (ms / 1e3), "tflops": flops / (ms / 1e3) / 1e12}
+        if g is not None:
+            got = U[torch.from_numpy(g["rows"]).to(dev)][:, : g["u_oracle"].shape[1]].double().cpu().numpy()
+            ent["eps2_vs_oracle_fp64"] = float(np.linalg.norm(got - g["u_oracle"]) / np.linalg.norm(g["u_oracle"]))
+            ent["eps2_vs_exact_KW"] = float(np.linalg.norm(got - g["u_exact"]) / np.linalg.norm(g["u_exact"]))
+        out["modes"][name] = ent
+    return out
+
+
 def serving_bench(G, torch, dev, works, handles, loads=(0.5, 0.8, 1.0)):
     """Continuous batching over 8 resident matrices: seeded Poisson arrivals,
     matrix uniform, r uniform in [1, 512], BF16 tensor cores; admission by
@@ -403,9 +440,12 @@ def native_arm(args):
     extra = {}
     want_batch = rank == 0 and world == 1 and not args.no_batch and not args.n
     want_serve = rank == 0 and world == 1 and not args.no_serve and not args.n
+    want_prec = rank == 0 and world == 1 and not args.no_precision and not args.n
 
     def _bg():
         try:
+            if want_prec:
+                extra["precision"] = (wl.C3, compress_many(G, [wl.C3], local)[0])
             if want_batch:
                 bw = wl.batching_instances()
                 extra["batch"] = (bw, compress_many(G, bw, local))
@@ -565,7 +605,13 @@ def native_arm(args):
         dense = dense_reference(torch, K, W, dev)
 
     bg.join()
-    batching = serving = None
+    batching = serving = precision = None
+    if "precision" in extra:
+        try:
+            precision = precision_bench(G, torch, dev, *extra["precision"], steps=args.steps)
+        except Exception as e:
+            precision = {"error": repr(e)[:300]}
+        extra.pop("precision")
     if "batch" in extra:
         try:
             batching = batching_bench(G, torch, dev, *extra["batch"], steps=max(3, min(args.steps, 10)),
@@ -594,7 +640,8 @@ def native_arm(args):
             "data": "synthetic: seeded 6-D standard-normal points, Gaussian kernel; seeded N(0,1) W",
             "config": config_dict(w, prec_name), "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches * args.steps,
-            "accuracy": acc, "modes": modes, "dense_cublas": dense, "batching": batching, "serving": serving,
+            "accuracy": acc, "modes": modes, "dense_cublas": dense, "precision_workload": precision, "batching": batching,
+            "serving": serving,
             "compress_seconds": round(compress_s, 2),
             "structure": {k: st[k] for k in ("depth", "mean_rank", "max_rank", "near_pairs", "far_pairs",
                                               "near_entries", "far_entries")},

@@ -119,3 +119,30 @@ def test_trim_keeps_tensor_core_results_and_rebuilds_cuda_core_stores():
     G.trim(h)
     assert np.array_equal(run(h, W, G.PREC_BF16X3), a)   # tiles kept
     assert np.array_equal(run(h, W, G.PREC_FP32), b32)   # stores rebuilt on demand
+
+
+GOLDEN_C3 = os.path.join(os.path.dirname(__file__), "golden", "imq4d_n131072_r2048_rows.npz")
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(not os.path.exists(GOLDEN_C3), reason="oracle rows not generated")
+def test_precision_workload_every_mode_against_oracle_rows():
+    """IMQ kernel, 4-D uniform points, N = 131072, m = 256, s = 512 (ranks up
+    to 512: tasks split across two MMA N tiles), tau 1e-6, r = 2048: every
+    mode against the oracle's FP64 rows (first 64 columns written by
+    tests/golden/make_rows.py)."""
+    g = np.load(GOLDEN_C3)
+    w = wl.C3
+    K = w.matrix()
+    h = G.compress(G.Entries.imq(K.points, w.bandwidth, w.shift), G.default_params(**w.params()))
+    assert G.stats(h)["skel_total"] == int(g["skel_total"])
+    W = torch.from_numpy(w.rhs(w.r).astype(np.float32)).cuda()
+    U = torch.empty_like(W)
+    rows = torch.from_numpy(g["rows"]).cuda()
+    cols = g["u_oracle"].shape[1]
+    for prec, tol in [(G.PREC_FP32, 1e-5)] + [(p, TOL[p]) for p in PRECS]:
+        U.fill_(float("nan"))
+        G.evaluate(h, W, U, prec)
+        G.synchronize(h)
+        got = U[rows][:, :cols].double().cpu().numpy()
+        assert rel(got, g["u_oracle"]) <= tol, (prec, rel(got, g["u_oracle"]))
