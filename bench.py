@@ -41,7 +41,7 @@ WORKLOAD = wl.C2
 GOLDEN = os.path.join(ROOT, "tests", "golden", "c2_rows.npz")
 GOLDEN_C3 = os.path.join(ROOT, "tests", "golden", "imq4d_n131072_r2048_rows.npz")
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic.json")
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic_tc_gemm_s2s.txt")
 # B300: 148 SMs x 128 FP32 lanes x 2 flop (FMA) per clock
 SMS, FP32_LANES = 148, 128
 # tensor-core dense rate relative to BF16 (nominal: TF32 1.1 / BF16 2.25 PFLOP/s)
@@ -585,12 +585,15 @@ def native_arm(args):
                                      f"{NOMINAL_RATIO[prec_name]:.3f} for {prec_name}")
     traffic = None
     if os.path.exists(TRAFFIC_PATH):
-        tr = json.load(open(TRAFFIC_PATH))
-        ent = tr.get(prec_name)
-        src_sha = hashlib.sha256(open(os.path.join(ROOT, "paper_1707_00164_b300", "csrc", ent["source"]),
-                                      "rb").read()).hexdigest() if ent else None
-        if ent and ent.get("sha256") == src_sha:
-            traffic = ent["dram_bytes_per_launch"]
+        tr = {}
+        for line in open(TRAFFIC_PATH):
+            if "=" in line and not line.startswith("#"):
+                k, v = line.split("=", 1)
+                tr[k.strip()] = v.strip()
+        src = os.path.join(ROOT, "paper_1707_00164_b300", "csrc", tr.get("source", "-"))
+        if tr.get("precision") == prec_name and os.path.exists(src) and \
+                hashlib.sha256(open(src, "rb").read()).hexdigest() == tr.get("sha256"):
+            traffic = float(tr["dram_bytes_per_launch"])  # null once the kernel source changed
     kname = ("gemm_simt_kernel" if prec_name in ("fp32", "fp64") else f"tc_gemm_kernel<{prec_name}>")
     roofline = {"kernel": f"{kname}, S2S launch (every far pair of every level, one launch per evaluation)",
                 "bound": bound,
