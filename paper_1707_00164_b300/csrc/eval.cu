@@ -5,13 +5,13 @@
 //   stage 1  leaf N2S tasks  w~_b = P_{b~b} WT[b], then one grouped launch
 //            per inner level, bottom-up:
 //            w~_a = P_{a~[l~r~]} [w~_l; w~_r]                  (N2S, POST)
-//   stage 2  one grouped launch over all levels:
+//   stage 2  one grouped launch over all levels and all leaves:
 //            u~_b = sum_{a in Far(b)} K_{b~a~} w~_a            (S2S)
+//            U[b] = sum_{a in Near(b)} K_{ba} WT[a]            (L2L, scattered
+//                                                   to the original order)
 //   stage 3  one launch per level, top-down, accumulating in place
 //            u~_b += (P^T_{p~[l~r~]} u~_p)[rows of b]          (S2N, PRE)
-//   stage 4  one grouped launch over the leaves, scattered to the original
-//            order:  U[b] = P^T_{b~b} u~_b + sum_{a in Near(b)} K_{ba} WT[a]
-//                                                              (S2N leaf + L2L)
+//   stage 4  one launch over the leaves:  U[b] += P^T_{b~b} u~_b  (S2N leaf)
 // Every launch is a grouped GEMM (eval_plan.hpp) whose tasks own disjoint
 // output rows; the sum over slabs runs in a fixed order inside one CTA, so
 // results are deterministic and nothing is accumulated with atomics (the
@@ -81,11 +81,12 @@ struct GemmParams {
     const T* pts;
     int dim, gen_kind;
     T gen_inv, gen_shift;  // Gaussian: exp(-d2*inv), inv = 1/(2h^2); IMQ: rsqrt(1 + d2*inv), inv = 1/h^2
-    T* out;
-    int64_t ldo;
-    const int64_t* out_map;
+    T* out_wtil;  // OUT_WTIL / OUT_UTIL: packed rows, leading dimension r
+    T* out_util;
+    T* out_u;     // OUT_U: the caller's U, rows through the tree permutation
+    int64_t ldu;
+    const int64_t* perm;
     int r;
-    int accumulate;  // out += sum of slabs (else out = sum of slabs)
 };
 
 __device__ __forceinline__ double kexp(double x) { return exp(x); }
@@ -211,17 +212,19 @@ __global__ void __launch_bounds__(256, 2) gemm_simt_kernel(const GemmParams<T> p
         k0 = nk0;
         cur = nxt;
     }
+    const int okind = task_out(tk.flags);
+    const bool accum = task_accumulate(tk.flags);
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
         const int row = i < TM / 2 ? ty * (TM / 2) + i : BM / 2 + ty * (TM / 2) + i - TM / 2;
         if (row >= mrows) continue;
-        int64_t orow = tk.out_row + m0 + row;
-        if (p.out_map) orow = p.out_map[orow];
-        T* o = p.out + orow * p.ldo;
+        const int64_t orow = tk.out_row + m0 + row;
+        T* o = okind == OUT_U ? p.out_u + p.perm[orow] * p.ldu
+                              : (okind == OUT_WTIL ? p.out_wtil : p.out_util) + orow * int64_t(p.r);
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
             const int col = n0 + (j < TN / 2 ? tx * (TN / 2) + j : BN / 2 + tx * (TN / 2) + j - TN / 2);
-            if (col < p.r) o[col] = p.accumulate ? o[col] + acc[i][j] : acc[i][j];
+            if (col < p.r) o[col] = accum ? o[col] + acc[i][j] : acc[i][j];
         }
     }
 }
@@ -280,9 +283,8 @@ static void build_plan(const Structure& st, bool cached, DeviceState& D) {
     for (int64_t h = 1; h < nn; ++h) field[h] = !st.far[h].empty() || (h > 0 && field[(h - 1) / 2]);
 
     D.launches.clear();
-    auto add_launch = [&](int out_buf, int stage) -> Launch& {
+    auto add_launch = [&](int stage) -> Launch& {
         D.launches.emplace_back();
-        D.launches.back().out_buf = out_buf;
         D.launches.back().stage = stage;
         return D.launches.back();
     };
@@ -293,8 +295,8 @@ static void build_plan(const Structure& st, bool cached, DeviceState& D) {
     };
     if (L == 0) {
         // a single leaf: U = K W
-        Launch& lo = add_launch(OUT_U, 4);
-        Task t{0, int32_t(N), 0, 0, 0};
+        Launch& lo = add_launch(2);
+        Task t{0, int32_t(N), 0, 0, OUT_U};
         lo.slabs.push_back(cached ? slab(A_KSTORE, 0, 0, int(N), int(N), B_WT, 0)
                                   : slab(A_GEN, 0, 0, 0, int(N), B_WT, 0));
         t.slab1 = 1;
@@ -303,10 +305,10 @@ static void build_plan(const Structure& st, bool cached, DeviceState& D) {
     }
     // stage 1 (upward): leaf N2S, then inner N2S bottom-up
     {
-        Launch& l = add_launch(OUT_WTIL, 1);
+        Launch& l = add_launch(1);
         for (int64_t b = 0; b < nl; ++b) {
             const int64_t h = st.leaf_node(b);
-            Task t{D.skel_off[h], int32_t(st.skel[h].size()), int32_t(l.slabs.size()), 0, 0};
+            Task t{D.skel_off[h], int32_t(st.skel[h].size()), int32_t(l.slabs.size()), 0, OUT_WTIL};
             l.slabs.push_back(slab(A_PSTORE, D.p_off[h], 0, int(st.node_size[h]), int(st.node_size[h]), B_WT,
                                    st.node_off[h]));
             t.slab1 = int32_t(l.slabs.size());
@@ -314,23 +316,24 @@ static void build_plan(const Structure& st, bool cached, DeviceState& D) {
         }
     }
     for (int lvl = L - 1; lvl >= 1; --lvl) {
-        Launch& l = add_launch(OUT_WTIL, 1);
+        Launch& l = add_launch(1);
         for (int64_t h = (int64_t(1) << lvl) - 1; h < (int64_t(2) << lvl) - 1; ++h) {
             const int nc = int(st.ncols(h));
-            Task t{D.skel_off[h], int32_t(st.skel[h].size()), int32_t(l.slabs.size()), 0, 0};
+            Task t{D.skel_off[h], int32_t(st.skel[h].size()), int32_t(l.slabs.size()), 0, OUT_WTIL};
             l.slabs.push_back(slab(A_PSTORE, D.p_off[h], 0, nc, nc, B_WTIL, D.skel_off[2 * h + 1]));
             t.slab1 = int32_t(l.slabs.size());
             l.tasks.push_back(t);
         }
     }
-    // stage 2: S2S for every node with a field, all levels in one launch
-    // (tasks of every level run side by side, heaviest first) ...
+    // stage 2: S2S for every node with a field (all levels) and L2L for every
+    // leaf (it needs only W), in one launch; tasks of every level run side
+    // by side, heaviest first ...
     {
-        Launch& l = add_launch(OUT_UTIL, 2);
+        Launch& l = add_launch(2);
         for (int64_t h = 1; h < nn; ++h) {
             if (!field[h]) continue;
             const int64_t sh = int64_t(st.skel[h].size());
-            Task t{D.skel_off[h], int32_t(sh), int32_t(l.slabs.size()), 0, 0};
+            Task t{D.skel_off[h], int32_t(sh), int32_t(l.slabs.size()), 0, OUT_UTIL};
             for (size_t u = 0; u < st.far[h].size(); ++u) {
                 const int64_t a = st.far[h][u];
                 const int sa = int(st.skel[a].size());
@@ -341,31 +344,9 @@ static void build_plan(const Structure& st, bool cached, DeviceState& D) {
             t.slab1 = int32_t(l.slabs.size());
             l.tasks.push_back(t);
         }
-        if (l.tasks.empty()) D.launches.pop_back();
-    }
-    // ... then the S2N pushes level by level, top-down, accumulated in place:
-    // u~_h += (P^T_{p~[l~r~]} u~_p)[rows of h]
-    for (int lvl = 2; lvl <= L; ++lvl) {
-        Launch& l = add_launch(OUT_UTIL, 3);
-        l.accumulate = 1;
-        for (int64_t h = (int64_t(1) << lvl) - 1; h < (int64_t(2) << lvl) - 1; ++h) {
-            const int64_t p = (h - 1) / 2;
-            if (!field[p]) continue;
-            const int sp = int(st.skel[p].size());
-            const int64_t rowoff = (h == 2 * p + 1) ? 0 : int64_t(st.skel[2 * p + 1].size());
-            Task t{D.skel_off[h], int32_t(st.skel[h].size()), int32_t(l.slabs.size()), 0, 0};
-            l.slabs.push_back(slab(A_PSTORE, D.pt_off[p] + rowoff * sp, 0, sp, sp, B_UTIL, D.skel_off[p]));
-            t.slab1 = int32_t(l.slabs.size());
-            l.tasks.push_back(t);
-        }
-        if (l.tasks.empty()) D.launches.pop_back();
-    }
-    // stage 3: leaf S2N + L2L, scattered to the original order
-    {
-        Launch& l = add_launch(OUT_U, 4);
         for (int64_t b = 0; b < nl; ++b) {
             const int64_t h = st.leaf_node(b);
-            Task t{st.node_off[h], int32_t(st.node_size[h]), int32_t(l.slabs.size()), 0, 0};
+            Task t{st.node_off[h], int32_t(st.node_size[h]), int32_t(l.slabs.size()), 0, OUT_U};
             for (size_t u = 0; u < st.near[b].size(); ++u) {
                 const int64_t ha = st.leaf_node(st.near[b][u]);
                 const int na = int(st.node_size[ha]);
@@ -373,13 +354,41 @@ static void build_plan(const Structure& st, bool cached, DeviceState& D) {
                                          : slab(A_GEN, st.node_off[h], st.node_off[ha], 0, na, B_WT,
                                                 st.node_off[ha]));
             }
-            if (field[h]) {
-                const int sh = int(st.skel[h].size());
-                l.slabs.push_back(slab(A_PSTORE, D.pt_off[h], 0, sh, sh, B_UTIL, D.skel_off[h]));
-            }
             t.slab1 = int32_t(l.slabs.size());
             l.tasks.push_back(t);
         }
+    }
+    // ... then the S2N pushes level by level, top-down, accumulated in place:
+    // u~_h += (P^T_{p~[l~r~]} u~_p)[rows of h]
+    for (int lvl = 2; lvl <= L; ++lvl) {
+        Launch& l = add_launch(3);
+        for (int64_t h = (int64_t(1) << lvl) - 1; h < (int64_t(2) << lvl) - 1; ++h) {
+            const int64_t p = (h - 1) / 2;
+            if (!field[p]) continue;
+            const int sp = int(st.skel[p].size());
+            const int64_t rowoff = (h == 2 * p + 1) ? 0 : int64_t(st.skel[2 * p + 1].size());
+            Task t{D.skel_off[h], int32_t(st.skel[h].size()), int32_t(l.slabs.size()), 0,
+                   OUT_UTIL | kTaskAccumulate};
+            l.slabs.push_back(slab(A_PSTORE, D.pt_off[p] + rowoff * sp, 0, sp, sp, B_UTIL, D.skel_off[p]));
+            t.slab1 = int32_t(l.slabs.size());
+            l.tasks.push_back(t);
+        }
+        if (l.tasks.empty()) D.launches.pop_back();
+    }
+    // stage 4: leaf S2N, U[leaf] += P^T_{b~b} u~_b (rows scattered to the
+    // original order) for the leaves with a far field
+    {
+        Launch& l = add_launch(4);
+        for (int64_t b = 0; b < nl; ++b) {
+            const int64_t h = st.leaf_node(b);
+            if (!field[h]) continue;
+            const int sh = int(st.skel[h].size());
+            Task t{st.node_off[h], int32_t(st.node_size[h]), int32_t(l.slabs.size()), 0, OUT_U | kTaskAccumulate};
+            l.slabs.push_back(slab(A_PSTORE, D.pt_off[h], 0, sh, sh, B_UTIL, D.skel_off[h]));
+            t.slab1 = int32_t(l.slabs.size());
+            l.tasks.push_back(t);
+        }
+        if (l.tasks.empty()) D.launches.pop_back();
     }
     // heaviest tasks first inside every launch (better tail behaviour)
     for (Launch& l : D.launches) {
@@ -558,6 +567,11 @@ static int run_simt(Handle& H, const T* W, int64_t ldw, T* U, int64_t ldu, int r
     p.gen_inv = H.K.kind == GOFMM_GEN_GAUSSIAN ? T(1.0 / (2.0 * H.K.h * H.K.h)) : T(1.0 / (H.K.h * H.K.h));
     p.gen_shift = T(H.K.shift);
     p.r = r;
+    p.out_wtil = WTIL;
+    p.out_util = UTIL;
+    p.out_u = U;
+    p.ldu = ldu;
+    p.perm = D.d_idx;
     int stage_done = 1;  // events ev[0..stage_done] recorded; ev[i+1] closes stage i
     for (size_t li = 0; li < D.launches.size(); ++li) {
         Launch& l = D.launches[li];
@@ -567,9 +581,6 @@ static int run_simt(Handle& H, const T* W, int64_t ldw, T* U, int64_t ldu, int r
         p.tasks = l.d_tasks;
         p.slabs = l.d_slabs;
         p.tiles = tl.first;
-        p.accumulate = l.accumulate;
-        if (l.out_buf == OUT_U) { p.out = U; p.ldo = ldu; p.out_map = D.d_idx; }
-        else { p.out = l.out_buf == OUT_WTIL ? WTIL : UTIL; p.ldo = r; p.out_map = nullptr; }
         dim3 grid(unsigned(tl.second), unsigned((r + BN - 1) / BN));
         gemm_simt_kernel<T, TM, TN><<<grid, 256, 0, s>>>(p);
         CUDA_OK(cudaGetLastError());
@@ -611,15 +622,17 @@ static int run_simt_on(Handle& H, const T* W, int64_t ldw, T* U, int64_t ldu, in
     p.gen_inv = H.K.kind == GOFMM_GEN_GAUSSIAN ? T(1.0 / (2.0 * H.K.h * H.K.h)) : T(1.0 / (H.K.h * H.K.h));
     p.gen_shift = T(H.K.shift);
     p.r = r;
+    p.out_wtil = WTIL;
+    p.out_util = UTIL;
+    p.out_u = U;
+    p.ldu = ldu;
+    p.perm = D.d_idx;
     for (Launch& l : D.launches) {
         const auto tl = l.tiles.at(BM);
         if (tl.second == 0) continue;
         p.tasks = l.d_tasks;
         p.slabs = l.d_slabs;
         p.tiles = tl.first;
-        p.accumulate = l.accumulate;
-        if (l.out_buf == OUT_U) { p.out = U; p.ldo = ldu; p.out_map = D.d_idx; }
-        else { p.out = l.out_buf == OUT_WTIL ? WTIL : UTIL; p.ldo = r; p.out_map = nullptr; }
         dim3 grid(unsigned(tl.second), unsigned((r + BN - 1) / BN));
         gemm_simt_kernel<T, TM, TN><<<grid, 256, 0, s>>>(p);
         CUDA_OK(cudaGetLastError());

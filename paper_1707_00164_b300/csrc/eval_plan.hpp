@@ -6,9 +6,16 @@
 // where A_slab is a cached K block, an interpolation matrix P / P^T, or K
 // entries generated on the fly, and B_slab is a row range of one of the
 // tree-ordered right-hand-side buffers.  The tasks of one launch write
-// disjoint rows, so no launch accumulates into memory another CTA writes.
+// disjoint rows (of one of the output buffers, chosen per task), so no
+// launch accumulates into memory another CTA writes.
 #pragma once
 #include <cstdint>
+
+#ifdef __CUDACC__
+#define GOFMM_HD __host__ __device__
+#else
+#define GOFMM_HD
+#endif
 
 namespace gofmm {
 
@@ -30,8 +37,11 @@ struct Task {
     int64_t out_row;  // first output row (tree position for OUT_U, packed row otherwise)
     int32_t m;        // rows
     int32_t slab0, slab1;  // slabs [slab0, slab1)
-    int32_t pad;
+    int32_t flags;    // bits 0-3: OutBuf; bit 4: accumulate (out += sum of slabs)
 };
+constexpr int32_t kTaskAccumulate = 16;
+GOFMM_HD inline int32_t task_out(int32_t flags) { return flags & 15; }
+GOFMM_HD inline bool task_accumulate(int32_t flags) { return (flags & kTaskAccumulate) != 0; }
 
 struct Tile {
     int32_t task;

@@ -60,9 +60,7 @@ inline void dfree(void* p) {
 
 // ---------------------------------------------------------------- plan --
 struct Launch {
-    int out_buf = OUT_WTIL;
     int stage = 0;
-    int accumulate = 0;  // out += sum of slabs
     std::vector<Task> tasks;
     std::vector<Slab> slabs;
     Task* d_tasks = nullptr;

@@ -335,7 +335,10 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
 #pragma unroll
                     for (int e = 0; e < 32; ++e) {
                         const int n = n0 + e;
-                        if (n < tk.m) sg.U[sg.perm[tk.out_pos + n] * sg.ldu + j] = v[e];
+                        if (n < tk.m) {
+                            float* d = sg.U + sg.perm[tk.out_pos + n] * sg.ldu + j;
+                            *d = tk.accumulate ? *d + v[e] : v[e];
+                        }
                     }
                     continue;
                 }
@@ -511,18 +514,19 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
         tl.stage = l.stage;
         for (const Task& t : l.tasks) {
             int64_t out_base;
-            if (l.out_buf == OUT_U) out_base = t.out_row;
+            const int okind = task_out(t.flags);
+            if (okind == OUT_U) out_base = t.out_row;
             else out_base = node_chunk.at(node_at_skel.at(t.out_row));
             for (int64_t q = 0; q * kMaxN < std::max<int64_t>(t.m, 1); ++q) {
                 const int32_t mq = int32_t(std::min<int64_t>(kMaxN, t.m - q * kMaxN));
                 TcTask tt{};
-                tt.out_pos = l.out_buf == OUT_U ? out_base + q * kMaxN : out_base + q * kMaxN / kc;
+                tt.out_pos = okind == OUT_U ? out_base + q * kMaxN : out_base + q * kMaxN / kc;
                 tt.m = mq;
                 tt.n_pad = std::max(16, (mq + 15) / 16 * 16);
                 tt.slab0 = int32_t(tl.slabs.size());
-                tt.out_kind = l.out_buf;
-                tt.accumulate = l.accumulate;
-                tt.out_cols = l.out_buf == OUT_U ? tt.n_pad : int32_t(std::min<int64_t>(kMaxN, padk(t.m) - q * kMaxN));
+                tt.out_kind = okind;
+                tt.accumulate = task_accumulate(t.flags) ? 1 : 0;
+                tt.out_cols = okind == OUT_U ? tt.n_pad : int32_t(std::min<int64_t>(kMaxN, padk(t.m) - q * kMaxN));
                 for (int si = t.slab0; si < t.slab1; ++si) {
                     const Slab& s = l.slabs[si];
                     if (s.a_src == A_GEN)
