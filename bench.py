@@ -568,10 +568,10 @@ def native_arm(args):
 
     # roofline of the grouped-GEMM kernel (all its launches in one evaluation)
     peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
-    # dominant kernel launch: the S2S + L2L grouped GEMM (every far pair of
-    # every level and every near pair, one launch)
+    # dominant kernel launch: the S2S grouped GEMM (every far pair of every
+    # level, one launch)
     flops_all = r * (st["flops_n2s"] + st["flops_s2s"] + st["flops_s2n"] + st["flops_l2l"])
-    flops = r * (st["flops_s2s"] + st["flops_l2l"])
+    flops = r * st["flops_s2s"]
     achieved = flops / (st_ms["s2s"] / 1e3) / 1e12
     gemm_ms = st_ms["upward"] + st_ms["s2s"] + st_ms["s2n"] + st_ms["leaf"]
     if prec_name in ("fp32", "fp64"):
@@ -596,7 +596,7 @@ def native_arm(args):
                 hashlib.sha256(open(src, "rb").read()).hexdigest() == tr.get("sha256"):
             traffic = float(tr["dram_bytes_per_launch"])  # null once the kernel source changed
     kname = ("gemm_simt_kernel" if prec_name in ("fp32", "fp64") else f"tc_gemm_kernel<{prec_name}>")
-    roofline = {"kernel": f"{kname}, S2S + L2L launch (every far pair of every level and every near pair)",
+    roofline = {"kernel": f"{kname}, S2S launch (every far pair of every level, one launch per evaluation)",
                 "bound": bound,
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": peak_src, "traffic": traffic, "flops_per_launch": flops,

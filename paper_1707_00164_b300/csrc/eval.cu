@@ -5,13 +5,13 @@
 //   stage 1  leaf N2S tasks  w~_b = P_{b~b} WT[b], then one grouped launch
 //            per inner level, bottom-up:
 //            w~_a = P_{a~[l~r~]} [w~_l; w~_r]                  (N2S, POST)
-//   stage 2  one grouped launch over all levels and all leaves:
+//   stage 2  one grouped launch over all levels:
 //            u~_b = sum_{a in Far(b)} K_{b~a~} w~_a            (S2S)
-//            U[b] = sum_{a in Near(b)} K_{ba} WT[a]            (L2L, scattered
-//                                                   to the original order)
 //   stage 3  one launch per level, top-down, accumulating in place
 //            u~_b += (P^T_{p~[l~r~]} u~_p)[rows of b]          (S2N, PRE)
-//   stage 4  one launch over the leaves:  U[b] += P^T_{b~b} u~_b  (S2N leaf)
+//   stage 4  one grouped launch over the leaves, scattered to the original
+//            order:  U[b] = P^T_{b~b} u~_b + sum_{a in Near(b)} K_{ba} WT[a]
+//                                                              (S2N leaf + L2L)
 // Every launch is a grouped GEMM (eval_plan.hpp) whose tasks own disjoint
 // output rows; the sum over slabs runs in a fixed order inside one CTA, so
 // results are deterministic and nothing is accumulated with atomics (the
@@ -295,7 +295,7 @@ static void build_plan(const Structure& st, bool cached, DeviceState& D) {
     };
     if (L == 0) {
         // a single leaf: U = K W
-        Launch& lo = add_launch(2);
+        Launch& lo = add_launch(4);
         Task t{0, int32_t(N), 0, 0, OUT_U};
         lo.slabs.push_back(cached ? slab(A_KSTORE, 0, 0, int(N), int(N), B_WT, 0)
                                   : slab(A_GEN, 0, 0, 0, int(N), B_WT, 0));
@@ -325,9 +325,8 @@ static void build_plan(const Structure& st, bool cached, DeviceState& D) {
             l.tasks.push_back(t);
         }
     }
-    // stage 2: S2S for every node with a field (all levels) and L2L for every
-    // leaf (it needs only W), in one launch; tasks of every level run side
-    // by side, heaviest first ...
+    // stage 2: S2S for every node with a field, all levels in one launch
+    // (tasks of every level run side by side, heaviest first) ...
     {
         Launch& l = add_launch(2);
         for (int64_t h = 1; h < nn; ++h) {
@@ -344,19 +343,7 @@ static void build_plan(const Structure& st, bool cached, DeviceState& D) {
             t.slab1 = int32_t(l.slabs.size());
             l.tasks.push_back(t);
         }
-        for (int64_t b = 0; b < nl; ++b) {
-            const int64_t h = st.leaf_node(b);
-            Task t{st.node_off[h], int32_t(st.node_size[h]), int32_t(l.slabs.size()), 0, OUT_U};
-            for (size_t u = 0; u < st.near[b].size(); ++u) {
-                const int64_t ha = st.leaf_node(st.near[b][u]);
-                const int na = int(st.node_size[ha]);
-                l.slabs.push_back(cached ? slab(A_KSTORE, near_koff[b][u], 0, na, na, B_WT, st.node_off[ha])
-                                         : slab(A_GEN, st.node_off[h], st.node_off[ha], 0, na, B_WT,
-                                                st.node_off[ha]));
-            }
-            t.slab1 = int32_t(l.slabs.size());
-            l.tasks.push_back(t);
-        }
+        if (l.tasks.empty()) D.launches.pop_back();
     }
     // ... then the S2N pushes level by level, top-down, accumulated in place:
     // u~_h += (P^T_{p~[l~r~]} u~_p)[rows of h]
@@ -375,20 +362,26 @@ static void build_plan(const Structure& st, bool cached, DeviceState& D) {
         }
         if (l.tasks.empty()) D.launches.pop_back();
     }
-    // stage 4: leaf S2N, U[leaf] += P^T_{b~b} u~_b (rows scattered to the
-    // original order) for the leaves with a far field
+    // stage 4: leaf S2N + L2L, scattered to the original order
     {
         Launch& l = add_launch(4);
         for (int64_t b = 0; b < nl; ++b) {
             const int64_t h = st.leaf_node(b);
-            if (!field[h]) continue;
-            const int sh = int(st.skel[h].size());
-            Task t{st.node_off[h], int32_t(st.node_size[h]), int32_t(l.slabs.size()), 0, OUT_U | kTaskAccumulate};
-            l.slabs.push_back(slab(A_PSTORE, D.pt_off[h], 0, sh, sh, B_UTIL, D.skel_off[h]));
+            Task t{st.node_off[h], int32_t(st.node_size[h]), int32_t(l.slabs.size()), 0, OUT_U};
+            for (size_t u = 0; u < st.near[b].size(); ++u) {
+                const int64_t ha = st.leaf_node(st.near[b][u]);
+                const int na = int(st.node_size[ha]);
+                l.slabs.push_back(cached ? slab(A_KSTORE, near_koff[b][u], 0, na, na, B_WT, st.node_off[ha])
+                                         : slab(A_GEN, st.node_off[h], st.node_off[ha], 0, na, B_WT,
+                                                st.node_off[ha]));
+            }
+            if (field[h]) {
+                const int sh = int(st.skel[h].size());
+                l.slabs.push_back(slab(A_PSTORE, D.pt_off[h], 0, sh, sh, B_UTIL, D.skel_off[h]));
+            }
             t.slab1 = int32_t(l.slabs.size());
             l.tasks.push_back(t);
         }
-        if (l.tasks.empty()) D.launches.pop_back();
     }
     // heaviest tasks first inside every launch (better tail behaviour)
     for (Launch& l : D.launches) {
