@@ -331,8 +331,13 @@ int gofmm_import(const char* path, const gofmm_entries* K, int cache_mode, int d
 int gofmm_stats(const gofmm_handle* h, gofmm_stats_t* s);
 
 /*
- * Stage timing: when enabled, gofmm_evaluate records CUDA events on its
- * stream around each stage.  gofmm_stage_times then synchronises on the last
+ * Stage timing.  enable = 1: gofmm_evaluate runs one launch per stage and
+ * records CUDA events on its stream around each stage (a diagnostic
+ * breakdown).  enable = 2: the production path (for the tensor-core
+ * precisions every grouped GEMM in one dependency-driven launch) with events
+ * around the gather and the GEMM launch; its time is reported as stage 1 and
+ * stages 2-4 read zero.  enable = 0: off (repeated calls may replay a CUDA
+ * graph).  gofmm_stage_times then synchronises on the last
  * event and fills ms[0..5] with the milliseconds of the last call's stages
  * (0 gather of W into tree order, 1 N2S upward pass, 2 S2S (one launch),
  * 3 S2N pushes level by level, 4 leaf S2N+L2L with scatter, 5 whole call)

@@ -491,7 +491,8 @@ int gofmm_stats(const gofmm_handle* hd, gofmm_stats_t* s) {
 int gofmm_set_timing(gofmm_handle* h, int enable) {
     return guarded([&] {
         if (!h) gofmm::fail(GOFMM_ERR_ARG, "handle is NULL");
-        h->h.timing = enable != 0;
+        if (enable < 0 || enable > 2) gofmm::fail(GOFMM_ERR_ARG, "timing level must be 0, 1 or 2");
+        h->h.timing = enable;
     });
 }
 

@@ -538,7 +538,8 @@ static int run_simt(Handle& H, const T* W, int64_t ldw, T* U, int64_t ldu, int r
     T* WTIL = static_cast<T*>(F.WTIL);
     T* UTIL = static_cast<T*>(F.UTIL);
     int launches = 0;
-    const bool timing = H.timing && D.ev_ok;
+    const bool timing = H.timing != 0 && D.ev_ok;
+    D.last_fused = false;
     if (timing) CUDA_OK(cudaEventRecord(D.ev[0], s));
     {
         dim3 blk(32, 8), grid(unsigned((D.n + 7) / 8));
@@ -692,7 +693,7 @@ void device_evaluate(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu
         return tc_run(H, D, static_cast<const float*>(Wd), ldw_d, static_cast<float*>(Ud), ldu_d, int(r),
                       precision, st);
     };
-    if (H.timing || host_buffers) {
+    if (H.timing != 0 || host_buffers) {
         D.last_launches = launch_all(s);
     } else {
         // replay the launch sequence as a CUDA graph once the same call repeats
@@ -766,6 +767,10 @@ void device_stage_times(Handle& H, float* ms, int n) {
     float t[6] = {0, 0, 0, 0, 0, 0};
     for (int i = 0; i < 5; ++i) CUDA_OK(cudaEventElapsedTime(&t[i], D.ev[i], D.ev[i + 1]));
     CUDA_OK(cudaEventElapsedTime(&t[5], D.ev[0], D.ev[5]));
+    if (D.last_fused) {  // gather, then one launch for every grouped GEMM
+        t[1] = t[1] + t[2] + t[3] + t[4];
+        t[2] = t[3] = t[4] = 0.f;
+    }
     for (int i = 0; i < n && i < 6; ++i) ms[i] = t[i];
     if (n > 6) ms[6] = float(D.last_launches);
 }

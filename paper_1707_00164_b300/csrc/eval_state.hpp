@@ -108,6 +108,7 @@ struct DeviceState {
     std::map<std::tuple<int, int64_t, const void*, int64_t, void*, int64_t>, GraphEntry> graphs;
     cudaStream_t capture_stream = nullptr;
     bool ev_ok = false;
+    bool last_fused = false;  // the last tensor-core call ran as one dependency-driven launch
     int last_launches = 0;
 };
 

@@ -46,7 +46,7 @@ int mode_of(int precision) {
 namespace {
 
 constexpr long long kSpinLimit = 4000000000LL;  // clock cycles (~2 s) before a wait gives up
-constexpr int kErrProducer = 1, kErrMma = 2, kErrEpilogue = 3;
+constexpr int kErrProducer = 1, kErrMma = 2, kErrEpilogue = 3, kErrDependency = 4;
 
 template <int MODE>
 struct Cfg {
@@ -90,6 +90,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* er
         }
     }
     return true;
+}
+// Bounded wait until *ctr >= e (acquire); false on timeout or a recorded error.
+__device__ __forceinline__ bool wait_counter(const int* ctr, int e, int* err) {
+    const long long t0 = clock64();
+    for (;;) {
+        int v;
+        asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+        if (v >= e) return true;
+        if (*reinterpret_cast<volatile int*>(err) != 0) return false;
+        if (clock64() - t0 > kSpinLimit) {
+            atomicCAS(err, 0, kErrDependency);
+            return false;
+        }
+        __nanosleep(64);
+    }
 }
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -224,6 +239,14 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
                 const TcTask tk = sg.tasks[tt.task];
                 const int rt = tt.rt;
                 const uint32_t b_bytes = uint32_t(tk.n_pad) * 128u;
+                if (p.dep_off) {
+                    // operands written earlier in this launch by other tiles
+                    for (int d = p.dep_off[tt.task]; d < p.dep_off[tt.task + 1] && ok; ++d)
+                        ok = wait_counter(p.counters + int64_t(p.deps[2 * d]) * p.dep_nrt + rt, p.deps[2 * d + 1],
+                                          p.err);
+                    if (!ok) break;
+                    asm volatile("fence.proxy.async.global;" ::: "memory");  // generic writes -> bulk copies
+                }
                 for (int si = tk.slab0; si < tk.slab1 && ok; ++si) {
                     const TcSlab sl = sg.slabs[si];
                     const int64_t a_off = (int64_t(rt) * sg.rt_chunks[sl.a_buf] + sl.a_chunk0) * kTileBytes;
@@ -397,6 +420,20 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty_bar(acc));
+            if (p.dep_off) {
+                // publish this warp's 32 rows of the tile: consumers wait for
+                // four arrivals (one per epilogue warp) per task piece
+                const int s0 = p.sig[2 * tt.task], s1 = p.sig[2 * tt.task + 1];
+                if (s0 >= 0 || s1 >= 0) {
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) {
+                        __threadfence();
+                        if (s0 >= 0) atomicAdd(p.counters + int64_t(s0) * p.dep_nrt + rt, 1);
+                        if (s1 >= 0) atomicAdd(p.counters + int64_t(s1) * p.dep_nrt + rt, 1);
+                    }
+                }
+            }
         }
     }
     tc_fence_before();
@@ -477,6 +514,102 @@ __global__ void tc_tile_kernel(const TileJob* __restrict__ jobs, const float* __
 }  // namespace
 
 // ------------------------------------------------------------------ host --
+// One launch for every grouped GEMM of an evaluation.  Completion counters
+// per (node, r-tile): w~ written (N2S), u~ written by S2S, u~ final (after
+// the S2N push when there is one).  Each task waits for the counters of what
+// it reads and bumps the counters of what it writes; tasks are ordered by
+// dependency depth (every dependency has a smaller depth, so the order is
+// topological), heaviest first within a depth.
+static void build_fused(const Structure& st, TcPrec& T) {
+    const int64_t nn = st.n_nodes();
+    TcFused& F = T.fused;
+    std::vector<int> pn2s(nn, 0), ps2s(nn, 0), ppush(nn, 0);
+    for (const TcLaunch& l : T.launches)
+        for (size_t k = 0; k < l.tasks.size(); ++k) {
+            const int64_t h = l.task_node[k];
+            if (l.stage == 1) ++pn2s[h];
+            else if (l.stage == 2) ++ps2s[h];
+            else if (l.stage == 3) ++ppush[h];
+        }
+    auto cWT = [&](int64_t h) { return int32_t(h); };
+    auto cS2S = [&](int64_t h) { return int32_t(nn + h); };
+    auto cUF = [&](int64_t h) { return int32_t(2 * nn + h); };
+    auto final_pieces = [&](int64_t h) { return ppush[h] ? ppush[h] : ps2s[h]; };
+    F.ncounters = int(3 * nn);
+    std::vector<int> cdepth(size_t(3 * nn), 0);
+    std::vector<int32_t> dep_off{0}, deps, sig;
+    std::vector<int> depth;
+    std::vector<int64_t> work;
+    F.tasks.clear();
+    F.slabs.clear();
+    for (const TcLaunch& l : T.launches)
+        for (size_t k = 0; k < l.tasks.size(); ++k) {
+            TcTask t = l.tasks[k];
+            const int32_t base = int32_t(F.slabs.size());
+            for (int si = t.slab0; si < t.slab1; ++si) F.slabs.push_back(l.slabs[si]);
+            t.slab1 = base + (t.slab1 - t.slab0);
+            t.slab0 = base;
+            const int64_t h = l.task_node[k];
+            std::vector<std::pair<int32_t, int32_t>> d;  // (counter, arrivals needed)
+            int32_t s0 = -1, s1 = -1;
+            if (l.stage == 1) {
+                if (!st.is_leaf(h)) {
+                    d.emplace_back(cWT(2 * h + 1), 4 * pn2s[2 * h + 1]);
+                    d.emplace_back(cWT(2 * h + 2), 4 * pn2s[2 * h + 2]);
+                }
+                s0 = cWT(h);
+            } else if (l.stage == 2) {
+                for (int64_t a : st.far[h]) d.emplace_back(cWT(a), 4 * pn2s[a]);
+                s0 = cS2S(h);
+                if (!ppush[h]) s1 = cUF(h);
+            } else if (l.stage == 3) {
+                const int64_t par = (h - 1) / 2;
+                d.emplace_back(cS2S(h), 4 * ps2s[h]);
+                d.emplace_back(cUF(par), 4 * final_pieces(par));
+                s0 = cUF(h);
+            } else if (ps2s[h] > 0) {  // leaf output reading u~ of the leaf
+                d.emplace_back(cUF(h), 4 * final_pieces(h));
+            }
+            std::sort(d.begin(), d.end());
+            d.erase(std::unique(d.begin(), d.end()), d.end());
+            int dp = 0;
+            for (auto& x : d) {
+                deps.push_back(x.first);
+                deps.push_back(x.second);
+                dp = std::max(dp, cdepth[x.first]);
+            }
+            dep_off.push_back(int32_t(deps.size() / 2));
+            sig.push_back(s0);
+            sig.push_back(s1);
+            depth.push_back(dp + 1);
+            if (s0 >= 0) cdepth[s0] = std::max(cdepth[s0], dp + 1);
+            if (s1 >= 0) cdepth[s1] = std::max(cdepth[s1], dp + 1);
+            work.push_back(int64_t(t.nchunks) * t.n_pad);
+            F.tasks.push_back(t);
+        }
+    F.order.resize(F.tasks.size());
+    for (size_t i = 0; i < F.order.size(); ++i) F.order[i] = int32_t(i);
+    std::stable_sort(F.order.begin(), F.order.end(), [&](int32_t a, int32_t b) {
+        return depth[a] < depth[b] || (depth[a] == depth[b] && work[a] > work[b]);
+    });
+    F.d_tasks = dupload(F.tasks);
+    F.d_slabs = dupload(F.slabs);
+    F.d_dep_off = dupload(dep_off);
+    F.d_deps = dupload(deps.empty() ? std::vector<int32_t>{0, 0} : deps);
+    F.d_sig = dupload(sig);
+}
+
+static std::pair<TcTile*, int> fused_tiles(TcFused& F, int n_rtiles) {
+    auto it = F.tiles.find(n_rtiles);
+    if (it != F.tiles.end()) return it->second;
+    std::vector<TcTile> t;
+    for (int32_t k : F.order)
+        for (int rt = 0; rt < n_rtiles; ++rt) t.push_back(TcTile{0, k, rt, 0});
+    auto v = std::make_pair(dupload(t), int(t.size()));
+    F.tiles[n_rtiles] = v;
+    return v;
+}
+
 static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::vector<TileJob>& jobs) {
     const int64_t nn = st.n_nodes(), nl = st.n_leaves();
     const int kc = T.kc;
@@ -573,6 +706,8 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
                 }
                 tt.slab1 = int32_t(tl.slabs.size());
                 tl.tasks.push_back(tt);
+                tl.task_node.push_back(okind == OUT_U ? st.leaf_node(leaf_at_pos.at(t.out_row))
+                                                      : node_at_skel.at(t.out_row));
             }
         }
         T.launches.push_back(std::move(tl));
@@ -613,6 +748,7 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
         l.d_tasks = dupload(l.tasks);
         l.d_slabs = dupload(l.slabs);
     }
+    build_fused(st, T);
 }
 
 template <int MODE>
@@ -678,6 +814,13 @@ void tc_prepare(Handle& H, DeviceState& D, int64_t r_max, int precision) {
     TcPrec* T = &tc_plan(H, D, precision);
     const int64_t r_pad = (r_max + 127) / 128 * 128;
     for (TcLaunch& l : T->launches) launch_tiles(l, int(r_pad / 128));
+    TcFused& F = T->fused;
+    if (F.counters_nrt < int(r_pad / 128)) {
+        dfree(F.d_counters);
+        F.d_counters = dalloc<int>(size_t(F.ncounters) * size_t(r_pad / 128));
+        F.counters_nrt = int(r_pad / 128);
+    }
+    for (int nrt = 1; nrt <= int(r_pad / 128); ++nrt) fused_tiles(F, nrt);
     if (T->r_cap < r_pad) {
         for (int i = 0; i < 3; ++i) {
             dfree(T->rt_hi[i]);
@@ -734,6 +877,23 @@ static void launch_gemm(const TcParams& p, int num_sms, cudaStream_t s) {
     CUDA_OK(cudaGetLastError());
 }
 
+// Cooperative launch: every CTA of the persistent grid is resident at once,
+// so tiles waiting on counters bumped by other CTAs always make progress.
+template <int MODE>
+static void launch_gemm_coop(const TcParams& p, int num_sms, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(std::min(p.ntiles, num_sms)));
+    cfg.blockDim = dim3(192);
+    cfg.dynamicSmemBytes = Cfg<MODE>::kSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CUDA_OK(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<MODE>, p));
+}
+
 void launch_gemm_mode(int mode, const TcParams& p, int num_sms, cudaStream_t s) {
     if (mode == TC_TF32) launch_gemm<TC_TF32>(p, num_sms, s);
     else if (mode == TC_BF16) launch_gemm<TC_BF16>(p, num_sms, s);
@@ -759,7 +919,7 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
                          int r, cudaStream_t s) {
     const int n_rtiles = (r + 127) / 128;
     int launches = 0;
-    const bool timing = H.timing && D.ev_ok;
+    const bool timing = H.timing != 0 && D.ev_ok;
     if (timing) CUDA_OK(cudaEventRecord(D.ev[0], s));
     launch_gather(T.mode, T, W, ldw, D.d_idx, T.rt_hi[0], T.rt_lo[0], r, s);
     ++launches;
@@ -767,18 +927,46 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
     TcParams p{};
     p.nsegs = 1;
     p.err = T.d_err;
-    int stage_done = 1;
-    for (TcLaunch& l : T.launches) {
-        while (timing && stage_done < l.stage) CUDA_OK(cudaEventRecord(D.ev[++stage_done], s));
-        if (l.tasks.empty()) continue;
-        const auto tl = launch_tiles(l, n_rtiles);
+    if (H.timing == 1) {
+        // one launch per stage (stage timing)
+        D.last_fused = false;
+        int stage_done = 1;
+        for (TcLaunch& l : T.launches) {
+            while (stage_done < l.stage) CUDA_OK(cudaEventRecord(D.ev[++stage_done], s));
+            if (l.tasks.empty()) continue;
+            const auto tl = launch_tiles(l, n_rtiles);
+            p.tiles = tl.first;
+            p.ntiles = tl.second;
+            p.segs[0] = make_seg(T, l, T.rt_hi, T.rt_lo, U, ldu, D.d_idx, r);
+            launch_gemm_mode(T.mode, p, T.num_sms, s);
+            ++launches;
+        }
+        while (stage_done < 5) CUDA_OK(cudaEventRecord(D.ev[++stage_done], s));
+    } else {
+        // every grouped GEMM in one dependency-driven launch
+        D.last_fused = true;
+        TcFused& F = T.fused;
+        if (F.counters_nrt < n_rtiles) fail(GOFMM_ERR_ARG, "fused plan not prepared for this r");
+        CUDA_OK(cudaMemsetAsync(F.d_counters, 0, size_t(F.ncounters) * n_rtiles * sizeof(int), s));
+        const auto tl = fused_tiles(F, n_rtiles);
         p.tiles = tl.first;
         p.ntiles = tl.second;
-        p.segs[0] = make_seg(T, l, T.rt_hi, T.rt_lo, U, ldu, D.d_idx, r);
-        launch_gemm_mode(T.mode, p, T.num_sms, s);
+        p.dep_off = F.d_dep_off;
+        p.deps = F.d_deps;
+        p.sig = F.d_sig;
+        p.counters = F.d_counters;
+        p.dep_nrt = n_rtiles;
+        TcSeg g = make_seg(T, T.launches.front(), T.rt_hi, T.rt_lo, U, ldu, D.d_idx, r);
+        g.tasks = F.d_tasks;
+        g.slabs = F.d_slabs;
+        p.segs[0] = g;
+        if (T.mode == TC_TF32) launch_gemm_coop<TC_TF32>(p, T.num_sms, s);
+        else if (T.mode == TC_BF16) launch_gemm_coop<TC_BF16>(p, T.num_sms, s);
+        else launch_gemm_coop<TC_BF16X3>(p, T.num_sms, s);
         ++launches;
+        if (timing)
+            for (int i = 2; i <= 5; ++i) CUDA_OK(cudaEventRecord(D.ev[i], s));
     }
-    while (timing && stage_done < 5) CUDA_OK(cudaEventRecord(D.ev[++stage_done], s));
     CUDA_OK(cudaMemcpyAsync(T.h_err, T.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     return launches;
 }
@@ -808,6 +996,12 @@ void tc_destroy(DeviceState& D) {
             for (auto& kv : l.tiles) dfree(kv.second.first);
         }
         dfree(T->d_chunk_pos); dfree(T->d_chunk_valid); dfree(T->b_hi); dfree(T->b_lo); dfree(T->d_err);
+        {
+            TcFused& F = T->fused;
+            dfree(F.d_tasks); dfree(F.d_slabs); dfree(F.d_dep_off); dfree(F.d_deps); dfree(F.d_sig);
+            dfree(F.d_counters);
+            for (auto& kv : F.tiles) dfree(kv.second.first);
+        }
         for (int i = 0; i < 3; ++i) { dfree(T->rt_hi[i]); dfree(T->rt_lo[i]); }
         if (T->h_err) cudaFreeHost(T->h_err);
         delete T;

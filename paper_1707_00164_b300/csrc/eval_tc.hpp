@@ -63,6 +63,15 @@ struct TcParams {
     int ntiles;
     int nsegs;
     int* err;
+    // dependency-driven mode (one launch for a whole evaluation; segment 0
+    // only): tile (task, rt) waits until counters[c * dep_nrt + rt] >= e for
+    // every (c, e) in deps[dep_off[task] .. dep_off[task+1]), and adds one to
+    // counters[sig[2 task + i] * dep_nrt + rt] (i = 0, 1; -1 = none) when done
+    const int32_t* dep_off;  // nullptr: no dependencies
+    const int32_t* deps;
+    const int32_t* sig;
+    int* counters;
+    int dep_nrt;
     TcSeg segs[kMaxSegs];
 };
 
@@ -75,10 +84,27 @@ struct TileJob {
 struct TcLaunch {
     std::vector<TcTask> tasks;
     std::vector<TcSlab> slabs;
+    std::vector<int64_t> task_node;  // node each task writes (host only)
     TcTask* d_tasks = nullptr;
     TcSlab* d_slabs = nullptr;
     int stage = 0;
     std::map<int, std::pair<TcTile*, int>> tiles;  // r-tiles -> tile list of this launch alone
+};
+
+// Every grouped GEMM of one evaluation as one dependency-driven launch.
+struct TcFused {
+    std::vector<TcTask> tasks;
+    std::vector<TcSlab> slabs;
+    std::vector<int32_t> order;  // tasks in a topological, heaviest-first order
+    TcTask* d_tasks = nullptr;
+    TcSlab* d_slabs = nullptr;
+    int32_t* d_dep_off = nullptr;
+    int32_t* d_deps = nullptr;
+    int32_t* d_sig = nullptr;
+    int ncounters = 0;
+    int* d_counters = nullptr;  // ncounters x r-tiles of the largest r prepared
+    int counters_nrt = 0;
+    std::map<int, std::pair<TcTile*, int>> tiles;  // r-tiles -> ordered tile list
 };
 
 struct TcPrec {
@@ -97,6 +123,7 @@ struct TcPrec {
     int* d_err = nullptr;
     int* h_err = nullptr;  // pinned
     int num_sms = 148;     // persistent grid size
+    TcFused fused;
 };
 
 struct TcState {

@@ -134,7 +134,7 @@ struct Handle {
     Structure st;
     Entries K;               // generator kinds keep their points; callbacks are dropped
     DeviceState* dev = nullptr;
-    bool timing = false;
+    int timing = 0;  // 0 off, 1 one launch per stage with stage events, 2 production path with events
 };
 
 // Device side (eval.cu); all throw Error.

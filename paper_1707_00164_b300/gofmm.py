@@ -295,7 +295,7 @@ def stats(h: Handle) -> dict:
 
 
 def set_timing(h: Handle, enable: bool):
-    _check(LIB.gofmm_set_timing(h.ptr, int(bool(enable))))
+    _check(LIB.gofmm_set_timing(h.ptr, int(enable)))
 
 
 def stage_times(h: Handle) -> dict:
