@@ -584,6 +584,16 @@ def native_arm(args):
         flops, launch_ms = flops_all, prod_ms["upward"]
     achieved = flops / (launch_ms / 1e3) / 1e12
     gemm_ms = st_ms["upward"] + st_ms["s2s"] + st_ms["s2n"] + st_ms["leaf"]
+    if prec_name in ("fp32", "fp64"):
+        mhz = peaks.get("sm_max_mhz", 2032.0)
+        per_lane = 2.0 if prec_name == "fp32" else 2.0 / 64.0
+        peak = SMS * FP32_LANES * per_lane * mhz * 1e6 / 1e12
+        bound, peak_src = "alu", f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 flop x {mhz:.0f} MHz"
+    else:
+        bf16 = peaks.get("bf16_tflops", 1800.0)
+        peak = bf16 * NOMINAL_RATIO[prec_name]
+        bound, peak_src = "tensor", (f"of measured bf16 burst ({bf16:.0f} TFLOP/s) x nominal ratio "
+                                     f"{NOMINAL_RATIO[prec_name]:.3f} for {prec_name}")
     traffic = None
     if os.path.exists(TRAFFIC_PATH):
         tr = {}
