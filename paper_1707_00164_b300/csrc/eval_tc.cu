@@ -518,8 +518,8 @@ __global__ void tc_tile_kernel(const TileJob* __restrict__ jobs, const float* __
 // per (node, r-tile): w~ written (N2S), u~ written by S2S, u~ final (after
 // the S2N push when there is one).  Each task waits for the counters of what
 // it reads and bumps the counters of what it writes; tasks are ordered by
-// dependency depth (every dependency has a smaller depth, so the order is
-// topological), heaviest first within a depth.
+// the length of the dependent work that follows them (critical path first),
+// which is a topological order.
 static void build_fused(const Structure& st, TcPrec& T) {
     const int64_t nn = st.n_nodes();
     TcFused& F = T.fused;
@@ -587,11 +587,27 @@ static void build_fused(const Structure& st, TcPrec& T) {
             work.push_back(int64_t(t.nchunks) * t.n_pad);
             F.tasks.push_back(t);
         }
-    F.order.resize(F.tasks.size());
-    for (size_t i = 0; i < F.order.size(); ++i) F.order[i] = int32_t(i);
-    std::stable_sort(F.order.begin(), F.order.end(), [&](int32_t a, int32_t b) {
-        return depth[a] < depth[b] || (depth[a] == depth[b] && work[a] > work[b]);
-    });
+    // priority: the longest chain of dependent work from a task to the end of
+    // the evaluation (critical path first).  A producer's chain is longer
+    // than any of its consumers', so the order stays topological.
+    const size_t nt = F.tasks.size();
+    std::vector<std::vector<int32_t>> consumers(size_t(F.ncounters));
+    for (size_t t = 0; t < nt; ++t)
+        for (int32_t d = dep_off[t]; d < dep_off[t + 1]; ++d) consumers[size_t(deps[2 * d])].push_back(int32_t(t));
+    std::vector<int64_t> tail(nt, 0);
+    for (size_t t = nt; t-- > 0;) {
+        int64_t best = 0;
+        for (int i = 0; i < 2; ++i) {
+            const int32_t c = sig[2 * t + i];
+            if (c < 0) continue;
+            for (int32_t u : consumers[size_t(c)]) best = std::max(best, tail[size_t(u)]);
+        }
+        tail[t] = work[t] + 1024 + best;  // + per-tile overhead
+    }
+    F.order.resize(nt);
+    for (size_t i = 0; i < nt; ++i) F.order[i] = int32_t(i);
+    std::stable_sort(F.order.begin(), F.order.end(), [&](int32_t a, int32_t b) { return tail[a] > tail[b]; });
+    (void)depth;
     F.d_tasks = dupload(F.tasks);
     F.d_slabs = dupload(F.slabs);
     F.d_dep_off = dupload(dep_off);
