@@ -190,13 +190,17 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + C::kStages * C::kStageBytes);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::kStages + 5);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::kStages + 9);
+    int* tid_slot = reinterpret_cast<int*>(tmem_slot + 1);  // [2]: tile ids handed from producer to consumers
     const uint32_t s_base = smem_u32(base);
     auto full_bar = [&](int s) { return smem_u32(&bars[s]); };
     auto empty_bar = [&](int s) { return smem_u32(&bars[C::kStages + s]); };
     auto tfull_bar = [&](int a) { return smem_u32(&bars[2 * C::kStages + a]); };
     auto tempty_bar = [&](int a) { return smem_u32(&bars[2 * C::kStages + 2 + a]); };
     const uint32_t drain_bar = smem_u32(&bars[2 * C::kStages + 4]);
+    auto idfull_bar = [&](int a) { return smem_u32(&bars[2 * C::kStages + 5 + a]); };
+    auto idempty_bar = [&](int a) { return smem_u32(&bars[2 * C::kStages + 7 + a]); };
+    const bool dyn = p.dep_off != nullptr;  // dynamic tile order (dependency mode)
     // stage s: A_hi | B_hi | (A_lo | B_lo)
     auto sA = [&](int s, int lo) { return s_base + s * C::kStageBytes + lo * (kTileBytes + kMaxN * 128); };
     auto sB = [&](int s, int lo) { return sA(s, lo) + kTileBytes; };
@@ -214,6 +218,10 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
             mbar_init(tempty_bar(a), 4);  // one arrival per epilogue warp
         }
         mbar_init(drain_bar, 1);
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(idfull_bar(a), 1);
+            mbar_init(idempty_bar(a), 5);  // MMA thread + four epilogue warps
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -233,7 +241,17 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
             int stage = 0, issued = 0;
             uint32_t phase = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (int i = 0, t = blockIdx.x; ok; ++i) {
+                if (dyn) {
+                    // take the next tile in priority order and hand its id on
+                    if (!mbar_wait(idempty_bar(i & 1), uint32_t(((i >> 1) & 1) ^ 1), p.err, kErrProducer)) break;
+                    t = atomicAdd(p.tile_next, 1);
+                    tid_slot[i & 1] = t < ntiles ? t : -1;
+                    mbar_arrive(idfull_bar(i & 1));
+                } else if (i > 0) {
+                    t += gridDim.x;
+                }
+                if (t >= ntiles) break;
                 const TcTile tt = p.tiles[t];
                 const TcSeg& sg = p.segs[tt.seg];
                 const TcTask tk = sg.tasks[tt.task];
@@ -286,7 +304,14 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
             int stage = 0, i = 0;
             uint32_t phase = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+            for (int t = blockIdx.x; ok; t += gridDim.x, ++i) {
+                if (dyn) {
+                    if (!mbar_wait(idfull_bar(i & 1), uint32_t((i >> 1) & 1), p.err, kErrMma)) break;
+                    t = tid_slot[i & 1];
+                    mbar_arrive(idempty_bar(i & 1));
+                    if (t < 0) break;
+                }
+                if (t >= ntiles) break;
                 const TcTile tt = p.tiles[t];
                 const TcTask tk = p.segs[tt.seg].tasks[tt.task];
                 const int acc = i & 1;
@@ -324,7 +349,17 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
         const int q4 = warp & 3;
         const int row = q4 * 32 + lane;  // row of the MMA tile = column of r
         int i = 0;
-        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+        for (int t = blockIdx.x;; t += gridDim.x, ++i) {
+            if (dyn) {
+                bool okid = mbar_wait(idfull_bar(i & 1), uint32_t((i >> 1) & 1), p.err, kErrEpilogue);
+                okid = __all_sync(0xffffffffu, okid);
+                if (!okid) break;
+                t = tid_slot[i & 1];
+                __syncwarp();
+                if (lane == 0) mbar_arrive(idempty_bar(i & 1));
+                if (t < 0) break;
+            }
+            if (t >= ntiles) break;
             const TcTile tt = p.tiles[t];
             const TcSeg& sg = p.segs[tt.seg];
             const TcTask tk = sg.tasks[tt.task];
@@ -833,7 +868,7 @@ void tc_prepare(Handle& H, DeviceState& D, int64_t r_max, int precision) {
     TcFused& F = T->fused;
     if (F.counters_nrt < int(r_pad / 128)) {
         dfree(F.d_counters);
-        F.d_counters = dalloc<int>(size_t(F.ncounters) * size_t(r_pad / 128));
+        F.d_counters = dalloc<int>(size_t(F.ncounters) * size_t(r_pad / 128) + 1);  // + tile counter
         F.counters_nrt = int(r_pad / 128);
     }
     for (int nrt = 1; nrt <= int(r_pad / 128); ++nrt) fused_tiles(F, nrt);
@@ -963,7 +998,7 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
         D.last_fused = true;
         TcFused& F = T.fused;
         if (F.counters_nrt < n_rtiles) fail(GOFMM_ERR_ARG, "fused plan not prepared for this r");
-        CUDA_OK(cudaMemsetAsync(F.d_counters, 0, size_t(F.ncounters) * n_rtiles * sizeof(int), s));
+        CUDA_OK(cudaMemsetAsync(F.d_counters, 0, (size_t(F.ncounters) * n_rtiles + 1) * sizeof(int), s));
         const auto tl = fused_tiles(F, n_rtiles);
         p.tiles = tl.first;
         p.ntiles = tl.second;
@@ -972,6 +1007,7 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
         p.sig = F.d_sig;
         p.counters = F.d_counters;
         p.dep_nrt = n_rtiles;
+        p.tile_next = F.d_counters + size_t(F.ncounters) * n_rtiles;
         TcSeg g = make_seg(T, T.launches.front(), T.rt_hi, T.rt_lo, U, ldu, D.d_idx, r);
         g.tasks = F.d_tasks;
         g.slabs = F.d_slabs;

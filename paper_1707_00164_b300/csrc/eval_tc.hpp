@@ -72,6 +72,7 @@ struct TcParams {
     const int32_t* sig;
     int* counters;
     int dep_nrt;
+    int* tile_next;  // dependency mode: tiles are taken in order from this counter (dynamic)
     TcSeg segs[kMaxSegs];
 };
 
