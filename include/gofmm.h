@@ -211,6 +211,15 @@ int gofmm_evaluate_static(gofmm_handle* h, const void* W, int64_t ldw, void* U, 
                           int64_t r, int dtype, int precision, void* stream);
 
 /*
+ * Diagnostic for the bounded waits (no counterpart in the paper): the next
+ * gofmm_evaluate of h in `precision` (a tensor-core precision, prepared)
+ * waits on a completion count that nothing reaches.  Its kernel gives up
+ * after about a second, returns, and gofmm_synchronize reports
+ * GOFMM_ERR_TIMEOUT once; the handle and the CUDA context stay usable.
+ */
+int gofmm_debug_stall_next(gofmm_handle* h, int precision);
+
+/*
  * Free the device copies the tensor-core precisions do not read (the
  * row-major FP64/FP32 block and interpolation stores and the CUDA-core
  * workspaces), keeping the tensor-core tiles of every precision prepared so
@@ -223,7 +232,8 @@ int gofmm_trim(gofmm_handle* h);
  * Wait for `stream` and report errors the kernels recorded asynchronously:
  * GOFMM_ERR_TIMEOUT when a tensor-core kernel gave up one of its bounded
  * waits (it then returned without finishing; the outputs of that call are
- * invalid), GOFMM_ERR_CUDA for a CUDA error.
+ * invalid; the error is reported once and cleared), GOFMM_ERR_CUDA for a
+ * CUDA error.
  */
 int gofmm_synchronize(gofmm_handle* h, void* stream);
 

@@ -294,6 +294,13 @@ int gofmm_evaluate_static(gofmm_handle* h, const void* W, int64_t ldw, void* U, 
     });
 }
 
+int gofmm_debug_stall_next(gofmm_handle* h, int precision) {
+    return guarded([&] {
+        if (!h) gofmm::fail(GOFMM_ERR_ARG, "handle is NULL");
+        gofmm::device_stall_next(h->h, precision);
+    });
+}
+
 int gofmm_trim(gofmm_handle* h) {
     return guarded([&] {
         if (!h) gofmm::fail(GOFMM_ERR_ARG, "handle is NULL");

@@ -755,8 +755,17 @@ void device_synchronize(Handle& H, void* stream) {
     DeviceGuard g(H.st.prm.device);
     CUDA_OK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
     CUDA_OK(cudaGetLastError());
-    if (const int e = tc_error(*H.dev))
+    if (const int e = tc_error(*H.dev)) {
+        tc_clear_error(*H.dev);  // reported once; the handle stays usable
         fail(GOFMM_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait (code " + std::to_string(e) + ")");
+    }
+}
+
+void device_stall_next(Handle& H, int precision) {
+    if (!H.dev) fail(GOFMM_ERR_ARG, "handle not prepared: call gofmm_prepare first");
+    DeviceGuard g(H.st.prm.device);
+    tc_stall_next(*H.dev, precision);
+    clear_graphs(*H.dev);  // the next call launches directly
 }
 
 void device_stage_times(Handle& H, float* ms, int n) {

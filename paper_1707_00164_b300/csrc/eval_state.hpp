@@ -126,5 +126,7 @@ int tc_run(Handle& H, DeviceState& D, const float* W, int64_t ldw, float* U, int
            cudaStream_t s);
 void tc_destroy(DeviceState& D);
 int tc_error(const DeviceState& D);  // deferred error code of a tensor-core kernel, 0 if none
+void tc_clear_error(DeviceState& D);
+void tc_stall_next(DeviceState& D, int precision);
 
 }  // namespace gofmm

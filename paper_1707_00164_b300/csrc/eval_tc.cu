@@ -45,7 +45,7 @@ int mode_of(int precision) {
 
 namespace {
 
-constexpr long long kSpinLimit = 4000000000LL;  // clock cycles (~2 s) before a wait gives up
+constexpr long long kSpinLimit = 2000000000LL;  // clock cycles (about a second) before a wait gives up
 constexpr int kErrProducer = 1, kErrMma = 2, kErrEpilogue = 3, kErrDependency = 4;
 
 template <int MODE>
@@ -646,6 +646,7 @@ static void build_fused(const Structure& st, TcPrec& T) {
     F.d_tasks = dupload(F.tasks);
     F.d_slabs = dupload(F.slabs);
     F.d_dep_off = dupload(dep_off);
+    F.deps_host = deps;
     F.d_deps = dupload(deps.empty() ? std::vector<int32_t>{0, 0} : deps);
     F.d_sig = dupload(sig);
 }
@@ -1004,6 +1005,10 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
         p.ntiles = tl.second;
         p.dep_off = F.d_dep_off;
         p.deps = F.d_deps;
+        if (F.stall_next) {  // diagnostic: one dependency nothing satisfies
+            p.deps = F.d_deps_stall;
+            F.stall_next = false;
+        }
         p.sig = F.d_sig;
         p.counters = F.d_counters;
         p.dep_nrt = n_rtiles;
@@ -1031,6 +1036,28 @@ int tc_run(Handle& H, DeviceState& D, const float* W, int64_t ldw, float* U, int
     return tc_launch_all(H, D, T, W, ldw, U, ldu, r, s);
 }
 
+void tc_stall_next(DeviceState& D, int precision) {
+    if (!D.tc || !D.tc->prec[mode_of(precision)])
+        fail(GOFMM_ERR_ARG, "handle not prepared for this precision: call gofmm_prepare first");
+    TcFused& F = D.tc->prec[mode_of(precision)]->fused;
+    if (!F.d_deps_stall) {
+        std::vector<int32_t> deps(F.deps_host);
+        if (deps.size() < 2) fail(GOFMM_ERR_UNSUPPORTED, "the plan has no dependency to stall");
+        deps[1] = 1 << 30;  // an arrival count no counter reaches
+        F.d_deps_stall = dupload(deps);
+    }
+    F.stall_next = true;
+}
+
+void tc_clear_error(DeviceState& D) {
+    if (!D.tc) return;
+    for (TcPrec* T : D.tc->prec)
+        if (T && T->h_err && *T->h_err) {
+            CUDA_OK(cudaMemset(T->d_err, 0, sizeof(int)));
+            *T->h_err = 0;
+        }
+}
+
 int tc_error(const DeviceState& D) {
     if (!D.tc) return 0;
     for (const TcPrec* T : D.tc->prec)
@@ -1051,6 +1078,7 @@ void tc_destroy(DeviceState& D) {
         {
             TcFused& F = T->fused;
             dfree(F.d_tasks); dfree(F.d_slabs); dfree(F.d_dep_off); dfree(F.d_deps); dfree(F.d_sig);
+            dfree(F.d_deps_stall);
             dfree(F.d_counters);
             for (auto& kv : F.tiles) dfree(kv.second.first);
         }

@@ -103,8 +103,11 @@ struct TcFused {
     int32_t* d_deps = nullptr;
     int32_t* d_sig = nullptr;
     int ncounters = 0;
-    int* d_counters = nullptr;  // ncounters x r-tiles of the largest r prepared
+    int* d_counters = nullptr;  // ncounters x r-tiles of the largest r prepared (+ tile counter)
     int counters_nrt = 0;
+    std::vector<int32_t> deps_host;
+    int32_t* d_deps_stall = nullptr;  // diagnostic copy with one unreachable arrival count
+    bool stall_next = false;
     std::map<int, std::pair<TcTile*, int>> tiles;  // r-tiles -> ordered tile list
 };
 

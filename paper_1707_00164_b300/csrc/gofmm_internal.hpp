@@ -146,6 +146,7 @@ void device_evaluate_static(Handle& H, const void* W, int64_t ldw, void* U, int6
 void device_destroy(Handle& H);
 void device_synchronize(Handle& H, void* stream);
 void device_trim(Handle& H);
+void device_stall_next(Handle& H, int precision);
 
 // Batching / serving engine (engine.cu).
 struct Engine;

@@ -76,6 +76,7 @@ def _load():
                                             C.c_int64, C.c_int, C.c_int, C.c_void_p]),
         "gofmm_synchronize": (C.c_int, [H, C.c_void_p]),
         "gofmm_trim": (C.c_int, [H]),
+        "gofmm_debug_stall_next": (C.c_int, [H, C.c_int]),
         "gofmm_engine_create": (C.c_int, [C.c_int, C.c_int, C.c_int64, C.POINTER(H)]),
         "gofmm_engine_submit": (C.c_int, [H, H, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int64,
                                           C.POINTER(C.c_int64)]),
@@ -255,6 +256,12 @@ def evaluate_host(h: Handle, W: np.ndarray, U: np.ndarray, precision: int, strea
     _check(LIB.gofmm_evaluate_host(h.ptr, C.c_void_p(W.ctypes.data), W.strides[0] // W.itemsize,
                                    C.c_void_p(U.ctypes.data), U.strides[0] // U.itemsize,
                                    W.shape[1], _dtype_code(W), int(precision), sp))
+
+
+def debug_stall_next(h: Handle, precision: int):
+    """gofmm_debug_stall_next: the next evaluation waits on a count nothing
+    reaches (tests the bounded-wait error path)."""
+    _check(LIB.gofmm_debug_stall_next(h.ptr, int(precision)))
 
 
 def trim(h: Handle):
