@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched form")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
     ap.add_argument("--no-precision", action="store_true", help="skip the precision workload")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default tensor-core configuration instead of autotuning it")
     ap.add_argument("--n", type=int, default=0,
                     help="profiling only: the same recipe at another N (not a bench line)")
     return ap.parse_args()
@@ -258,19 +260,21 @@ def compress_many(G, works, device):
     return out
 
 
-def batching_bench(G, torch, dev, works, handles, steps, warmup):
+def batching_bench(G, torch, dev, works, handles, steps, warmup, tuning=True):
     """64 uneven instances (N log-uniform in [2048, 65536], r in {16..256})
     as one static batch: one persistent grouped launch per step for all of
     them, replayed as a CUDA graph; compared with the same 64 evaluations
     issued one after another."""
     prec = G.PREC_BF16X3
+    stream = torch.cuda.current_stream(dev)
     for w, h in zip(works, handles):
         G.prepare(h, w.r, prec)
+    tune = G.autotune_batch(handles, [w.r for w in works], prec, None, stream) if tuning else None
+    for h in handles:
         G.trim(h)
     Ws = [torch.from_numpy(w.rhs().astype(np.float32)).to(dev) for w in works]
     Us = [torch.empty_like(W) for W in Ws]
     B = G.Batch(handles, [w.r for w in works], prec)
-    stream = torch.cuda.current_stream(dev)
     for _ in range(max(warmup, 2)):
         B.evaluate(Ws, Us, stream)
     torch.cuda.synchronize(dev)
@@ -305,10 +309,13 @@ def batching_bench(G, torch, dev, works, handles, steps, warmup):
             "instances": len(works), "sum_N_r": nr, "ms_per_batch": ms, "value": nr / (ms / 1e3),
             "unit": UNIT, "launches_per_batch": info["launches"], "graph": True,
             "sequential_ms": seq_ms, "sequential_value": nr / (seq_ms / 1e3),
-            "bitwise_equal_to_sequential": bool(same)}
+            "bitwise_equal_to_sequential": bool(same),
+            "autotune": None if tune is None else {
+                "piece": tune["piece"], "candidates_ms": {str(c["piece"]): round(c["ms"], 4)
+                                                          for c in tune["candidates"]}}}
 
 
-def precision_bench(G, torch, dev, w, h, steps):
+def precision_bench(G, torch, dev, w, h, steps, tuning=True):
     """The precision workload (IMQ, 4-D uniform points, N = 131072, m 256,
     s 512, tau 1e-6, r = 2048): every mode timed, with eps2 against the FP64
     oracle rows of the same structure and against the exact K W rows."""
@@ -323,6 +330,7 @@ def precision_bench(G, torch, dev, w, h, steps):
     for name in ("fp32", "tf32", "bf16", "bf16x3"):
         pr = G.PRECISIONS[name]
         G.prepare(h, w.r, pr)
+        tune = G.autotune(h, w.r, pr, None, stream) if name != "fp32" and tuning else None
         for _ in range(2):
             G.evaluate(h, W, U, pr, stream)
         G.synchronize(h, stream)
@@ -335,6 +343,9 @@ def precision_bench(G, torch, dev, w, h, steps):
         G.synchronize(h, stream)
         ms = a.elapsed_time(b) / nst
         ent = {"ms": ms, "value": w.n * w.r / (ms / 1e3), "tflops": flops / (ms / 1e3) / 1e12}
+        if tune is not None:
+            ent["config"] = {k: tune[k] for k in ("piece", "schedule", "order")}
+            ent["tune_ms"] = [round(c["ms"], 4) for c in tune["candidates"]]
         if g is not None:
             got = U[torch.from_numpy(g["rows"]).to(dev)][:, : g["u_oracle"].shape[1]].double().cpu().numpy()
             ent["eps2_vs_oracle_fp64"] = float(np.linalg.norm(got - g["u_oracle"]) / np.linalg.norm(g["u_oracle"]))
@@ -473,6 +484,11 @@ def native_arm(args):
     W = torch.from_numpy(Wn).to(dev)
     U = torch.empty_like(W)
     stream = torch.cuda.current_stream(dev)
+    # tensor-core launch configuration picked by the library's autotuner
+    # (outside the timed region, like compression)
+    tune = None
+    if prec_name in ("tf32", "bf16", "bf16x3") and not args.no_tune:
+        tune = G.autotune(h, r, prec, None, stream)
 
     def barrier():
         if world > 1:
@@ -580,8 +596,9 @@ def native_arm(args):
     flops_all = r * (st["flops_n2s"] + st["flops_s2s"] + st["flops_s2n"] + st["flops_l2l"])
     if prec_name in ("fp32", "fp64"):
         flops, launch_ms = r * st["flops_s2s"], st_ms["s2s"]
-    else:
-        flops, launch_ms = flops_all, prod_ms["upward"]
+    else:  # every GEMM launch of the production path (one launch when fused)
+        flops = flops_all
+        launch_ms = prod_ms["upward"] + prod_ms["s2s"] + prod_ms["s2n"] + prod_ms["leaf"]
     achieved = flops / (launch_ms / 1e3) / 1e12
     gemm_ms = st_ms["upward"] + st_ms["s2s"] + st_ms["s2n"] + st_ms["leaf"]
     if prec_name in ("fp32", "fp64"):
@@ -595,21 +612,30 @@ def native_arm(args):
         bound, peak_src = "tensor", (f"of measured bf16 burst ({bf16:.0f} TFLOP/s) x nominal ratio "
                                      f"{NOMINAL_RATIO[prec_name]:.3f} for {prec_name}")
     traffic = None
+    tr = {}
     if os.path.exists(TRAFFIC_PATH):
-        tr = {}
         for line in open(TRAFFIC_PATH):
             if "=" in line and not line.startswith("#"):
                 k, v = line.split("=", 1)
                 tr[k.strip()] = v.strip()
         src = os.path.join(ROOT, "paper_1707_00164_b300", "csrc", tr.get("source", "-"))
         if tr.get("precision") == prec_name and os.path.exists(src) and \
-                hashlib.sha256(open(src, "rb").read()).hexdigest() == tr.get("sha256"):
+                hashlib.sha256(open(src, "rb").read()).hexdigest() == tr.get("sha256") and \
+                tr.get("workload") == w.name:
             traffic = float(tr["dram_bytes_per_launch"])  # null once the kernel source changed
+
+    def traffic_matches_config(t):
+        cfg = f"{t['piece']}/{['fused', 'staged'][t['schedule']]}/{['critical', 'local'][t['order']]}"
+        return tr.get("config") == cfg
     if prec_name in ("fp32", "fp64"):
         kdesc = "gemm_simt_kernel, S2S launch (every far pair of every level)"
-    else:
+    elif tune is None or tune["schedule"] == G.SCHED_FUSED:
         kdesc = (f"tc_gemm_kernel<{prec_name}>: one dependency-driven persistent launch per evaluation "
                  f"(all N2S, S2S, S2N and L2L tiles)")
+    else:
+        kdesc = f"tc_gemm_kernel<{prec_name}>: every launch of the staged schedule (N2S, S2S, S2N, L2L)"
+    if tune is not None:
+        traffic = traffic if traffic_matches_config(tune) else None
     roofline = {"kernel": kdesc, "bound": bound,
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": peak_src, "traffic": traffic, "flops_per_launch": flops,
@@ -625,14 +651,15 @@ def native_arm(args):
     batching = serving = precision = None
     if "precision" in extra:
         try:
-            precision = precision_bench(G, torch, dev, *extra["precision"], steps=args.steps)
+            precision = precision_bench(G, torch, dev, *extra["precision"], steps=args.steps,
+                                        tuning=not args.no_tune)
         except Exception as e:
             precision = {"error": repr(e)[:300]}
         extra.pop("precision")
     if "batch" in extra:
         try:
             batching = batching_bench(G, torch, dev, *extra["batch"], steps=max(3, min(args.steps, 10)),
-                                      warmup=args.warmup)
+                                      warmup=args.warmup, tuning=not args.no_tune)
         except Exception as e:
             batching = {"error": repr(e)[:300]}
         extra.pop("batch")
@@ -657,7 +684,7 @@ def native_arm(args):
             "data": "synthetic: seeded 6-D standard-normal points, Gaussian kernel; seeded N(0,1) W",
             "config": config_dict(w, prec_name), "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches * args.steps,
-            "accuracy": acc, "modes": modes, "dense_cublas": dense, "precision_workload": precision, "batching": batching,
+            "autotune": tune, "accuracy": acc, "modes": modes, "dense_cublas": dense, "precision_workload": precision, "batching": batching,
             "serving": serving,
             "compress_seconds": round(compress_s, 2),
             "structure": {k: st[k] for k in ("depth", "mean_rank", "max_rank", "near_pairs", "far_pairs",

@@ -67,6 +67,14 @@ extern "C" {
 #define GOFMM_PREC_BF16 3   /* ... on BF16 tensor cores, FP32 accumulate        */
 #define GOFMM_PREC_BF16X3 4 /* ... split BF16 (hi*hi + hi*lo + lo*hi), FP32 acc */
 
+/* ---- tensor-core launch configuration (gofmm_set_tc_config, autotuner) --- */
+#define GOFMM_SCHED_FUSED 0    /* every grouped GEMM of an evaluation in one
+                                  dependency-driven persistent launch        */
+#define GOFMM_SCHED_STAGED 1   /* one persistent launch per stage            */
+#define GOFMM_ORDER_CRITICAL 0 /* fused tiles: longest dependent chain first */
+#define GOFMM_ORDER_LOCAL 1    /* fused tiles: topological, (stage, level)
+                                  groups by critical path, heap order inside */
+
 /*
  * Entry callback: fill out[i*nJ + j] = K(I[i], J[j]) for 0 <= i < nI,
  * 0 <= j < nJ (row-major, FP64) and return 0.  Any nonzero return aborts the
@@ -343,10 +351,11 @@ int gofmm_stats(const gofmm_handle* h, gofmm_stats_t* s);
 /*
  * Stage timing.  enable = 1: gofmm_evaluate runs one launch per stage and
  * records CUDA events on its stream around each stage (a diagnostic
- * breakdown).  enable = 2: the production path (for the tensor-core
- * precisions every grouped GEMM in one dependency-driven launch) with events
- * around the gather and the GEMM launch; its time is reported as stage 1 and
- * stages 2-4 read zero.  enable = 0: off (repeated calls may replay a CUDA
+ * breakdown).  enable = 2: the production path with events: under the
+ * fused schedule of the tensor-core precisions (the default) every grouped
+ * GEMM is one dependency-driven launch, whose time is reported as stage 1
+ * with stages 2-4 reading zero; under the staged schedule (and on the CUDA
+ * cores) the stages are timed one by one.  enable = 0: off (repeated calls may replay a CUDA
  * graph).  gofmm_stage_times then synchronises on the last
  * event and fills ms[0..5] with the milliseconds of the last call's stages
  * (0 gather of W into tree order, 1 N2S upward pass, 2 S2S (one launch),
@@ -370,6 +379,67 @@ int gofmm_stage_times(gofmm_handle* h, float* ms, int n);
  * A negative return is an error code (unknown `what`, NULL handle).
  */
 int64_t gofmm_view(const gofmm_handle* h, int what, void* out);
+
+/*
+ * Tensor-core launch configuration of one tensor-core precision (TF32, BF16,
+ * BF16X3) of a handle.  The paper has no counterpart (its GPU tasks were
+ * grouped by hand, §2.3); it is an interface of this library.  Every
+ * configuration computes bitwise the same U: a task's summation order does
+ * not depend on how tasks are cut or ordered.
+ *   piece    : 128 or 256, the tallest task piece (the MMA N ceiling); taller
+ *              blocks are cut into pieces.  128 halves the block tile held
+ *              in shared memory, which deepens the copy pipeline (3 stages
+ *              instead of 2 in BF16X3, 6 instead of 4 otherwise) at the cost
+ *              of reading each right-hand-side tile once per piece.
+ *   schedule : GOFMM_SCHED_*.
+ *   order    : GOFMM_ORDER_* (tile order of the fused launch).
+ * A new `piece` rebuilds the precision's plan if one exists (synchronises
+ * the device); batches made from the handle before that refuse to run
+ * (ERR_ARG), and the call fails with ERR_ARG while a serving engine holds
+ * requests of the handle.  Default: 256, FUSED, CRITICAL.  Errors: ERR_ARG.
+ */
+int gofmm_set_tc_config(gofmm_handle* h, int precision, int piece, int schedule, int order);
+int gofmm_get_tc_config(const gofmm_handle* h, int precision, int* piece, int* schedule, int* order);
+
+typedef struct {
+    int piece, schedule, order; /* the configuration chosen and applied        */
+    int from_cache;             /* 1: taken from the cache file, none measured */
+    int n_candidates;           /* candidates measured by this call            */
+    int cand_piece[8], cand_schedule[8], cand_order[8];
+    float cand_ms[8];           /* median ms of one evaluation (one batch call) */
+    char key[32];               /* signature: structure(s), r, precision, GPU  */
+} gofmm_tune_t;
+
+/*
+ * Autotuner.  Times gofmm_evaluate of h with r right-hand sides in a
+ * tensor-core precision under each candidate configuration (piece 256 and
+ * 128, each with the fused launch in CRITICAL and LOCAL order and with the
+ * STAGED schedule; 3 warm-up and 7 timed calls each, CUDA events on
+ * `stream`, on scratch W = 0 and U the library allocates), applies the
+ * fastest with gofmm_set_tc_config and reports all of them in *out.
+ * cache_path (may be NULL): a JSON file of earlier choices.  If it holds
+ * an entry for the same key (the structure's signature, ceil(r/128),
+ * precision, GPU name and SM count), that choice is applied without
+ * measuring (from_cache = 1; this needs no GPU); otherwise the new choice
+ * is added to the file (written to a temporary file, then renamed).
+ * A file that is not such a cache is an error and is left alone.
+ * Errors: ERR_ARG (bad precision or r, unreadable/unwritable cache),
+ * ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT.
+ */
+int gofmm_autotune(gofmm_handle* h, int64_t r, int precision, const char* cache_path, void* stream,
+                   gofmm_tune_t* out);
+
+/*
+ * The same for a static batch (gofmm_batch_create): the candidates are
+ * piece 256 and 128 applied to every handle; each is timed as a whole
+ * batch call.  Create the batch after tuning.
+ */
+int gofmm_autotune_batch(gofmm_handle* const* hs, const int64_t* r, int count, int precision,
+                         const char* cache_path, void* stream, gofmm_tune_t* out);
+
+/* The cache key gofmm_autotune (count = 1) or gofmm_autotune_batch would
+ * use, written to key (32 bytes, NUL-terminated).  Needs no GPU. */
+int gofmm_autotune_key(gofmm_handle* const* hs, const int64_t* r, int count, int precision, char* key);
 
 /* Description of the last error on this thread ("" if none). */
 const char* gofmm_last_error(void);

@@ -301,6 +301,77 @@ int gofmm_debug_stall_next(gofmm_handle* h, int precision) {
     });
 }
 
+int gofmm_set_tc_config(gofmm_handle* h, int precision, int piece, int schedule, int order) {
+    return guarded([&] {
+        if (!h) gofmm::fail(GOFMM_ERR_ARG, "handle is NULL");
+        gofmm::device_set_tc_config(h->h, precision, piece, schedule, order);
+    });
+}
+
+int gofmm_get_tc_config(const gofmm_handle* h, int precision, int* piece, int* schedule, int* order) {
+    return guarded([&] {
+        if (!h) gofmm::fail(GOFMM_ERR_ARG, "handle is NULL");
+        if (precision != GOFMM_PREC_TF32 && precision != GOFMM_PREC_BF16 && precision != GOFMM_PREC_BF16X3)
+            gofmm::fail(GOFMM_ERR_ARG, "the launch configuration belongs to a tensor-core precision");
+        const int mode = precision == GOFMM_PREC_TF32 ? 0 : precision == GOFMM_PREC_BF16 ? 1 : 2;
+        if (piece) *piece = h->h.tc_piece[mode];
+        if (schedule) *schedule = h->h.tc_schedule[mode];
+        if (order) *order = h->h.tc_order[mode];
+    });
+}
+
+namespace {
+void fill_tune(const gofmm::TuneResult& t, gofmm_tune_t* out) {
+    if (!out) return;
+    std::memset(out, 0, sizeof *out);
+    out->piece = t.piece;
+    out->schedule = t.schedule;
+    out->order = t.order;
+    out->from_cache = t.from_cache;
+    out->n_candidates = t.n;
+    for (int k = 0; k < t.n && k < 8; ++k) {
+        out->cand_piece[k] = t.cand_piece[k];
+        out->cand_schedule[k] = t.cand_schedule[k];
+        out->cand_order[k] = t.cand_order[k];
+        out->cand_ms[k] = t.cand_ms[k];
+    }
+    std::snprintf(out->key, sizeof out->key, "%s", t.key.c_str());
+}
+}  // namespace
+
+int gofmm_autotune(gofmm_handle* h, int64_t r, int precision, const char* cache_path, void* stream,
+                   gofmm_tune_t* out) {
+    return guarded([&] {
+        if (!h) gofmm::fail(GOFMM_ERR_ARG, "handle is NULL");
+        fill_tune(gofmm::autotune(h->h, r, precision, cache_path, stream), out);
+    });
+}
+
+int gofmm_autotune_batch(gofmm_handle* const* hs, const int64_t* r, int count, int precision,
+                         const char* cache_path, void* stream, gofmm_tune_t* out) {
+    return guarded([&] {
+        if (!hs || !r || count < 1) gofmm::fail(GOFMM_ERR_ARG, "need count >= 1 handles and r values");
+        std::vector<gofmm::Handle*> v;
+        for (int i = 0; i < count; ++i) {
+            if (!hs[i]) gofmm::fail(GOFMM_ERR_ARG, "NULL handle");
+            v.push_back(&hs[i]->h);
+        }
+        fill_tune(gofmm::autotune_batch(v.data(), r, count, precision, cache_path, stream), out);
+    });
+}
+
+int gofmm_autotune_key(gofmm_handle* const* hs, const int64_t* r, int count, int precision, char* key) {
+    return guarded([&] {
+        if (!hs || !r || count < 1 || !key) gofmm::fail(GOFMM_ERR_ARG, "need handles, r values and a key buffer");
+        std::vector<gofmm::Handle*> v;
+        for (int i = 0; i < count; ++i) {
+            if (!hs[i]) gofmm::fail(GOFMM_ERR_ARG, "NULL handle");
+            v.push_back(&hs[i]->h);
+        }
+        std::snprintf(key, 32, "%s", gofmm::tune_key_batch(v.data(), r, count, precision).c_str());
+    });
+}
+
 int gofmm_trim(gofmm_handle* h) {
     return guarded([&] {
         if (!h) gofmm::fail(GOFMM_ERR_ARG, "handle is NULL");

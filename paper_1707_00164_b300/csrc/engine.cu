@@ -131,6 +131,7 @@ void retire(Engine& E) {
         if (e != cudaSuccess) fail(GOFMM_ERR_CUDA, std::string("engine event: ") + cudaGetErrorString(e));
         pool_free(E, q->ws_off, q->ws_bytes);
         cudaEventDestroy(q->done_ev);
+        --q->H->inflight;
         E.state[q->id] = 2;
         ++E.completed;
         delete q;
@@ -187,6 +188,7 @@ int64_t engine_submit(Engine& E, Handle& H, const float* W, int64_t ldw, float* 
     if (q->ws_bytes > E.pool_bytes)
         fail(GOFMM_ERR_NOMEM, "request needs " + std::to_string(q->ws_bytes) + " bytes of workspace; the pool has " +
                                   std::to_string(E.pool_bytes));
+    ++H.inflight;  // the plan may not be rebuilt until the request retires
     E.state[q->id] = 0;
     E.queue.push_back(q.release());
     return E.queue.back()->id;
@@ -233,6 +235,7 @@ int64_t engine_step(Engine& E, cudaStream_t s) {
         TcParams p{};
         p.nsegs = int(nb);
         p.err = E.d_err;
+        int piece = 0;
         struct W8 {
             int64_t w;
             TcTile t;
@@ -242,6 +245,7 @@ int64_t engine_step(Engine& E, cudaStream_t s) {
             EngineRequest* q = gemm[b0 + k];
             const TcLaunch& l = q->T->launches[q->next - 1];
             p.segs[k] = make_seg(*q->T, l, q->rt_hi, q->rt_lo, q->U, q->ldu, q->H->dev->d_idx, q->r);
+            piece = std::max(piece, q->T->piece);
             for (size_t t = 0; t < l.tasks.size(); ++t) {
                 const int64_t w = int64_t(l.tasks[t].nchunks) * l.tasks[t].n_pad + 1;
                 for (int rt = 0; rt < q->n_rtiles; ++rt) tiles.push_back(W8{w, TcTile{int32_t(k), int32_t(t), rt, 0}});
@@ -264,7 +268,7 @@ int64_t engine_step(Engine& E, cudaStream_t s) {
                                 cudaMemcpyHostToDevice, s));
         p.tiles = E.d_tiles[slot];
         p.ntiles = int(tiles.size());
-        launch_gemm_mode(E.mode, p, E.num_sms, s);
+        launch_gemm_mode(E.mode, piece, p, E.num_sms, s);
         CUDA_OK(cudaEventRecord(E.ring_ev[slot], s));
         E.ring_used[slot] = true;
         ++E.launches;
@@ -340,10 +344,17 @@ void engine_destroy(Engine* E) {
     cudaGetDevice(&old);
     cudaSetDevice(E->device);
     cudaDeviceSynchronize();
-    for (EngineRequest* q : E->queue) delete q;
-    for (EngineRequest* q : E->active) delete q;
+    for (EngineRequest* q : E->queue) {
+        --q->H->inflight;
+        delete q;
+    }
+    for (EngineRequest* q : E->active) {
+        --q->H->inflight;
+        delete q;
+    }
     for (EngineRequest* q : E->finishing) {
         if (q->done_ev) cudaEventDestroy(q->done_ev);
+        --q->H->inflight;
         delete q;
     }
     for (int i = 0; i < Engine::kRing; ++i) {
@@ -370,6 +381,7 @@ namespace gofmm {
 struct BatchItem {
     Handle* H;
     TcPrec* T;
+    int64_t epoch;  // the handle's plan epoch when the batch was made
     int r, n_rtiles;
     uint8_t* rt_hi[3];
     uint8_t* rt_lo[3];
@@ -381,6 +393,7 @@ struct BatchStep {
         std::vector<std::pair<int, int>> segs;  // (item, plan launch) per segment
         TcTile* d_tiles = nullptr;
         int ntiles = 0;
+        int piece = 0;  // tallest task piece of the segments' plans
     };
     std::vector<Launch> launches;
 };
@@ -418,6 +431,7 @@ Batch* batch_create(Handle* const* hs, const int64_t* r, int count, int precisio
         BatchItem it{};
         it.H = &H;
         it.T = H.dev->tc->prec[B->mode];
+        it.epoch = H.plan_epoch;
         it.r = int(r[i]);
         it.n_rtiles = int((r[i] + 127) / 128);
         B->items.push_back(it);
@@ -457,6 +471,7 @@ Batch* batch_create(Handle* const* hs, const int64_t* r, int count, int precisio
                 const int i = gemm[b0 + k];
                 const TcLaunch& l = B->items[i].T->launches[next[i] - 1];
                 bl.segs.emplace_back(i, next[i] - 1);
+                bl.piece = std::max(bl.piece, B->items[i].T->piece);
                 for (size_t t = 0; t < l.tasks.size(); ++t) {
                     const int64_t w = int64_t(l.tasks[t].nchunks) * l.tasks[t].n_pad + 1;
                     for (int rt = 0; rt < B->items[i].n_rtiles; ++rt)
@@ -505,7 +520,7 @@ static void batch_launch(Batch& B, const float* const* W, const int64_t* ldw, fl
                 p.segs[k] = make_seg(*it.T, it.T->launches[bl.segs[k].second], it.rt_hi, it.rt_lo, U[i], ldu[i],
                                      it.H->dev->d_idx, it.r);
             }
-            launch_gemm_mode(B.mode, p, B.num_sms, s);
+            launch_gemm_mode(B.mode, bl.piece, p, B.num_sms, s);
         }
     }
     CUDA_OK(cudaMemcpyAsync(B.h_err, B.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -518,6 +533,9 @@ int batch_evaluate(Batch& B, const float* const* W, const int64_t* ldw, float* c
         fail(GOFMM_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait (code " + std::to_string(*B.h_err) + ")");
     std::vector<const void*> key;
     for (size_t i = 0; i < B.items.size(); ++i) {
+        if (B.items[i].H->plan_epoch != B.items[i].epoch)
+            fail(GOFMM_ERR_ARG, "the plan of batch item " + std::to_string(i) +
+                                    " was rebuilt after the batch was created: create the batch again");
         if (!W[i] || !U[i] || ldw[i] < B.items[i].r || ldu[i] < B.items[i].r)
             fail(GOFMM_ERR_ARG, "bad W/U of batch item " + std::to_string(i));
         key.push_back(W[i]);

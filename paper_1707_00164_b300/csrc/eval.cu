@@ -26,6 +26,7 @@
 
 #include "eval_plan.hpp"
 #include "eval_state.hpp"
+#include "eval_tc.hpp"
 
 namespace gofmm {
 
@@ -759,6 +760,40 @@ void device_synchronize(Handle& H, void* stream) {
         tc_clear_error(*H.dev);  // reported once; the handle stays usable
         fail(GOFMM_ERR_TIMEOUT, "a tensor-core kernel gave up a bounded wait (code " + std::to_string(e) + ")");
     }
+}
+
+void device_set_tc_config(Handle& H, int precision, int piece, int schedule, int order) {
+    if (precision != GOFMM_PREC_TF32 && precision != GOFMM_PREC_BF16 && precision != GOFMM_PREC_BF16X3)
+        fail(GOFMM_ERR_ARG, "the launch configuration belongs to a tensor-core precision (TF32, BF16, BF16X3)");
+    if (piece != 128 && piece != 256) fail(GOFMM_ERR_ARG, "piece must be 128 or 256");
+    if (schedule != GOFMM_SCHED_FUSED && schedule != GOFMM_SCHED_STAGED) fail(GOFMM_ERR_ARG, "unknown schedule");
+    if (order != GOFMM_ORDER_CRITICAL && order != GOFMM_ORDER_LOCAL) fail(GOFMM_ERR_ARG, "unknown order");
+    const int mode = mode_of(precision);
+    if (piece != H.tc_piece[mode] && H.inflight > 0)
+        fail(GOFMM_ERR_ARG, "a serving engine holds requests of this handle: drain it before changing the plan");
+    const bool replan = piece != H.tc_piece[mode] && H.dev && H.dev->tc && H.dev->tc->prec[mode];
+    H.tc_schedule[mode] = schedule;
+    H.tc_order[mode] = order;
+    if (!H.dev) {
+        H.tc_piece[mode] = piece;
+        return;
+    }
+    DeviceGuard g(H.st.prm.device);
+    clear_graphs(*H.dev);  // captured launches carry the old configuration
+    if (!replan) {
+        H.tc_piece[mode] = piece;
+        if (H.dev->tc && H.dev->tc->prec[mode]) {
+            // tile lists of the order now selected
+            const int64_t r_cap = H.dev->tc->prec[mode]->r_cap;
+            if (r_cap > 0) tc_prepare(H, *H.dev, r_cap, precision);
+        }
+        return;
+    }
+    const int64_t r_cap = H.dev->tc->prec[mode]->r_cap;
+    tc_drop_plan(*H.dev, precision);
+    H.tc_piece[mode] = piece;
+    ++H.plan_epoch;
+    device_prepare(H, std::max<int64_t>(r_cap, 1), precision);
 }
 
 void device_stall_next(Handle& H, int precision) {

@@ -34,6 +34,8 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <set>
+#include <tuple>
 
 #include "eval_tc.hpp"
 
@@ -48,14 +50,21 @@ namespace {
 constexpr long long kSpinLimit = 2000000000LL;  // clock cycles (about a second) before a wait gives up
 constexpr int kErrProducer = 1, kErrMma = 2, kErrEpilogue = 3, kErrDependency = 4;
 
-template <int MODE>
+// NMAX: the tallest task piece the kernel accepts (MMA N ceiling, 128 or
+// 256).  A stage holds one 128 x 128 B tile of right-hand sides and one
+// NMAX x 128 B block tile (twice for split BF16x3); as many stages as fit in
+// about 200 KB of shared memory, so a lower ceiling buys a deeper pipeline.
+template <int MODE, int NMAX = kMaxN>
 struct Cfg {
     static constexpr bool kSplit = MODE == TC_BF16X3;
-    static constexpr int kStages = kSplit ? 2 : 4;
-    static constexpr int kStageBytes = (kSplit ? 2 : 1) * (kTileBytes + kMaxN * 128);
+    static constexpr int kStageBytes = (kSplit ? 2 : 1) * (kTileBytes + NMAX * 128);
+    static constexpr int kStages = (200 * 1024 / kStageBytes) < 8 ? (200 * 1024 / kStageBytes) : 8;
     static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;  // + alignment slack, barriers
     static constexpr int kKc = MODE == TC_TF32 ? 32 : 64;
     static constexpr int kEs = MODE == TC_TF32 ? 4 : 2;
+    static constexpr int kTmemCols = 2 * NMAX;  // two accumulators
+    static_assert(kStages >= 2, "at least a double-buffered stage ring");
+    static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -184,9 +193,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // ring runs on across tiles and the accumulator is double-buffered in TMEM
 // (2 x 256 columns), so the epilogue of one tile overlaps the MMAs of the
 // next.
-template <int MODE>
+template <int MODE, int NMAX>
 __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
-    using C = Cfg<MODE>;
+    using C = Cfg<MODE, NMAX>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + C::kStages * C::kStageBytes);
@@ -202,7 +211,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
     auto idempty_bar = [&](int a) { return smem_u32(&bars[2 * C::kStages + 7 + a]); };
     const bool dyn = p.dep_off != nullptr;  // dynamic tile order (dependency mode)
     // stage s: A_hi | B_hi | (A_lo | B_lo)
-    auto sA = [&](int s, int lo) { return s_base + s * C::kStageBytes + lo * (kTileBytes + kMaxN * 128); };
+    auto sA = [&](int s, int lo) { return s_base + s * C::kStageBytes + lo * (kTileBytes + NMAX * 128); };
     auto sB = [&](int s, int lo) { return sA(s, lo) + kTileBytes; };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -226,7 +235,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(512)
+                     "r"(C::kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -317,7 +326,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
                 const int acc = i & 1;
                 if (!mbar_wait(tempty_bar(acc), uint32_t(((i >> 1) & 1) ^ 1), p.err, kErrMma)) break;
                 tc_fence_after();
-                const uint32_t tacc = tmem + uint32_t(acc * 256);
+                const uint32_t tacc = tmem + uint32_t(acc * NMAX);
                 const uint32_t idesc = make_idesc(MODE == TC_TF32 ? 2 : 1, tk.n_pad);
                 for (int q = 0; q < tk.nchunks; ++q) {
                     if (!mbar_wait(full_bar(stage), phase, p.err, kErrMma)) { ok = false; break; }
@@ -371,7 +380,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
             ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
             if (!ok) break;
             tc_fence_after();
-            const uint32_t taddr = tmem + uint32_t(acc * 256) + (uint32_t(q4 * 32) << 16);
+            const uint32_t taddr = tmem + uint32_t(acc * NMAX) + (uint32_t(q4 * 32) << 16);
             // RT outputs write the whole output segment of the task (zeros in the
             // padding columns and in rows j >= r), so every RT element a later
             // stage reads was written earlier in the same evaluation; only the
@@ -476,7 +485,8 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::kTmemCols)
+                     : "memory");
     }
 }
 
@@ -575,6 +585,8 @@ static void build_fused(const Structure& st, TcPrec& T) {
     std::vector<int32_t> dep_off{0}, deps, sig;
     std::vector<int> depth;
     std::vector<int64_t> work;
+    std::vector<std::pair<int, int>> group;  // (stage, tree level) of every task
+    std::vector<int64_t> node_of;
     F.tasks.clear();
     F.slabs.clear();
     for (const TcLaunch& l : T.launches)
@@ -620,6 +632,12 @@ static void build_fused(const Structure& st, TcPrec& T) {
             if (s0 >= 0) cdepth[s0] = std::max(cdepth[s0], dp + 1);
             if (s1 >= 0) cdepth[s1] = std::max(cdepth[s1], dp + 1);
             work.push_back(int64_t(t.nchunks) * t.n_pad);
+            {
+                int lev = 0;
+                for (int64_t x = h + 1; x > 1; x >>= 1) ++lev;
+                group.emplace_back(l.stage, lev);
+                node_of.push_back(h);
+            }
             F.tasks.push_back(t);
         }
     // priority: the longest chain of dependent work from a task to the end of
@@ -643,6 +661,51 @@ static void build_fused(const Structure& st, TcPrec& T) {
     for (size_t i = 0; i < nt; ++i) F.order[i] = int32_t(i);
     std::stable_sort(F.order.begin(), F.order.end(), [&](int32_t a, int32_t b) { return tail[a] > tail[b]; });
     (void)depth;
+
+    // Locality order: a topological order (Kahn) that takes, among the ready
+    // tasks, those of the (stage, tree level) group with the longest critical
+    // path first and, inside a group, in heap order.  Neighbouring nodes share
+    // most of their far (and near) lists, so consecutive tiles read the same
+    // skeleton weights and the reads hit L2 instead of HBM.
+    {
+        std::vector<std::vector<int32_t>> producers(size_t(F.ncounters));
+        for (size_t t = 0; t < nt; ++t)
+            for (int i = 0; i < 2; ++i)
+                if (sig[2 * t + i] >= 0) producers[size_t(sig[2 * t + i])].push_back(int32_t(t));
+        std::map<std::pair<int, int>, int64_t> gmax;  // (stage, level) -> longest tail
+        for (size_t t = 0; t < nt; ++t) {
+            int64_t& g = gmax[group[t]];
+            g = std::max(g, tail[t]);
+        }
+        std::vector<std::vector<int32_t>> succ(nt);
+        std::vector<int32_t> indeg(nt, 0);
+        for (size_t t = 0; t < nt; ++t) {
+            std::vector<int32_t> pre;
+            for (int32_t d = dep_off[t]; d < dep_off[t + 1]; ++d)
+                for (int32_t u : producers[size_t(deps[2 * d])]) pre.push_back(u);
+            std::sort(pre.begin(), pre.end());
+            pre.erase(std::unique(pre.begin(), pre.end()), pre.end());
+            for (int32_t u : pre) succ[size_t(u)].push_back(int32_t(t));
+            indeg[t] = int32_t(pre.size());
+        }
+        // ready set ordered by (group's longest tail desc, stage, level, node, task)
+        auto key = [&](int32_t t) {
+            return std::make_tuple(-gmax[group[size_t(t)]], group[size_t(t)].first, group[size_t(t)].second,
+                                   node_of[size_t(t)], t);
+        };
+        std::set<std::tuple<int64_t, int, int, int64_t, int32_t>> ready;
+        for (size_t t = 0; t < nt; ++t)
+            if (indeg[t] == 0) ready.insert(key(int32_t(t)));
+        F.order_local.clear();
+        while (!ready.empty()) {
+            const int32_t t = std::get<4>(*ready.begin());
+            ready.erase(ready.begin());
+            F.order_local.push_back(t);
+            for (int32_t u : succ[size_t(t)])
+                if (--indeg[size_t(u)] == 0) ready.insert(key(u));
+        }
+        if (F.order_local.size() != nt) fail(GOFMM_ERR_ARG, "dependency cycle in the fused plan");
+    }
     F.d_tasks = dupload(F.tasks);
     F.d_slabs = dupload(F.slabs);
     F.d_dep_off = dupload(dep_off);
@@ -651,20 +714,25 @@ static void build_fused(const Structure& st, TcPrec& T) {
     F.d_sig = dupload(sig);
 }
 
-static std::pair<TcTile*, int> fused_tiles(TcFused& F, int n_rtiles) {
-    auto it = F.tiles.find(n_rtiles);
+// Tile list of the fused launch: tasks in the given order (GOFMM_ORDER_*),
+// the r-tiles of a task adjacent.
+static std::pair<TcTile*, int> fused_tiles(TcFused& F, int n_rtiles, int order) {
+    const int key = n_rtiles * 2 + (order == GOFMM_ORDER_LOCAL ? 1 : 0);
+    auto it = F.tiles.find(key);
     if (it != F.tiles.end()) return it->second;
     std::vector<TcTile> t;
-    for (int32_t k : F.order)
+    for (int32_t k : order == GOFMM_ORDER_LOCAL ? F.order_local : F.order)
         for (int rt = 0; rt < n_rtiles; ++rt) t.push_back(TcTile{0, k, rt, 0});
     auto v = std::make_pair(dupload(t), int(t.size()));
-    F.tiles[n_rtiles] = v;
+    F.tiles[key] = v;
     return v;
 }
 
 static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::vector<TileJob>& jobs) {
     const int64_t nn = st.n_nodes(), nl = st.n_leaves();
     const int kc = T.kc;
+    const int64_t P = T.piece;
+    if (P != 128 && P != 256) fail(GOFMM_ERR_ARG, "task piece height must be 128 or 256");
     auto padk = [&](int64_t x) { return (x + kc - 1) / kc * kc; };
     std::vector<int64_t> leaf_chunk(nl), node_chunk(nn, -1);
     std::map<int64_t, int64_t> leaf_at_pos, node_at_skel;
@@ -702,16 +770,16 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
             const int okind = task_out(t.flags);
             if (okind == OUT_U) out_base = t.out_row;
             else out_base = node_chunk.at(node_at_skel.at(t.out_row));
-            for (int64_t q = 0; q * kMaxN < std::max<int64_t>(t.m, 1); ++q) {
-                const int32_t mq = int32_t(std::min<int64_t>(kMaxN, t.m - q * kMaxN));
+            for (int64_t q = 0; q * P < std::max<int64_t>(t.m, 1); ++q) {
+                const int32_t mq = int32_t(std::min<int64_t>(P, t.m - q * P));
                 TcTask tt{};
-                tt.out_pos = okind == OUT_U ? out_base + q * kMaxN : out_base + q * kMaxN / kc;
+                tt.out_pos = okind == OUT_U ? out_base + q * P : out_base + q * P / kc;
                 tt.m = mq;
                 tt.n_pad = std::max(16, (mq + 15) / 16 * 16);
                 tt.slab0 = int32_t(tl.slabs.size());
                 tt.out_kind = okind;
                 tt.accumulate = task_accumulate(t.flags) ? 1 : 0;
-                tt.out_cols = okind == OUT_U ? tt.n_pad : int32_t(std::min<int64_t>(kMaxN, padk(t.m) - q * kMaxN));
+                tt.out_cols = okind == OUT_U ? tt.n_pad : int32_t(std::min<int64_t>(P, padk(t.m) - q * P));
                 for (int si = t.slab0; si < t.slab1; ++si) {
                     const Slab& s = l.slabs[si];
                     if (s.a_src == A_GEN)
@@ -741,7 +809,7 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
                     ts.nchunks = int32_t(kpad / kc);
                     ts.b_off = bbytes;
                     TileJob jb{};
-                    jb.src_off = s.a_off + q * kMaxN * int64_t(s.lda);
+                    jb.src_off = s.a_off + q * P * int64_t(s.lda);
                     jb.dst_off = bbytes;
                     jb.src_ld = s.lda;
                     jb.m = mq;
@@ -772,7 +840,7 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
     const int64_t chunks[3] = {T.wt_chunks, T.sk_chunks, T.sk_chunks};
     for (const TcLaunch& l : T.launches)
         for (const TcTask& t : l.tasks) {
-            check(t.m >= 1 && t.m <= kMaxN && t.n_pad % 16 == 0 && t.n_pad >= t.m && t.n_pad <= kMaxN, "task shape");
+            check(t.m >= 1 && t.m <= P && t.n_pad % 16 == 0 && t.n_pad >= t.m && t.n_pad <= P, "task shape");
             check(t.slab0 >= 0 && t.slab0 <= t.slab1 && t.slab1 <= int32_t(l.slabs.size()), "task slabs");
             if (t.out_kind == OUT_U)
                 check(t.out_pos >= 0 && t.out_pos + t.m <= st.n, "output rows");
@@ -805,7 +873,10 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
 
 template <int MODE>
 static void set_smem_attr() {
-    CUDA_OK(cudaFuncSetAttribute(tc_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<MODE>::kSmem));
+    CUDA_OK(cudaFuncSetAttribute(tc_gemm_kernel<MODE, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 Cfg<MODE, 256>::kSmem));
+    CUDA_OK(cudaFuncSetAttribute(tc_gemm_kernel<MODE, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 Cfg<MODE, 128>::kSmem));
 }
 
 // Tile list of one launch alone: tasks in plan order (heaviest first), the
@@ -831,6 +902,7 @@ TcPrec& tc_plan(Handle& H, DeviceState& D, int precision) {
         t->kc = mode == TC_TF32 ? 32 : 64;
         t->es = mode == TC_TF32 ? 4 : 2;
         t->split = mode == TC_BF16X3;
+        t->piece = H.tc_piece[mode];
         std::vector<TileJob> jobs;
         build_tc_plan(H.st, D, *t, jobs);
         t->b_hi = dalloc<uint8_t>(size_t(std::max<int64_t>(t->b_bytes, 16)));
@@ -872,7 +944,7 @@ void tc_prepare(Handle& H, DeviceState& D, int64_t r_max, int precision) {
         F.d_counters = dalloc<int>(size_t(F.ncounters) * size_t(r_pad / 128) + 1);  // + tile counter
         F.counters_nrt = int(r_pad / 128);
     }
-    for (int nrt = 1; nrt <= int(r_pad / 128); ++nrt) fused_tiles(F, nrt);
+    for (int nrt = 1; nrt <= int(r_pad / 128); ++nrt) fused_tiles(F, nrt, H.tc_order[T->mode]);
     if (T->r_cap < r_pad) {
         for (int i = 0; i < 3; ++i) {
             dfree(T->rt_hi[i]);
@@ -922,34 +994,53 @@ TcSeg make_seg(const TcPrec& T, const TcLaunch& l, uint8_t* const* rt_hi, uint8_
     return g;
 }
 
-template <int MODE>
+template <int MODE, int NMAX>
 static void launch_gemm(const TcParams& p, int num_sms, cudaStream_t s) {
     const int grid = std::min(p.ntiles, num_sms);
-    tc_gemm_kernel<MODE><<<unsigned(grid), 192, Cfg<MODE>::kSmem, s>>>(p);
+    tc_gemm_kernel<MODE, NMAX><<<unsigned(grid), 192, Cfg<MODE, NMAX>::kSmem, s>>>(p);
     CUDA_OK(cudaGetLastError());
 }
 
 // Cooperative launch: every CTA of the persistent grid is resident at once,
 // so tiles waiting on counters bumped by other CTAs always make progress.
-template <int MODE>
+template <int MODE, int NMAX>
 static void launch_gemm_coop(const TcParams& p, int num_sms, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(std::min(p.ntiles, num_sms)));
     cfg.blockDim = dim3(192);
-    cfg.dynamicSmemBytes = Cfg<MODE>::kSmem;
+    cfg.dynamicSmemBytes = Cfg<MODE, NMAX>::kSmem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    CUDA_OK(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<MODE>, p));
+    CUDA_OK(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<MODE, NMAX>, p));
 }
 
-void launch_gemm_mode(int mode, const TcParams& p, int num_sms, cudaStream_t s) {
-    if (mode == TC_TF32) launch_gemm<TC_TF32>(p, num_sms, s);
-    else if (mode == TC_BF16) launch_gemm<TC_BF16>(p, num_sms, s);
-    else launch_gemm<TC_BF16X3>(p, num_sms, s);
+// piece: the tallest task piece among the launch's segments (128 or 256)
+void launch_gemm_mode(int mode, int piece, const TcParams& p, int num_sms, cudaStream_t s) {
+    if (piece <= 128) {
+        if (mode == TC_TF32) launch_gemm<TC_TF32, 128>(p, num_sms, s);
+        else if (mode == TC_BF16) launch_gemm<TC_BF16, 128>(p, num_sms, s);
+        else launch_gemm<TC_BF16X3, 128>(p, num_sms, s);
+    } else {
+        if (mode == TC_TF32) launch_gemm<TC_TF32, 256>(p, num_sms, s);
+        else if (mode == TC_BF16) launch_gemm<TC_BF16, 256>(p, num_sms, s);
+        else launch_gemm<TC_BF16X3, 256>(p, num_sms, s);
+    }
+}
+
+static void launch_gemm_coop_mode(int mode, int piece, const TcParams& p, int num_sms, cudaStream_t s) {
+    if (piece <= 128) {
+        if (mode == TC_TF32) launch_gemm_coop<TC_TF32, 128>(p, num_sms, s);
+        else if (mode == TC_BF16) launch_gemm_coop<TC_BF16, 128>(p, num_sms, s);
+        else launch_gemm_coop<TC_BF16X3, 128>(p, num_sms, s);
+    } else {
+        if (mode == TC_TF32) launch_gemm_coop<TC_TF32, 256>(p, num_sms, s);
+        else if (mode == TC_BF16) launch_gemm_coop<TC_BF16, 256>(p, num_sms, s);
+        else launch_gemm_coop<TC_BF16X3, 256>(p, num_sms, s);
+    }
 }
 
 void launch_gather(int mode, const TcPrec& T, const float* W, int64_t ldw, const int64_t* perm,
@@ -979,8 +1070,8 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
     TcParams p{};
     p.nsegs = 1;
     p.err = T.d_err;
-    if (H.timing == 1) {
-        // one launch per stage (stage timing)
+    if (H.timing == 1 || H.tc_schedule[T.mode] == GOFMM_SCHED_STAGED) {
+        // one launch per stage (stage timing, or the staged schedule)
         D.last_fused = false;
         int stage_done = 1;
         for (TcLaunch& l : T.launches) {
@@ -990,7 +1081,7 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
             p.tiles = tl.first;
             p.ntiles = tl.second;
             p.segs[0] = make_seg(T, l, T.rt_hi, T.rt_lo, U, ldu, D.d_idx, r);
-            launch_gemm_mode(T.mode, p, T.num_sms, s);
+            launch_gemm_mode(T.mode, T.piece, p, T.num_sms, s);
             ++launches;
         }
         while (stage_done < 5) CUDA_OK(cudaEventRecord(D.ev[++stage_done], s));
@@ -1000,7 +1091,7 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
         TcFused& F = T.fused;
         if (F.counters_nrt < n_rtiles) fail(GOFMM_ERR_ARG, "fused plan not prepared for this r");
         CUDA_OK(cudaMemsetAsync(F.d_counters, 0, (size_t(F.ncounters) * n_rtiles + 1) * sizeof(int), s));
-        const auto tl = fused_tiles(F, n_rtiles);
+        const auto tl = fused_tiles(F, n_rtiles, H.tc_order[T.mode]);
         p.tiles = tl.first;
         p.ntiles = tl.second;
         p.dep_off = F.d_dep_off;
@@ -1017,9 +1108,7 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
         g.tasks = F.d_tasks;
         g.slabs = F.d_slabs;
         p.segs[0] = g;
-        if (T.mode == TC_TF32) launch_gemm_coop<TC_TF32>(p, T.num_sms, s);
-        else if (T.mode == TC_BF16) launch_gemm_coop<TC_BF16>(p, T.num_sms, s);
-        else launch_gemm_coop<TC_BF16X3>(p, T.num_sms, s);
+        launch_gemm_coop_mode(T.mode, T.piece, p, T.num_sms, s);
         ++launches;
         if (timing)
             for (int i = 2; i <= 5; ++i) CUDA_OK(cudaEventRecord(D.ev[i], s));
@@ -1065,10 +1154,9 @@ int tc_error(const DeviceState& D) {
     return 0;
 }
 
-void tc_destroy(DeviceState& D) {
-    if (!D.tc) return;
-    for (TcPrec*& T : D.tc->prec) {
-        if (!T) continue;
+static void free_prec(TcPrec*& T) {
+    if (!T) return;
+    {
         for (TcLaunch& l : T->launches) {
             dfree(l.d_tasks);
             dfree(l.d_slabs);
@@ -1087,6 +1175,17 @@ void tc_destroy(DeviceState& D) {
         delete T;
         T = nullptr;
     }
+}
+
+void tc_drop_plan(DeviceState& D, int precision) {
+    if (!D.tc) return;
+    CUDA_OK(cudaDeviceSynchronize());  // no launch may still read the plan
+    free_prec(D.tc->prec[mode_of(precision)]);
+}
+
+void tc_destroy(DeviceState& D) {
+    if (!D.tc) return;
+    for (TcPrec*& T : D.tc->prec) free_prec(T);
     delete D.tc;
     D.tc = nullptr;
 }

@@ -96,7 +96,8 @@ struct TcLaunch {
 struct TcFused {
     std::vector<TcTask> tasks;
     std::vector<TcSlab> slabs;
-    std::vector<int32_t> order;  // tasks in a topological, heaviest-first order
+    std::vector<int32_t> order;        // tasks in a topological, critical-path-first order
+    std::vector<int32_t> order_local;  // topological; groups by critical path, heap order inside
     TcTask* d_tasks = nullptr;
     TcSlab* d_slabs = nullptr;
     int32_t* d_dep_off = nullptr;
@@ -108,11 +109,12 @@ struct TcFused {
     std::vector<int32_t> deps_host;
     int32_t* d_deps_stall = nullptr;  // diagnostic copy with one unreachable arrival count
     bool stall_next = false;
-    std::map<int, std::pair<TcTile*, int>> tiles;  // r-tiles -> ordered tile list
+    std::map<int, std::pair<TcTile*, int>> tiles;  // 2 x r-tiles + order -> ordered tile list
 };
 
 struct TcPrec {
     int mode = 0, kc = 0, es = 0;
+    int piece = kMaxN;  // task piece height: tasks taller than this are split (MMA N ceiling)
     bool split = false;
     std::vector<TcLaunch> launches;
     int64_t wt_chunks = 0, sk_chunks = 0;
@@ -139,7 +141,8 @@ int mode_of(int precision);
 TcPrec& tc_plan(Handle& H, DeviceState& D, int precision);  // plan + B tiles (allocates, synchronises)
 TcSeg make_seg(const TcPrec& T, const TcLaunch& l, uint8_t* const* rt_hi, uint8_t* const* rt_lo, float* U,
                int64_t ldu, const int64_t* perm, int r);
-void launch_gemm_mode(int mode, const TcParams& p, int num_sms, cudaStream_t s);
+void launch_gemm_mode(int mode, int piece, const TcParams& p, int num_sms, cudaStream_t s);
+void tc_drop_plan(DeviceState& D, int precision);  // frees one mode's plan, stores and buffers
 void launch_gather(int mode, const TcPrec& T, const float* W, int64_t ldw, const int64_t* perm, uint8_t* wt_hi,
                    uint8_t* wt_lo, int r, cudaStream_t s);
 

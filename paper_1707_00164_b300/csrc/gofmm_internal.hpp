@@ -135,6 +135,13 @@ struct Handle {
     Entries K;               // generator kinds keep their points; callbacks are dropped
     DeviceState* dev = nullptr;
     int timing = 0;  // 0 off, 1 one launch per stage with stage events, 2 production path with events
+    // tensor-core launch configuration per mode (TF32, BF16, BF16X3), set by
+    // the autotuner or by the caller; read when the mode's plan is built
+    int tc_piece[3] = {256, 256, 256};  // task piece height (MMA N ceiling): 128 or 256
+    int tc_schedule[3] = {0, 0, 0};     // GOFMM_SCHED_FUSED or GOFMM_SCHED_STAGED
+    int tc_order[3] = {0, 0, 0};        // GOFMM_ORDER_CRITICAL or GOFMM_ORDER_LOCAL (fused schedule)
+    int64_t plan_epoch = 0;  // bumped whenever a tensor-core plan is rebuilt (batches check it)
+    int64_t inflight = 0;    // engine requests of this handle not yet retired
 };
 
 // Device side (eval.cu); all throw Error.
@@ -147,6 +154,21 @@ void device_destroy(Handle& H);
 void device_synchronize(Handle& H, void* stream);
 void device_trim(Handle& H);
 void device_stall_next(Handle& H, int precision);
+
+// Tensor-core launch configuration and its autotuner (tune.cu).
+constexpr int kTuneMax = 8;  // candidates of one tuning run
+struct TuneResult {
+    int piece = 256, schedule = 0, order = 0, from_cache = 0, n = 0;
+    int cand_piece[kTuneMax] = {}, cand_schedule[kTuneMax] = {}, cand_order[kTuneMax] = {};
+    float cand_ms[kTuneMax] = {};
+    std::string key;
+};
+void device_set_tc_config(Handle& H, int precision, int piece, int schedule, int order);
+std::string tune_key(const Handle& H, int64_t r, int precision);
+std::string tune_key_batch(Handle* const* hs, const int64_t* r, int count, int precision);
+TuneResult autotune(Handle& H, int64_t r, int precision, const char* cache_path, void* stream);
+TuneResult autotune_batch(Handle* const* hs, const int64_t* r, int count, int precision, const char* cache_path,
+                          void* stream);
 
 // Batching / serving engine (engine.cu).
 struct Engine;

@@ -27,6 +27,8 @@ DTYPE_F64, DTYPE_F32 = 0, 1
 PREC_FP64, PREC_FP32, PREC_TF32, PREC_BF16, PREC_BF16X3 = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "tf32": PREC_TF32, "bf16": PREC_BF16,
               "bf16x3": PREC_BF16X3}
+SCHED_FUSED, SCHED_STAGED = 0, 1
+ORDER_CRITICAL, ORDER_LOCAL = 0, 1
 
 BLOCK_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(C.c_int64), C.c_int64,
                        C.POINTER(C.c_int64), C.c_int64, C.POINTER(C.c_double))
@@ -45,6 +47,12 @@ class ParamsC(C.Structure):
                 ("n_sample", C.c_int), ("ann_max_iter", C.c_int), ("num_threads", C.c_int),
                 ("ann_target_recall", C.c_double), ("knn_exact_max", C.c_int64),
                 ("seed", C.c_uint64), ("device", C.c_int), ("reserved", C.c_int)]
+
+
+class TuneC(C.Structure):
+    _fields_ = [("piece", C.c_int), ("schedule", C.c_int), ("order", C.c_int), ("from_cache", C.c_int),
+                ("n_candidates", C.c_int), ("cand_piece", C.c_int * 8), ("cand_schedule", C.c_int * 8),
+                ("cand_order", C.c_int * 8), ("cand_ms", C.c_float * 8), ("key", C.c_char * 32)]
 
 
 class StatsC(C.Structure):
@@ -98,6 +106,13 @@ def _load():
         "gofmm_set_timing": (C.c_int, [H, C.c_int]),
         "gofmm_stage_times": (C.c_int, [H, C.POINTER(C.c_float), C.c_int]),
         "gofmm_view": (C.c_int64, [H, C.c_int, C.c_void_p]),
+        "gofmm_set_tc_config": (C.c_int, [H, C.c_int, C.c_int, C.c_int, C.c_int]),
+        "gofmm_get_tc_config": (C.c_int, [H, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                          C.POINTER(C.c_int)]),
+        "gofmm_autotune": (C.c_int, [H, C.c_int64, C.c_int, C.c_char_p, C.c_void_p, C.POINTER(TuneC)]),
+        "gofmm_autotune_batch": (C.c_int, [C.POINTER(H), C.POINTER(C.c_int64), C.c_int, C.c_int, C.c_char_p,
+                                           C.c_void_p, C.POINTER(TuneC)]),
+        "gofmm_autotune_key": (C.c_int, [C.POINTER(H), C.POINTER(C.c_int64), C.c_int, C.c_int, C.c_char_p]),
         "gofmm_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -299,6 +314,65 @@ def stats(h: Handle) -> dict:
     s = StatsC()
     _check(LIB.gofmm_stats(h.ptr, C.byref(s)))
     return {name: getattr(s, name) for name, _ in StatsC._fields_}
+
+
+def set_tc_config(h: Handle, precision: int, piece: int = 256, schedule: int = SCHED_FUSED,
+                  order: int = ORDER_CRITICAL):
+    _check(LIB.gofmm_set_tc_config(h.ptr, int(precision), int(piece), int(schedule), int(order)))
+
+
+def get_tc_config(h: Handle, precision: int) -> dict:
+    p, s, o = C.c_int(), C.c_int(), C.c_int()
+    _check(LIB.gofmm_get_tc_config(h.ptr, int(precision), C.byref(p), C.byref(s), C.byref(o)))
+    return dict(piece=p.value, schedule=s.value, order=o.value)
+
+
+def _tune_dict(t: TuneC) -> dict:
+    n = t.n_candidates
+    return dict(piece=t.piece, schedule=t.schedule, order=t.order, from_cache=bool(t.from_cache),
+                key=t.key.decode(),
+                candidates=[dict(piece=t.cand_piece[k], schedule=t.cand_schedule[k], order=t.cand_order[k],
+                                 ms=t.cand_ms[k]) for k in range(n)])
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return C.c_void_p(None)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def autotune(h: Handle, r: int, precision: int, cache_path: Optional[str] = None, stream=None) -> dict:
+    t = TuneC()
+    path = cache_path.encode() if cache_path else None
+    _check(LIB.gofmm_autotune(h.ptr, int(r), int(precision), path, _stream_ptr(stream), C.byref(t)))
+    return _tune_dict(t)
+
+
+def _handle_array(handles):
+    return (C.c_void_p * len(handles))(*[h.ptr.value if isinstance(h.ptr, C.c_void_p) else h.ptr
+                                         for h in handles])
+
+
+def autotune_batch(handles, rs, precision: int, cache_path: Optional[str] = None, stream=None) -> dict:
+    t = TuneC()
+    r = (C.c_int64 * len(handles))(*[int(x) for x in rs])
+    path = cache_path.encode() if cache_path else None
+    _check(LIB.gofmm_autotune_batch(_handle_array(handles), r, len(handles), int(precision), path,
+                                    _stream_ptr(stream), C.byref(t)))
+    return _tune_dict(t)
+
+
+def autotune_key(handles, rs, precision: int) -> str:
+    buf = C.create_string_buffer(32)
+    r = (C.c_int64 * len(handles))(*[int(x) for x in rs])
+    _check(LIB.gofmm_autotune_key(_handle_array(handles), r, len(handles), int(precision), buf))
+    return buf.value.decode()
 
 
 def set_timing(h: Handle, enable: bool):
