@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--no-precision", action="store_true", help="skip the precision workload")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default tensor-core configuration instead of autotuning it")
+    ap.add_argument("--config", default="",
+                    help="force the tensor-core configuration of the main workload, piece/schedule/order "
+                         "(e.g. 128/staged/local); no autotuning")
     ap.add_argument("--n", type=int, default=0,
                     help="profiling only: the same recipe at another N (not a bench line)")
     return ap.parse_args()
@@ -487,7 +490,11 @@ def native_arm(args):
     # tensor-core launch configuration picked by the library's autotuner
     # (outside the timed region, like compression)
     tune = None
-    if prec_name in ("tf32", "bf16", "bf16x3") and not args.no_tune:
+    if prec_name in ("tf32", "bf16", "bf16x3") and args.config:
+        pc, sc, oc = args.config.split("/")
+        G.set_tc_config(h, prec, int(pc), ["fused", "staged"].index(sc), ["critical", "local"].index(oc))
+        tune = dict(G.get_tc_config(h, prec), forced=True, candidates=[])
+    elif prec_name in ("tf32", "bf16", "bf16x3") and not args.no_tune:
         tune = G.autotune(h, r, prec, None, stream)
 
     def barrier():

@@ -71,9 +71,11 @@ extern "C" {
 #define GOFMM_SCHED_FUSED 0    /* every grouped GEMM of an evaluation in one
                                   dependency-driven persistent launch        */
 #define GOFMM_SCHED_STAGED 1   /* one persistent launch per stage            */
-#define GOFMM_ORDER_CRITICAL 0 /* fused tiles: longest dependent chain first */
-#define GOFMM_ORDER_LOCAL 1    /* fused tiles: topological, (stage, level)
-                                  groups by critical path, heap order inside */
+#define GOFMM_ORDER_CRITICAL 0 /* fused launch: longest dependent chain first;
+                                  staged launches: heaviest task first       */
+#define GOFMM_ORDER_LOCAL 1    /* fused: topological, (stage, level) groups by
+                                  critical path, heap order inside; staged:
+                                  heap order                                 */
 
 /*
  * Entry callback: fill out[i*nJ + j] = K(I[i], J[j]) for 0 <= i < nI,
@@ -392,7 +394,7 @@ int64_t gofmm_view(const gofmm_handle* h, int what, void* out);
  *              instead of 2 in BF16X3, 6 instead of 4 otherwise) at the cost
  *              of reading each right-hand-side tile once per piece.
  *   schedule : GOFMM_SCHED_*.
- *   order    : GOFMM_ORDER_* (tile order of the fused launch).
+ *   order    : GOFMM_ORDER_* (tile order inside the launches).
  * A new `piece` rebuilds the precision's plan if one exists (synchronises
  * the device); batches made from the handle before that refuse to run
  * (ERR_ARG), and the call fails with ERR_ARG while a serving engine holds
@@ -413,8 +415,8 @@ typedef struct {
 /*
  * Autotuner.  Times gofmm_evaluate of h with r right-hand sides in a
  * tensor-core precision under each candidate configuration (piece 256 and
- * 128, each with the fused launch in CRITICAL and LOCAL order and with the
- * STAGED schedule; 3 warm-up and 7 timed calls each, CUDA events on
+ * 128, each with the FUSED and the STAGED schedule in CRITICAL and in LOCAL
+ * order: 8 candidates; 3 warm-up and 7 timed calls each, CUDA events on
  * `stream`, on scratch W = 0 and U the library allocates), applies the
  * fastest with gofmm_set_tc_config and reports all of them in *out.
  * cache_path (may be NULL): a JSON file of earlier choices.  If it holds

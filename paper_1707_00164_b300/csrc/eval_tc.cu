@@ -879,16 +879,25 @@ static void set_smem_attr() {
                                  Cfg<MODE, 128>::kSmem));
 }
 
-// Tile list of one launch alone: tasks in plan order (heaviest first), the
-// r-tiles of a task adjacent so they share the task's B tiles through L2.
-static std::pair<TcTile*, int> launch_tiles(TcLaunch& l, int n_rtiles) {
-    auto it = l.tiles.find(n_rtiles);
+// Tile list of one launch alone, the r-tiles of a task adjacent so they
+// share the task's B tiles through L2.  CRITICAL: tasks in plan order
+// (heaviest first, for the tail of the launch); LOCAL: tasks in heap order
+// (tree levels top down, nodes left to right), so that consecutive tasks
+// share most of their far or near lists and re-read operands from L2.
+static std::pair<TcTile*, int> launch_tiles(TcLaunch& l, int n_rtiles, int order) {
+    const int key = n_rtiles * 2 + (order == GOFMM_ORDER_LOCAL ? 1 : 0);
+    auto it = l.tiles.find(key);
     if (it != l.tiles.end()) return it->second;
+    std::vector<int32_t> tasks(l.tasks.size());
+    for (size_t k = 0; k < tasks.size(); ++k) tasks[k] = int32_t(k);
+    if (order == GOFMM_ORDER_LOCAL)
+        std::stable_sort(tasks.begin(), tasks.end(),
+                         [&](int32_t a, int32_t b) { return l.task_node[size_t(a)] < l.task_node[size_t(b)]; });
     std::vector<TcTile> t;
-    for (size_t k = 0; k < l.tasks.size(); ++k)
-        for (int rt = 0; rt < n_rtiles; ++rt) t.push_back(TcTile{0, int32_t(k), rt, 0});
+    for (int32_t k : tasks)
+        for (int rt = 0; rt < n_rtiles; ++rt) t.push_back(TcTile{0, k, rt, 0});
     auto v = std::make_pair(dupload(t), int(t.size()));
-    l.tiles[n_rtiles] = v;
+    l.tiles[key] = v;
     return v;
 }
 
@@ -937,7 +946,7 @@ TcPrec& tc_plan(Handle& H, DeviceState& D, int precision) {
 void tc_prepare(Handle& H, DeviceState& D, int64_t r_max, int precision) {
     TcPrec* T = &tc_plan(H, D, precision);
     const int64_t r_pad = (r_max + 127) / 128 * 128;
-    for (TcLaunch& l : T->launches) launch_tiles(l, int(r_pad / 128));
+    for (TcLaunch& l : T->launches) launch_tiles(l, int(r_pad / 128), H.tc_order[T->mode]);
     TcFused& F = T->fused;
     if (F.counters_nrt < int(r_pad / 128)) {
         dfree(F.d_counters);
@@ -1077,7 +1086,7 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
         for (TcLaunch& l : T.launches) {
             while (stage_done < l.stage) CUDA_OK(cudaEventRecord(D.ev[++stage_done], s));
             if (l.tasks.empty()) continue;
-            const auto tl = launch_tiles(l, n_rtiles);
+            const auto tl = launch_tiles(l, n_rtiles, H.tc_order[T.mode]);
             p.tiles = tl.first;
             p.ntiles = tl.second;
             p.segs[0] = make_seg(T, l, T.rt_hi, T.rt_lo, U, ldu, D.d_idx, r);
