@@ -492,7 +492,7 @@ def native_arm(args):
     tune = None
     if prec_name in ("tf32", "bf16", "bf16x3") and args.config:
         pc, sc, oc = args.config.split("/")
-        G.set_tc_config(h, prec, int(pc), ["fused", "staged"].index(sc), ["critical", "local"].index(oc))
+        G.set_tc_config(h, prec, int(pc), ["fused", "staged", "pair"].index(sc), ["critical", "local"].index(oc))
         tune = dict(G.get_tc_config(h, prec), forced=True, candidates=[])
     elif prec_name in ("tf32", "bf16", "bf16x3") and not args.no_tune:
         tune = G.autotune(h, r, prec, None, stream)
@@ -632,7 +632,7 @@ def native_arm(args):
             traffic = float(tr["dram_bytes_per_launch"])  # null once the kernel source changed
 
     def traffic_matches_config(t):
-        cfg = f"{t['piece']}/{['fused', 'staged'][t['schedule']]}/{['critical', 'local'][t['order']]}"
+        cfg = f"{t['piece']}/{['fused', 'staged', 'pair'][t['schedule']]}/{['critical', 'local'][t['order']]}"
         return tr.get("config") == cfg
     if prec_name in ("fp32", "fp64"):
         kdesc = "gemm_simt_kernel, S2S launch (every far pair of every level)"
@@ -640,7 +640,8 @@ def native_arm(args):
         kdesc = (f"tc_gemm_kernel<{prec_name}>: one dependency-driven persistent launch per evaluation "
                  f"(all N2S, S2S, S2N and L2L tiles)")
     else:
-        kdesc = f"tc_gemm_kernel<{prec_name}>: every launch of the staged schedule (N2S, S2S, S2N, L2L)"
+        kname = "tc_gemm_pair_kernel" if tune["schedule"] == G.SCHED_PAIR else "tc_gemm_kernel"
+        kdesc = f"{kname}<{prec_name}>: every launch of the staged schedule (N2S, S2S, S2N, L2L)"
     if tune is not None:
         traffic = traffic if traffic_matches_config(tune) else None
     roofline = {"kernel": kdesc, "bound": bound,

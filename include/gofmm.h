@@ -71,6 +71,8 @@ extern "C" {
 #define GOFMM_SCHED_FUSED 0    /* every grouped GEMM of an evaluation in one
                                   dependency-driven persistent launch        */
 #define GOFMM_SCHED_STAGED 1   /* one persistent launch per stage            */
+#define GOFMM_SCHED_PAIR 2     /* one launch per stage on SM pairs: M = 256
+                                  MMAs over two r-tiles (tcgen05 cta_group::2) */
 #define GOFMM_ORDER_CRITICAL 0 /* fused launch: longest dependent chain first;
                                   staged launches: heaviest task first       */
 #define GOFMM_ORDER_LOCAL 1    /* fused: topological, (stage, level) groups by
@@ -407,16 +409,16 @@ typedef struct {
     int piece, schedule, order; /* the configuration chosen and applied        */
     int from_cache;             /* 1: taken from the cache file, none measured */
     int n_candidates;           /* candidates measured by this call            */
-    int cand_piece[8], cand_schedule[8], cand_order[8];
-    float cand_ms[8];           /* median ms of one evaluation (one batch call) */
+    int cand_piece[16], cand_schedule[16], cand_order[16];
+    float cand_ms[16];          /* median ms of one evaluation (one batch call) */
     char key[32];               /* signature: structure(s), r, precision, GPU  */
 } gofmm_tune_t;
 
 /*
  * Autotuner.  Times gofmm_evaluate of h with r right-hand sides in a
  * tensor-core precision under each candidate configuration (piece 256 and
- * 128, each with the FUSED and the STAGED schedule in CRITICAL and in LOCAL
- * order: 8 candidates; 3 warm-up and 7 timed calls each, CUDA events on
+ * 128, each with the FUSED, STAGED and PAIR schedules in CRITICAL and in
+ * LOCAL order: 12 candidates; 3 warm-up and 7 timed calls each, CUDA events on
  * `stream`, on scratch W = 0 and U the library allocates), applies the
  * fastest with gofmm_set_tc_config and reports all of them in *out.
  * cache_path (may be NULL): a JSON file of earlier choices.  If it holds

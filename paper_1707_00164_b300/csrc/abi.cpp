@@ -329,7 +329,7 @@ void fill_tune(const gofmm::TuneResult& t, gofmm_tune_t* out) {
     out->order = t.order;
     out->from_cache = t.from_cache;
     out->n_candidates = t.n;
-    for (int k = 0; k < t.n && k < 8; ++k) {
+    for (int k = 0; k < t.n && k < 16; ++k) {
         out->cand_piece[k] = t.cand_piece[k];
         out->cand_schedule[k] = t.cand_schedule[k];
         out->cand_order[k] = t.cand_order[k];

@@ -48,7 +48,7 @@ int mode_of(int precision) {
 namespace {
 
 constexpr long long kSpinLimit = 2000000000LL;  // clock cycles (about a second) before a wait gives up
-constexpr int kErrProducer = 1, kErrMma = 2, kErrEpilogue = 3, kErrDependency = 4;
+constexpr int kErrProducer = 1, kErrMma = 2, kErrEpilogue = 3, kErrDependency = 4, kErrTmemPair = 5;
 
 // NMAX: the tallest task piece the kernel accepts (MMA N ceiling, 128 or
 // 256).  A stage holds one 128 x 128 B tile of right-hand sides and one
@@ -186,6 +186,92 @@ __device__ __forceinline__ uint32_t swz(uint32_t row, uint32_t byte) {
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Epilogue of one tile: the accumulator rows of this thread (one column j
+// of r) for the task's n_pad block rows, read from TMEM at taddr and written
+// as U rows (scattered to the original order, FP32) or as the next stage's
+// RT operand (rounded to the mode's format, hi/lo for split BF16).
+template <int MODE>
+__device__ __forceinline__ void write_tile(const TcSeg& sg, const TcTask& tk, int rt, int row, uint32_t taddr) {
+    using C = Cfg<MODE>;
+    const int j = rt * 128 + row;
+    const bool jv = j < sg.r;
+    const int ncols = tk.out_kind == OUT_U ? tk.n_pad : (tk.accumulate ? tk.n_pad : tk.out_cols);
+    for (int n0 = 0; n0 < ncols; n0 += 32) {
+        float v[32];
+        if (tk.nchunks > 0 && n0 < tk.n_pad) {
+            tmem_ld32(taddr + uint32_t(n0), v);
+#pragma unroll
+            for (int e = 0; e < 32; ++e)
+                if (n0 + e >= tk.n_pad || !jv) v[e] = 0.f;  // TMEM past n_pad is not this tile's
+        } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) v[e] = 0.f;
+        }
+        if (tk.out_kind == OUT_U) {
+            if (!jv) continue;
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                const int n = n0 + e;
+                if (n < tk.m) {
+                    float* d = sg.U + sg.perm[tk.out_pos + n] * sg.ldu + j;
+                    *d = tk.accumulate ? *d + v[e] : v[e];
+                }
+            }
+            continue;
+        }
+        if (tk.accumulate && !jv) continue;
+        // RT output: 32 consecutive k of this row, inside one chunk
+        const int buf = tk.out_kind == OUT_WTIL ? 1 : 2;
+        const int64_t chunk = tk.out_pos + n0 / C::kKc;
+        const uint32_t byte0 = uint32_t((n0 % C::kKc) * C::kEs);
+        uint8_t* thi = sg.rt_hi[buf] + (int64_t(rt) * sg.rt_chunks[buf] + chunk) * kTileBytes;
+        if constexpr (MODE == TC_TF32) {
+#pragma unroll
+            for (int piece = 0; piece < 8; ++piece) {
+                if (tk.accumulate && n0 + 4 * piece >= tk.n_pad) break;
+                float4* dst = reinterpret_cast<float4*>(thi + swz(row, byte0 + piece * 16));
+                float4 o = make_float4(v[4 * piece], v[4 * piece + 1], v[4 * piece + 2], v[4 * piece + 3]);
+                if (tk.accumulate) {
+                    const float4 e = *dst;
+                    o.x += e.x; o.y += e.y; o.z += e.z; o.w += e.w;
+                }
+                *dst = make_float4(round_tf32(o.x), round_tf32(o.y), round_tf32(o.z), round_tf32(o.w));
+            }
+        } else {
+            uint8_t* tlo = C::kSplit ? sg.rt_lo[buf] + (int64_t(rt) * sg.rt_chunks[buf] + chunk) * kTileBytes
+                                     : nullptr;
+#pragma unroll
+            for (int piece = 0; piece < 4; ++piece) {
+                if (tk.accumulate && n0 + 8 * piece >= tk.n_pad) break;
+                const uint32_t pos = swz(row, byte0 + piece * 16);
+                float x[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) x[e] = v[8 * piece + e];
+                if (tk.accumulate) {
+                    const uint4 eh = *reinterpret_cast<const uint4*>(thi + pos);
+                    const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&eh);
+                    uint4 el = make_uint4(0, 0, 0, 0);
+                    if constexpr (C::kSplit) el = *reinterpret_cast<const uint4*>(tlo + pos);
+                    const __nv_bfloat16* l = reinterpret_cast<const __nv_bfloat16*>(&el);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        x[e] += __bfloat162float(h[e]) + (C::kSplit ? __bfloat162float(l[e]) : 0.f);
+                }
+                uint4 oh, ol;
+                __nv_bfloat16* hh = reinterpret_cast<__nv_bfloat16*>(&oh);
+                __nv_bfloat16* ll = reinterpret_cast<__nv_bfloat16*>(&ol);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    hh[e] = __float2bfloat16_rn(x[e]);
+                    ll[e] = __float2bfloat16_rn(x[e] - __bfloat162float(hh[e]));
+                }
+                *reinterpret_cast<uint4*>(thi + pos) = oh;
+                if constexpr (C::kSplit) *reinterpret_cast<uint4*>(tlo + pos) = ol;
+            }
+        }
+    }
 }
 
 // Persistent grouped GEMM: CTA b processes tiles b, b + gridDim.x, ... (tile
@@ -373,8 +459,6 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
             const TcSeg& sg = p.segs[tt.seg];
             const TcTask tk = sg.tasks[tt.task];
             const int rt = tt.rt;
-            const int j = rt * 128 + row;
-            const bool jv = j < sg.r;
             const int acc = i & 1;
             bool ok = mbar_wait(tfull_bar(acc), uint32_t((i >> 1) & 1), p.err, kErrEpilogue);
             ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
@@ -385,81 +469,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
             // padding columns and in rows j >= r), so every RT element a later
             // stage reads was written earlier in the same evaluation; only the
             // in-place S2N pushes touch valid elements alone.
-            const int ncols = tk.out_kind == OUT_U ? tk.n_pad : (tk.accumulate ? tk.n_pad : tk.out_cols);
-            for (int n0 = 0; n0 < ncols; n0 += 32) {
-                float v[32];
-                if (tk.nchunks > 0 && n0 < tk.n_pad) {
-                    tmem_ld32(taddr + uint32_t(n0), v);
-#pragma unroll
-                    for (int e = 0; e < 32; ++e)
-                        if (n0 + e >= tk.n_pad || !jv) v[e] = 0.f;  // TMEM past n_pad is not this tile's
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 32; ++e) v[e] = 0.f;
-                }
-                if (tk.out_kind == OUT_U) {
-                    if (!jv) continue;
-#pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        const int n = n0 + e;
-                        if (n < tk.m) {
-                            float* d = sg.U + sg.perm[tk.out_pos + n] * sg.ldu + j;
-                            *d = tk.accumulate ? *d + v[e] : v[e];
-                        }
-                    }
-                    continue;
-                }
-                if (tk.accumulate && !jv) continue;
-                // RT output: 32 consecutive k of this row, inside one chunk
-                const int buf = tk.out_kind == OUT_WTIL ? 1 : 2;
-                const int64_t chunk = tk.out_pos + n0 / C::kKc;
-                const uint32_t byte0 = uint32_t((n0 % C::kKc) * C::kEs);
-                uint8_t* thi = sg.rt_hi[buf] + (int64_t(rt) * sg.rt_chunks[buf] + chunk) * kTileBytes;
-                if constexpr (MODE == TC_TF32) {
-#pragma unroll
-                    for (int piece = 0; piece < 8; ++piece) {
-                        if (tk.accumulate && n0 + 4 * piece >= tk.n_pad) break;
-                        float4* dst = reinterpret_cast<float4*>(thi + swz(row, byte0 + piece * 16));
-                        float4 o = make_float4(v[4 * piece], v[4 * piece + 1], v[4 * piece + 2], v[4 * piece + 3]);
-                        if (tk.accumulate) {
-                            const float4 e = *dst;
-                            o.x += e.x; o.y += e.y; o.z += e.z; o.w += e.w;
-                        }
-                        *dst = make_float4(round_tf32(o.x), round_tf32(o.y), round_tf32(o.z), round_tf32(o.w));
-                    }
-                } else {
-                    uint8_t* tlo = C::kSplit ? sg.rt_lo[buf] + (int64_t(rt) * sg.rt_chunks[buf] + chunk) * kTileBytes
-                                             : nullptr;
-#pragma unroll
-                    for (int piece = 0; piece < 4; ++piece) {
-                        if (tk.accumulate && n0 + 8 * piece >= tk.n_pad) break;
-                        const uint32_t pos = swz(row, byte0 + piece * 16);
-                        float x[8];
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) x[e] = v[8 * piece + e];
-                        if (tk.accumulate) {
-                            const uint4 eh = *reinterpret_cast<const uint4*>(thi + pos);
-                            const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&eh);
-                            uint4 el = make_uint4(0, 0, 0, 0);
-                            if constexpr (C::kSplit) el = *reinterpret_cast<const uint4*>(tlo + pos);
-                            const __nv_bfloat16* l = reinterpret_cast<const __nv_bfloat16*>(&el);
-#pragma unroll
-                            for (int e = 0; e < 8; ++e)
-                                x[e] += __bfloat162float(h[e]) + (C::kSplit ? __bfloat162float(l[e]) : 0.f);
-                        }
-                        uint4 oh, ol;
-                        __nv_bfloat16* hh = reinterpret_cast<__nv_bfloat16*>(&oh);
-                        __nv_bfloat16* ll = reinterpret_cast<__nv_bfloat16*>(&ol);
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            hh[e] = __float2bfloat16_rn(x[e]);
-                            ll[e] = __float2bfloat16_rn(x[e] - __bfloat162float(hh[e]));
-                        }
-                        *reinterpret_cast<uint4*>(thi + pos) = oh;
-                        if constexpr (C::kSplit) *reinterpret_cast<uint4*>(tlo + pos) = ol;
-                    }
-                }
-            }
+            write_tile<MODE>(sg, tk, rt, row, taddr);
             // accumulator buffer free for the MMA of the tile after next
             tc_fence_before();
             __syncwarp();
@@ -486,6 +496,292 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
         __syncwarp();
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::kTmemCols)
+                     : "memory");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// SM-pair variant (tcgen05 cta_group::2).  A cluster of two CTAs computes one
+// 256 x N output tile: two r-tiles (2q and 2q + 1) of one task.  CTA c of the
+// pair stages the 128 right-hand-side columns of r-tile 2q + c and block rows
+// [c N/2, (c + 1) N/2) of each chunk; the even CTA issues the M = 256 MMAs,
+// which read both CTAs' shared memory and leave each CTA's 128 accumulator
+// rows in that CTA's TMEM, so each CTA's epilogue writes its own r-tile as in
+// the single-SM kernel.  Per SM, a chunk then stages 128 + N/2 rows instead
+// of 128 + N for the same MMA work.
+//
+// Bulk copies signal a barrier of their own CTA only, so the odd CTA's MMA
+// warp (idle otherwise) forwards each completed stage to the even CTA's
+// barrier with a remote arrive; the even CTA's commits arrive on both CTAs'
+// barriers (multicast).  Static tile order (the staged schedule).
+template <int MODE, int NMAX>
+struct Cfg2 {
+    static constexpr bool kSplit = MODE == TC_BF16X3;
+    static constexpr int kBHalf = NMAX / 2 * 128;  // bytes of one CTA's half block tile
+    static constexpr int kStageBytes = (kSplit ? 2 : 1) * (kTileBytes + kBHalf);
+    static constexpr int kStages = (200 * 1024 / kStageBytes) < 8 ? (200 * 1024 / kStageBytes) : 8;
+    static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
+    static constexpr int kTmemCols = 2 * NMAX;  // two accumulators
+    static_assert(kStages >= 2 && kSmem <= 227 * 1024, "stage ring");
+};
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// shared::cluster address of the same shared-memory offset in CTA `rank`
+__device__ __forceinline__ uint32_t peer_addr(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait with cluster-scope acquire (arrivals from the other CTA).
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, int* err, int code) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait_cluster(bar, parity)) {
+        if (*reinterpret_cast<volatile int*>(err) != 0) return false;
+        if (clock64() - t0 > kSpinLimit) {
+            atomicCAS(err, 0, code);
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t cluster_addr) {
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(cluster_addr) : "memory");
+    return v;
+}
+template <int MODE>
+__device__ __forceinline__ void mma_pair(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    if constexpr (MODE == TC_TF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc));
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc));
+    }
+}
+// commit of the pair's MMAs issued so far: one arrival on the barrier at the
+// same offset in both CTAs
+__device__ __forceinline__ void mma_commit_pair(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            bar),
+        "h"(uint16_t(3))
+        : "memory");
+}
+
+template <int MODE, int NMAX>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
+    tc_gemm_pair_kernel(const __grid_constant__ TcParams p) {
+    using C = Cfg2<MODE, NMAX>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base + C::kStages * C::kStageBytes);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::kStages + 5);
+    const uint32_t s_base = smem_u32(base);
+    auto full_bar = [&](int s) { return smem_u32(&bars[s]); };
+    auto empty_bar = [&](int s) { return smem_u32(&bars[C::kStages + s]); };
+    auto tfull_bar = [&](int a) { return smem_u32(&bars[2 * C::kStages + a]); };
+    auto tempty_bar = [&](int a) { return smem_u32(&bars[2 * C::kStages + 2 + a]); };
+    const uint32_t drain_bar = smem_u32(&bars[2 * C::kStages + 4]);
+    // stage s: A_hi | B_hi half | (A_lo | B_lo half)
+    auto sA = [&](int s, int lo) { return s_base + s * C::kStageBytes + lo * (kTileBytes + C::kBHalf); };
+    auto sB = [&](int s, int lo) { return sA(s, lo) + kTileBytes; };
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t crank = cluster_rank();
+    const bool leader = crank == 0;
+    const int pair = int(blockIdx.x >> 1), npairs = int(gridDim.x >> 1);
+    const int ntiles = p.ntiles;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::kStages; ++s) {
+            mbar_init(full_bar(s), leader ? 2 : 1);  // leader: own copies + the odd CTA's forward
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(tfull_bar(a), 1);
+            mbar_init(tempty_bar(a), 8);  // four epilogue warps in each CTA (used in the leader)
+        }
+        mbar_init(drain_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(C::kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();  // barriers of both CTAs initialised, TMEM allocated
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    // the two CTAs must address the same TMEM columns
+    if (!leader && threadIdx.x == 0 && ld_cluster_u32(peer_addr(smem_u32(tmem_slot), 0)) != tmem)
+        atomicCAS(p.err, 0, kErrTmemPair);
+    cluster_sync_all();
+    const bool run = *reinterpret_cast<volatile int*>(p.err) == 0;
+
+    if (run && warp == 0) {
+        if (lane == 0) {
+            // ---- producer (both CTAs): own r-tile and own half of each block chunk
+            int stage = 0, issued = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int t = pair; t < ntiles && ok; t += npairs) {
+                const TcTile tt = p.tiles[t];
+                const TcSeg& sg = p.segs[tt.seg];
+                const TcTask tk = sg.tasks[tt.task];
+                const int rt = 2 * tt.rt + int(crank);
+                const bool live = rt * 128 < sg.r;  // the odd half of the last pair may be padding
+                const uint32_t half = uint32_t(tk.n_pad) / 2u * 128u;
+                const uint32_t a_bytes = live ? uint32_t(kTileBytes) : 0u;
+                for (int si = tk.slab0; si < tk.slab1 && ok; ++si) {
+                    const TcSlab sl = sg.slabs[si];
+                    const int64_t a_off = (int64_t(rt) * sg.rt_chunks[sl.a_buf] + sl.a_chunk0) * kTileBytes;
+                    const int64_t b_row = int64_t(tk.n_pad) * 128;
+                    const int64_t b_off = sl.b_off + int64_t(crank) * half;
+                    for (int c = 0; c < sl.nchunks; ++c) {
+                        if (!mbar_wait(empty_bar(stage), phase ^ 1u, p.err, kErrProducer)) { ok = false; break; }
+                        mbar_expect_tx(full_bar(stage), (C::kSplit ? 2u : 1u) * (a_bytes + half));
+                        if (live)
+                            bulk_g2s(sA(stage, 0), sg.rt_hi[sl.a_buf] + a_off + int64_t(c) * kTileBytes, kTileBytes,
+                                     full_bar(stage));
+                        bulk_g2s(sB(stage, 0), sg.b_hi + b_off + int64_t(c) * b_row, half, full_bar(stage));
+                        if constexpr (C::kSplit) {
+                            if (live)
+                                bulk_g2s(sA(stage, 1), sg.rt_lo[sl.a_buf] + a_off + int64_t(c) * kTileBytes,
+                                         kTileBytes, full_bar(stage));
+                            bulk_g2s(sB(stage, 1), sg.b_lo + b_off + int64_t(c) * b_row, half, full_bar(stage));
+                        }
+                        ++issued;
+                        if (++stage == C::kStages) { stage = 0; phase ^= 1u; }
+                    }
+                }
+            }
+            if (!ok) {
+                const int outstanding = issued < C::kStages ? issued : C::kStages;
+                for (int q = 1; q <= outstanding; ++q) {
+                    const int idx = issued - q;
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(full_bar(idx % C::kStages), uint32_t((idx / C::kStages) & 1)) &&
+                           clock64() - t0 < kSpinLimit) {
+                    }
+                }
+            }
+        }
+    } else if (run && warp == 1) {
+        if (lane == 0 && leader) {
+            // ---- MMA issuer (even CTA, one thread)
+            int stage = 0, i = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int t = pair; t < ntiles && ok; t += npairs, ++i) {
+                const TcTile tt = p.tiles[t];
+                const TcTask tk = p.segs[tt.seg].tasks[tt.task];
+                const int acc = i & 1;
+                if (!mbar_wait_cluster(tempty_bar(acc), uint32_t(((i >> 1) & 1) ^ 1), p.err, kErrMma)) break;
+                tc_fence_after();
+                const uint32_t tacc = tmem + uint32_t(acc * NMAX);
+                const uint32_t idesc = (1u << 4) | (uint32_t(MODE == TC_TF32 ? 2 : 1) << 7) |
+                                       (uint32_t(MODE == TC_TF32 ? 2 : 1) << 10) | (uint32_t(tk.n_pad >> 3) << 17) |
+                                       (uint32_t(256 >> 4) << 24);
+                for (int q = 0; q < tk.nchunks; ++q) {
+                    if (!mbar_wait_cluster(full_bar(stage), phase, p.err, kErrMma)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint64_t da = sw128_desc(sA(stage, 0)), db = sw128_desc(sB(stage, 0));
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t off = uint64_t(kk * 2);
+                        mma_pair<MODE>(tacc, da + off, db + off, idesc, (q > 0 || kk > 0) ? 1u : 0u);
+                        if constexpr (C::kSplit) {
+                            const uint64_t dal = sw128_desc(sA(stage, 1)), dbl = sw128_desc(sB(stage, 1));
+                            mma_pair<MODE>(tacc, da + off, dbl + off, idesc, 1u);
+                            mma_pair<MODE>(tacc, dal + off, db + off, idesc, 1u);
+                        }
+                    }
+                    mma_commit_pair(empty_bar(stage));
+                    if (++stage == C::kStages) { stage = 0; phase ^= 1u; }
+                }
+                if (!ok) break;
+                mma_commit_pair(tfull_bar(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             drain_bar)
+                         : "memory");
+            const long long t0 = clock64();
+            while (!mbar_try_wait(drain_bar, 0) && clock64() - t0 < kSpinLimit) {
+            }
+        } else if (lane == 0) {
+            // ---- odd CTA: forward each landed stage to the even CTA's barrier
+            int stage = 0;
+            uint32_t phase = 0;
+            bool ok = true;
+            for (int t = pair; t < ntiles && ok; t += npairs) {
+                const TcTile tt = p.tiles[t];
+                const TcTask tk = p.segs[tt.seg].tasks[tt.task];
+                for (int q = 0; q < tk.nchunks; ++q) {
+                    if (!mbar_wait(full_bar(stage), phase, p.err, kErrMma)) { ok = false; break; }
+                    mbar_arrive_cluster(peer_addr(full_bar(stage), 0));
+                    if (++stage == C::kStages) { stage = 0; phase ^= 1u; }
+                }
+            }
+        }
+    } else if (run) {
+        // ---- epilogue: warps 2..5 own TMEM lane quarters (warp % 4)
+        const int q4 = warp & 3;
+        const int row = q4 * 32 + lane;
+        const uint32_t tempty_leader = peer_addr(tempty_bar(0), 0);  // + 8 bytes for accumulator 1
+        int i = 0;
+        for (int t = pair; t < ntiles; t += npairs, ++i) {
+            const TcTile tt = p.tiles[t];
+            const TcSeg& sg = p.segs[tt.seg];
+            const TcTask tk = sg.tasks[tt.task];
+            const int rt = 2 * tt.rt + int(crank);
+            const int acc = i & 1;
+            bool ok = mbar_wait_cluster(tfull_bar(acc), uint32_t((i >> 1) & 1), p.err, kErrEpilogue);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t taddr = tmem + uint32_t(acc * NMAX) + (uint32_t(q4 * 32) << 16);
+            if (rt * 128 < sg.r) write_tile<MODE>(sg, tk, rt, row, taddr);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(tempty_leader + uint32_t(acc * 8));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();  // no MMA of the pair runs and no TMEM read is pending
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::kTmemCols)
                      : "memory");
     }
 }
@@ -877,6 +1173,10 @@ static void set_smem_attr() {
                                  Cfg<MODE, 256>::kSmem));
     CUDA_OK(cudaFuncSetAttribute(tc_gemm_kernel<MODE, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  Cfg<MODE, 128>::kSmem));
+    CUDA_OK(cudaFuncSetAttribute(tc_gemm_pair_kernel<MODE, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 Cfg2<MODE, 256>::kSmem));
+    CUDA_OK(cudaFuncSetAttribute(tc_gemm_pair_kernel<MODE, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 Cfg2<MODE, 128>::kSmem));
 }
 
 // Tile list of one launch alone, the r-tiles of a task adjacent so they
@@ -884,8 +1184,11 @@ static void set_smem_attr() {
 // (heaviest first, for the tail of the launch); LOCAL: tasks in heap order
 // (tree levels top down, nodes left to right), so that consecutive tasks
 // share most of their far or near lists and re-read operands from L2.
-static std::pair<TcTile*, int> launch_tiles(TcLaunch& l, int n_rtiles, int order) {
-    const int key = n_rtiles * 2 + (order == GOFMM_ORDER_LOCAL ? 1 : 0);
+// With pair = true the list holds pairs of r-tiles (rt = pair index) for the
+// SM-pair kernel.
+static std::pair<TcTile*, int> launch_tiles(TcLaunch& l, int n_rtiles, int order, bool pair = false) {
+    if (pair) n_rtiles = (n_rtiles + 1) / 2;
+    const int key = n_rtiles * 4 + (order == GOFMM_ORDER_LOCAL ? 1 : 0) + (pair ? 2 : 0);
     auto it = l.tiles.find(key);
     if (it != l.tiles.end()) return it->second;
     std::vector<int32_t> tasks(l.tasks.size());
@@ -900,6 +1203,8 @@ static std::pair<TcTile*, int> launch_tiles(TcLaunch& l, int n_rtiles, int order
     l.tiles[key] = v;
     return v;
 }
+
+static void occupancy_pairs(int num_sms);
 
 TcPrec& tc_plan(Handle& H, DeviceState& D, int precision) {
     if (!D.tc) D.tc = new TcState();
@@ -938,6 +1243,7 @@ TcPrec& tc_plan(Handle& H, DeviceState& D, int precision) {
         set_smem_attr<TC_TF32>();
         set_smem_attr<TC_BF16>();
         set_smem_attr<TC_BF16X3>();
+        occupancy_pairs(t->num_sms);  // before any stream capture
         T = t.release();
     }
     return *T;
@@ -946,7 +1252,8 @@ TcPrec& tc_plan(Handle& H, DeviceState& D, int precision) {
 void tc_prepare(Handle& H, DeviceState& D, int64_t r_max, int precision) {
     TcPrec* T = &tc_plan(H, D, precision);
     const int64_t r_pad = (r_max + 127) / 128 * 128;
-    for (TcLaunch& l : T->launches) launch_tiles(l, int(r_pad / 128), H.tc_order[T->mode]);
+    for (TcLaunch& l : T->launches)
+        launch_tiles(l, int(r_pad / 128), H.tc_order[T->mode], H.tc_schedule[T->mode] == GOFMM_SCHED_PAIR);
     TcFused& F = T->fused;
     if (F.counters_nrt < int(r_pad / 128)) {
         dfree(F.d_counters);
@@ -1040,6 +1347,58 @@ void launch_gemm_mode(int mode, int piece, const TcParams& p, int num_sms, cudaS
     }
 }
 
+// SM-pair kernel: clusters of two CTAs (static tiles).  The grid is the
+// number of clusters the GPU holds at once (pairs of SMs of one GPC), so no
+// cluster waits for a second wave.
+template <int MODE, int NMAX>
+static int resident_pairs(int num_sms) {
+    static int cached = 0;  // per kernel instantiation; one device type per process
+    if (cached > 0) return cached;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(num_sms / 2 * 2));
+    cfg.blockDim = dim3(192);
+    cfg.dynamicSmemBytes = Cfg2<MODE, NMAX>::kSmem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    CUDA_OK(cudaOccupancyMaxActiveClusters(&n, tc_gemm_pair_kernel<MODE, NMAX>, &cfg));
+    cached = std::max(1, std::min(n, num_sms / 2));
+    return cached;
+}
+
+static void occupancy_pairs(int num_sms) {
+    resident_pairs<TC_TF32, 128>(num_sms);
+    resident_pairs<TC_TF32, 256>(num_sms);
+    resident_pairs<TC_BF16, 128>(num_sms);
+    resident_pairs<TC_BF16, 256>(num_sms);
+    resident_pairs<TC_BF16X3, 128>(num_sms);
+    resident_pairs<TC_BF16X3, 256>(num_sms);
+}
+
+template <int MODE, int NMAX>
+static void launch_gemm_pair(const TcParams& p, int num_sms, cudaStream_t s) {
+    const int pairs = std::min(p.ntiles, resident_pairs<MODE, NMAX>(num_sms));
+    tc_gemm_pair_kernel<MODE, NMAX><<<unsigned(2 * pairs), 192, Cfg2<MODE, NMAX>::kSmem, s>>>(p);
+    CUDA_OK(cudaGetLastError());
+}
+
+static void launch_gemm_pair_mode(int mode, int piece, const TcParams& p, int num_sms, cudaStream_t s) {
+    if (piece <= 128) {
+        if (mode == TC_TF32) launch_gemm_pair<TC_TF32, 128>(p, num_sms, s);
+        else if (mode == TC_BF16) launch_gemm_pair<TC_BF16, 128>(p, num_sms, s);
+        else launch_gemm_pair<TC_BF16X3, 128>(p, num_sms, s);
+    } else {
+        if (mode == TC_TF32) launch_gemm_pair<TC_TF32, 256>(p, num_sms, s);
+        else if (mode == TC_BF16) launch_gemm_pair<TC_BF16, 256>(p, num_sms, s);
+        else launch_gemm_pair<TC_BF16X3, 256>(p, num_sms, s);
+    }
+}
+
 static void launch_gemm_coop_mode(int mode, int piece, const TcParams& p, int num_sms, cudaStream_t s) {
     if (piece <= 128) {
         if (mode == TC_TF32) launch_gemm_coop<TC_TF32, 128>(p, num_sms, s);
@@ -1079,18 +1438,21 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
     TcParams p{};
     p.nsegs = 1;
     p.err = T.d_err;
-    if (H.timing == 1 || H.tc_schedule[T.mode] == GOFMM_SCHED_STAGED) {
-        // one launch per stage (stage timing, or the staged schedule)
+    const int sched = H.tc_schedule[T.mode];
+    if (H.timing == 1 || sched != GOFMM_SCHED_FUSED) {
+        // one launch per stage (stage timing, or a staged schedule)
         D.last_fused = false;
+        const bool pair = sched == GOFMM_SCHED_PAIR;
         int stage_done = 1;
         for (TcLaunch& l : T.launches) {
             while (stage_done < l.stage) CUDA_OK(cudaEventRecord(D.ev[++stage_done], s));
             if (l.tasks.empty()) continue;
-            const auto tl = launch_tiles(l, n_rtiles, H.tc_order[T.mode]);
+            const auto tl = launch_tiles(l, n_rtiles, H.tc_order[T.mode], pair);
             p.tiles = tl.first;
             p.ntiles = tl.second;
             p.segs[0] = make_seg(T, l, T.rt_hi, T.rt_lo, U, ldu, D.d_idx, r);
-            launch_gemm_mode(T.mode, T.piece, p, T.num_sms, s);
+            if (pair) launch_gemm_pair_mode(T.mode, T.piece, p, T.num_sms, s);
+            else launch_gemm_mode(T.mode, T.piece, p, T.num_sms, s);
             ++launches;
         }
         while (stage_done < 5) CUDA_OK(cudaEventRecord(D.ev[++stage_done], s));

@@ -138,7 +138,7 @@ struct Handle {
     // tensor-core launch configuration per mode (TF32, BF16, BF16X3), set by
     // the autotuner or by the caller; read when the mode's plan is built
     int tc_piece[3] = {256, 256, 256};  // task piece height (MMA N ceiling): 128 or 256
-    int tc_schedule[3] = {0, 0, 0};     // GOFMM_SCHED_FUSED or GOFMM_SCHED_STAGED
+    int tc_schedule[3] = {0, 0, 0};     // GOFMM_SCHED_FUSED, _STAGED or _PAIR
     int tc_order[3] = {0, 0, 0};        // GOFMM_ORDER_CRITICAL or GOFMM_ORDER_LOCAL (fused schedule)
     int64_t plan_epoch = 0;  // bumped whenever a tensor-core plan is rebuilt (batches check it)
     int64_t inflight = 0;    // engine requests of this handle not yet retired
@@ -156,7 +156,7 @@ void device_trim(Handle& H);
 void device_stall_next(Handle& H, int precision);
 
 // Tensor-core launch configuration and its autotuner (tune.cu).
-constexpr int kTuneMax = 8;  // candidates of one tuning run
+constexpr int kTuneMax = 16;  // candidates of one tuning run
 struct TuneResult {
     int piece = 256, schedule = 0, order = 0, from_cache = 0, n = 0;
     int cand_piece[kTuneMax] = {}, cand_schedule[kTuneMax] = {}, cand_order[kTuneMax] = {};

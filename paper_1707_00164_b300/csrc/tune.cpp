@@ -429,10 +429,9 @@ TuneResult autotune(Handle& H, int64_t r, int precision, const char* cache_path,
     DevBuf W(size_t(n) * size_t(r) * sizeof(float)), U(size_t(n) * size_t(r) * sizeof(float));
     const int saved_timing = H.timing;
     H.timing = 0;  // the production path, graph replay included
-    const int cands[4][2] = {{GOFMM_SCHED_FUSED, GOFMM_ORDER_CRITICAL},
-                             {GOFMM_SCHED_FUSED, GOFMM_ORDER_LOCAL},
-                             {GOFMM_SCHED_STAGED, GOFMM_ORDER_CRITICAL},
-                             {GOFMM_SCHED_STAGED, GOFMM_ORDER_LOCAL}};
+    const int cands[6][2] = {{GOFMM_SCHED_FUSED, GOFMM_ORDER_CRITICAL}, {GOFMM_SCHED_FUSED, GOFMM_ORDER_LOCAL},
+                             {GOFMM_SCHED_STAGED, GOFMM_ORDER_CRITICAL}, {GOFMM_SCHED_STAGED, GOFMM_ORDER_LOCAL},
+                             {GOFMM_SCHED_PAIR, GOFMM_ORDER_CRITICAL},   {GOFMM_SCHED_PAIR, GOFMM_ORDER_LOCAL}};
     float best = 0.f;
     try {
         for (int piece : {256, 128})

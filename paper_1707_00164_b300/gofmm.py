@@ -27,7 +27,7 @@ DTYPE_F64, DTYPE_F32 = 0, 1
 PREC_FP64, PREC_FP32, PREC_TF32, PREC_BF16, PREC_BF16X3 = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "tf32": PREC_TF32, "bf16": PREC_BF16,
               "bf16x3": PREC_BF16X3}
-SCHED_FUSED, SCHED_STAGED = 0, 1
+SCHED_FUSED, SCHED_STAGED, SCHED_PAIR = 0, 1, 2
 ORDER_CRITICAL, ORDER_LOCAL = 0, 1
 
 BLOCK_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(C.c_int64), C.c_int64,
@@ -51,8 +51,8 @@ class ParamsC(C.Structure):
 
 class TuneC(C.Structure):
     _fields_ = [("piece", C.c_int), ("schedule", C.c_int), ("order", C.c_int), ("from_cache", C.c_int),
-                ("n_candidates", C.c_int), ("cand_piece", C.c_int * 8), ("cand_schedule", C.c_int * 8),
-                ("cand_order", C.c_int * 8), ("cand_ms", C.c_float * 8), ("key", C.c_char * 32)]
+                ("n_candidates", C.c_int), ("cand_piece", C.c_int * 16), ("cand_schedule", C.c_int * 16),
+                ("cand_order", C.c_int * 16), ("cand_ms", C.c_float * 16), ("key", C.c_char * 32)]
 
 
 class StatsC(C.Structure):
