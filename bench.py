@@ -41,7 +41,7 @@ WORKLOAD = wl.C2
 GOLDEN = os.path.join(ROOT, "tests", "golden", "c2_rows.npz")
 GOLDEN_C3 = os.path.join(ROOT, "tests", "golden", "imq4d_n131072_r2048_rows.npz")
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic_tc_gemm_s2s.txt")
+TRAFFIC_PATH = os.path.join(ROOT, "profiles", "traffic_tc_gemm.txt")
 # B300: 148 SMs x 128 FP32 lanes x 2 flop (FMA) per clock
 SMS, FP32_LANES = 148, 128
 # tensor-core dense rate relative to BF16 (nominal: TF32 1.1 / BF16 2.25 PFLOP/s)
@@ -618,22 +618,23 @@ def native_arm(args):
         peak = bf16 * NOMINAL_RATIO[prec_name]
         bound, peak_src = "tensor", (f"of measured bf16 burst ({bf16:.0f} TFLOP/s) x nominal ratio "
                                      f"{NOMINAL_RATIO[prec_name]:.3f} for {prec_name}")
+    # DRAM bytes of the GEMM launches of one evaluation, per launch
+    # configuration, from an ncu capture of the same kernel source (null
+    # when the source, workload or precision differs)
     traffic = None
     tr = {}
     if os.path.exists(TRAFFIC_PATH):
         for line in open(TRAFFIC_PATH):
             if "=" in line and not line.startswith("#"):
-                k, v = line.split("=", 1)
+                k, v = line.split("#")[0].split("=", 1)
                 tr[k.strip()] = v.strip()
         src = os.path.join(ROOT, "paper_1707_00164_b300", "csrc", tr.get("source", "-"))
-        if tr.get("precision") == prec_name and os.path.exists(src) and \
-                hashlib.sha256(open(src, "rb").read()).hexdigest() == tr.get("sha256") and \
-                tr.get("workload") == w.name:
-            traffic = float(tr["dram_bytes_per_launch"])  # null once the kernel source changed
-
-    def traffic_matches_config(t):
-        cfg = f"{t['piece']}/{['fused', 'staged', 'pair'][t['schedule']]}/{['critical', 'local'][t['order']]}"
-        return tr.get("config") == cfg
+        current = (tr.get("precision") == prec_name and os.path.exists(src) and tr.get("workload") == w.name
+                   and hashlib.sha256(open(src, "rb").read()).hexdigest() == tr.get("sha256"))
+        if current and tune is not None:
+            cfg = (f"{tune['piece']}/{['fused', 'staged', 'pair'][tune['schedule']]}/"
+                   f"{['critical', 'local'][tune['order']]}")
+            traffic = float(tr[cfg]) if cfg in tr else None
     if prec_name in ("fp32", "fp64"):
         kdesc = "gemm_simt_kernel, S2S launch (every far pair of every level)"
     elif tune is None or tune["schedule"] == G.SCHED_FUSED:
@@ -642,9 +643,13 @@ def native_arm(args):
     else:
         kname = "tc_gemm_pair_kernel" if tune["schedule"] == G.SCHED_PAIR else "tc_gemm_kernel"
         kdesc = f"{kname}<{prec_name}>: every launch of the staged schedule (N2S, S2S, S2N, L2L)"
-    if tune is not None:
-        traffic = traffic if traffic_matches_config(tune) else None
-    roofline = {"kernel": kdesc, "bound": bound,
+    # algorithmic bytes of those launches: every cached block and
+    # interpolation tile once, W read once, skeleton weights and potentials
+    # written and read once each, U written once (FP32)
+    be = {"tf32": 4, "bf16": 2, "bf16x3": 4, "fp32": 4, "fp64": 8}[prec_name]
+    alg_bytes = ((st["near_entries"] + st["far_entries"] + st["interp_entries"]) * be + w.n * r * be
+                 + 4 * st["skel_total"] * r * be + w.n * r * 4)
+    roofline = {"kernel": kdesc, "bound": bound, "algorithmic_bytes": alg_bytes,
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": peak_src, "traffic": traffic, "flops_per_launch": flops,
                 "launch_ms": launch_ms,
