@@ -661,6 +661,17 @@ def native_arm(args):
         dense = dense_reference(torch, K, W, dev)
 
     bg.join()
+    # compression of the throughput workload with the sampled blocks K_{I'a}
+    # generated on the host and on the GPU (not part of any timed number)
+    compression = None
+    if rank == 0 and world == 1 and not args.n:
+        compression = {}
+        for mode in (0, 1):
+            t0 = time.perf_counter()
+            hc = G.compress(entries, G.default_params(**w.params(), device=local, sample_device=mode))
+            compression["device_sampling_s" if mode else "host_sampling_s"] = round(time.perf_counter() - t0, 3)
+            G.free(hc)
+        compression["host_threads"] = os.cpu_count()
     batching = serving = precision = None
     if "precision" in extra:
         try:
@@ -699,7 +710,7 @@ def native_arm(args):
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches * args.steps,
             "autotune": tune, "accuracy": acc, "modes": modes, "dense_cublas": dense, "precision_workload": precision, "batching": batching,
             "serving": serving,
-            "compress_seconds": round(compress_s, 2),
+            "compress_seconds": round(compress_s, 2), "compression": compression,
             "structure": {k: st[k] for k in ("depth", "mean_rank", "max_rank", "near_pairs", "far_pairs",
                                               "near_entries", "far_entries")},
         }))

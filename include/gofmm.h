@@ -120,7 +120,11 @@ typedef struct gofmm_params {
     int64_t knn_exact_max;  /* exhaustive neighbour search up to this N       */
     uint64_t seed;          /* seeds every random choice of the method        */
     int device;             /* CUDA device that will evaluate                 */
-    int reserved;
+    int sample_device;      /* 1: generate the sampled blocks K_{I' a} of the
+                               skeletonization (Alg. 2 steps 8-9) on `device`
+                               in FP64, level by level; the pivoted QR and
+                               the solve stay on the host (generator kinds
+                               only; needs a GPU).  0: host (default)        */
 } gofmm_params;
 
 /* Figures of a compressed matrix (for the flop/byte accounting). */

@@ -22,7 +22,7 @@ INCLUDE = os.path.join(ROOT, "include")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CXX_SOURCES = ["compress.cpp", "abi.cpp", "tune.cpp"]
-CU_SOURCES = ["eval.cu", "eval_tc.cu", "eval_static.cu", "engine.cu"]
+CU_SOURCES = ["eval.cu", "eval_tc.cu", "eval_static.cu", "engine.cu", "sample.cu"]
 
 
 def _deps():

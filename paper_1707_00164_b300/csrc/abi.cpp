@@ -96,6 +96,8 @@ gofmm::Params make_params(const gofmm_params* p) {
     q.knn_exact_max = p->knn_exact_max;
     q.seed = p->seed;
     q.device = p->device;
+    q.sample_device = p->sample_device;
+    if (q.sample_device != 0 && q.sample_device != 1) fail(GOFMM_ERR_ARG, "sample_device must be 0 or 1");
     if (q.m < 1) fail(GOFMM_ERR_ARG, "leaf_size must be >= 1");
     if (q.s < 1) fail(GOFMM_ERR_ARG, "max_rank must be >= 1");
     if (!(q.tau >= 0)) fail(GOFMM_ERR_ARG, "tau must be >= 0");

@@ -11,6 +11,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <numeric>
 
 #include "gofmm_internal.hpp"
@@ -614,13 +615,47 @@ static std::vector<int64_t> sample_rows(const Structure& st, const std::vector<i
     return cand;
 }
 
-// Alg. 6 in postorder over every node except the root.
-static void skeletonize(const Ctx& c, Structure& st, const std::vector<int64_t>& knn, int kappa) {
+// Alg. 6 in postorder over every node except the root.  With sampler set,
+// the sampled blocks K_{I'a} of a whole level are generated on the GPU in
+// one call before the level's decompositions run on the host.
+static void skeletonize(const Ctx& c, Structure& st, const std::vector<int64_t>& knn, int kappa,
+                        DeviceSampler* sampler) {
     const int L = st.depth;
     st.skel.assign(st.n_nodes(), {});
     st.P.assign(st.n_nodes(), {});
     for (int lvl = L; lvl >= 1; --lvl) {
         const int64_t first = (int64_t(1) << lvl) - 1, cnt = int64_t(1) << lvl;
+        if (sampler) {
+            const size_t nc = static_cast<size_t>(cnt);
+            std::vector<std::vector<int64_t>> rows(nc), cols(nc);
+            std::vector<std::vector<double>> A(nc);
+            parallel_for(cnt, c.par, [&](int64_t t) {
+                const int64_t h = first + t;
+                if (lvl == L) {
+                    cols[t].assign(st.perm.begin() + st.node_off[h], st.perm.begin() + st.node_off[h] + st.node_size[h]);
+                } else {
+                    cols[t] = st.skel[2 * h + 1];
+                    cols[t].insert(cols[t].end(), st.skel[2 * h + 2].begin(), st.skel[2 * h + 2].end());
+                }
+                rows[t] = sample_rows(st, knn, kappa, h);
+                A[t].resize(rows[t].size() * cols[t].size());
+            });
+            std::vector<SampleJob> jobs(nc);
+            for (int64_t t = 0; t < cnt; ++t)
+                jobs[t] = SampleJob{rows[t].data(), int64_t(rows[t].size()), cols[t].data(), int64_t(cols[t].size()),
+                                    A[t].data()};
+            sampler->sample(jobs);
+            parallel_for(cnt, c.par, [&](int64_t t) {
+                const int64_t h = first + t;
+                const int64_t m = int64_t(rows[t].size()), n = int64_t(cols[t].size());
+                IdResult id = interpolative_decomposition(A[t], m, n, st.prm.s, st.prm.tau);
+                std::vector<int64_t> sk(id.s);
+                for (int64_t u = 0; u < id.s; ++u) sk[u] = cols[t][id.perm[u]];
+                st.skel[h] = std::move(sk);
+                st.P[h] = std::move(id.P);
+            });
+            continue;
+        }
         parallel_for(cnt, c.par, [&](int64_t t) {
             const int64_t h = first + t;
             std::vector<int64_t> cols;
@@ -699,7 +734,9 @@ void compress(const Entries& K, Structure& st) {
     leaf_near(st, knn, kappa, leaf_of);
     if (prm.far_mode == GOFMM_FAR_PAPER) far_paper(st);
     else far_symmetric(st);
-    skeletonize(c, st, knn, kappa);
+    std::unique_ptr<DeviceSampler> sampler;
+    if (prm.sample_device) sampler = std::make_unique<DeviceSampler>(K, prm.device);
+    skeletonize(c, st, knn, kappa, sampler.get());
     if (!K.is_generator() && prm.cache_mode == GOFMM_CACHE_BLOCKS) cache_blocks_host(K, st);
     st.compress_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }

@@ -71,6 +71,7 @@ struct Params {
     int64_t knn_exact_max = 16384;
     uint64_t seed = 0;
     int device = 0;
+    int sample_device = 0;  // skeletonization blocks K_{I'a} generated on the GPU
 };
 
 // ---------------------------------------------------------------------------
@@ -104,6 +105,30 @@ struct Structure {
         return is_leaf(h) ? node_size[h]
                           : int64_t(skel[2 * h + 1].size() + skel[2 * h + 2].size());
     }
+};
+
+// Generator entries on the GPU for compression (sample.cu): FP64 blocks
+// K(rows, cols), written column-major (m x n, leading dimension m) into host
+// memory, for many (rows, cols) pairs per call.
+struct SampleJob {
+    const int64_t* rows;
+    int64_t m;
+    const int64_t* cols;
+    int64_t n;
+    double* out;
+};
+class DeviceSampler {
+public:
+    DeviceSampler(const Entries& K, int device);  // uploads the points once
+    ~DeviceSampler();
+    DeviceSampler(const DeviceSampler&) = delete;
+    DeviceSampler& operator=(const DeviceSampler&) = delete;
+    void sample(const std::vector<SampleJob>& jobs);
+
+private:
+    const Entries& K_;
+    int device_;
+    double* d_pts_ = nullptr;
 };
 
 int tree_depth(int64_t n, int64_t m);

@@ -46,7 +46,7 @@ class ParamsC(C.Structure):
                 ("far_mode", C.c_int), ("cache_mode", C.c_int), ("n_centroid", C.c_int),
                 ("n_sample", C.c_int), ("ann_max_iter", C.c_int), ("num_threads", C.c_int),
                 ("ann_target_recall", C.c_double), ("knn_exact_max", C.c_int64),
-                ("seed", C.c_uint64), ("device", C.c_int), ("reserved", C.c_int)]
+                ("seed", C.c_uint64), ("device", C.c_int), ("sample_device", C.c_int)]
 
 
 class TuneC(C.Structure):

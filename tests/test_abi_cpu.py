@@ -105,3 +105,16 @@ def test_evaluate_without_a_gpu_fails_loudly():
         G.evaluate_host(h, W, U, G.PREC_FP64)
     assert e.value.code == G.ERR_CUDA
     assert not U.any()
+
+
+def test_device_sampling_needs_a_generator_and_a_gpu():
+    w, K = _small()
+    with pytest.raises(G.GofmmError) as e:  # no GPU here: fails loudly, no host fallback
+        G.compress(G.Entries.gaussian(K.points, 0.3, 1e-3), G.default_params(leaf_size=32, sample_device=1))
+    assert e.value.code == G.ERR_CUDA
+    with pytest.raises(G.GofmmError) as e:
+        G.compress(G.Entries.callback(w.n, K), G.default_params(leaf_size=32, sample_device=1))
+    assert e.value.code == G.ERR_ARG
+    with pytest.raises(G.GofmmError) as e:
+        G.compress(G.Entries.gaussian(K.points, 0.3, 1e-3), G.default_params(leaf_size=32, sample_device=2))
+    assert e.value.code == G.ERR_ARG
