@@ -383,6 +383,7 @@ def serving_bench(G, torch, dev, works, handles, loads=(0.5, 0.8, 1.0)):
         lat = np.zeros(len(mats))
         i = done = 0
         waiting = []          # arrived, output not yet allocated (admission by free HBM)
+        inflight = []         # events of the steps the GPU may still be running
         used = 0
         t0 = _t.perf_counter()
         while done < len(mats):
@@ -402,8 +403,14 @@ def serving_bench(G, torch, dev, works, handles, loads=(0.5, 0.8, 1.0)):
                 used += need
                 waiting.pop(0)
             if pending:
+                # at most two steps in flight: the host prepares step k + 1
+                # while the GPU runs step k
                 eng.step(stream)
-                stream.synchronize()
+                ev = torch.cuda.Event()
+                ev.record(stream)
+                inflight.append(ev)
+                if len(inflight) > 2:
+                    inflight.pop(0).synchronize()
                 tnow = _t.perf_counter() - t0
                 for rid in list(pending):
                     if eng.poll(rid) == G.Engine.DONE:
@@ -413,6 +420,7 @@ def serving_bench(G, torch, dev, works, handles, loads=(0.5, 0.8, 1.0)):
                         done += 1
             elif i < len(mats):
                 _t.sleep(max(0.0, min(1e-3, arrivals[i] - now)))
+        stream.synchronize()
         return lat, _t.perf_counter() - t0
 
     run(np.zeros(len(mats)))  # warm-up (graphs, caches, allocator)

@@ -54,14 +54,6 @@ struct Engine {
     std::vector<EngineRequest*> finishing;  // completed on the host side, waiting for their event
     std::unordered_map<int64_t, int> state;  // 0 queued, 1 running, 2 done
     int64_t next_id = 1;
-    // tile upload ring
-    static constexpr int kRing = 4;
-    TcTile* h_tiles[kRing] = {};
-    TcTile* d_tiles[kRing] = {};
-    size_t tile_cap[kRing] = {};
-    cudaEvent_t ring_ev[kRing] = {};
-    bool ring_used[kRing] = {};
-    int ring_pos = 0;
     int* d_err = nullptr;
     int* h_err = nullptr;
     // statistics
@@ -155,12 +147,6 @@ Engine* engine_create(int device, int precision, int64_t pool_bytes) {
     E->pool_bytes = size_t(pool_bytes) / 256 * 256;
     E->pool = dalloc<uint8_t>(E->pool_bytes);
     E->free_blocks[0] = E->pool_bytes;
-    for (int i = 0; i < Engine::kRing; ++i) {
-        E->tile_cap[i] = 1 << 16;
-        CUDA_OK(cudaMallocHost(&E->h_tiles[i], E->tile_cap[i] * sizeof(TcTile)));
-        E->d_tiles[i] = dalloc<TcTile>(E->tile_cap[i]);
-        CUDA_OK(cudaEventCreateWithFlags(&E->ring_ev[i], cudaEventDisableTiming));
-    }
     E->d_err = dalloc<int>(1);
     CUDA_OK(cudaMemset(E->d_err, 0, sizeof(int)));
     CUDA_OK(cudaMallocHost(&E->h_err, sizeof(int)));
@@ -232,45 +218,26 @@ int64_t engine_step(Engine& E, cudaStream_t s) {
         if (q->next >= 1 && q->next <= int(q->T->launches.size())) gemm.push_back(q);
     for (size_t b0 = 0; b0 < gemm.size(); b0 += kMaxSegs) {
         const size_t nb = std::min<size_t>(kMaxSegs, gemm.size() - b0);
+        // every segment brings the device tile list its plan keeps for its
+        // launch and r (heaviest task first); the kernel maps a global tile
+        // index to its segment, so a step uploads and sorts nothing
         TcParams p{};
         p.nsegs = int(nb);
         p.err = E.d_err;
-        int piece = 0;
-        struct W8 {
-            int64_t w;
-            TcTile t;
-        };
-        std::vector<W8> tiles;
+        p.tiles = nullptr;
+        int piece = 0, total = 0;
         for (size_t k = 0; k < nb; ++k) {
             EngineRequest* q = gemm[b0 + k];
-            const TcLaunch& l = q->T->launches[q->next - 1];
+            TcLaunch& l = q->T->launches[q->next - 1];
             p.segs[k] = make_seg(*q->T, l, q->rt_hi, q->rt_lo, q->U, q->ldu, q->H->dev->d_idx, q->r);
+            const auto tl = launch_tiles(l, q->n_rtiles, q->H->tc_order[E.mode]);
+            p.segs[k].tiles = tl.first;
+            p.segs[k].tile_base = total;
+            total += tl.second;
             piece = std::max(piece, q->T->piece);
-            for (size_t t = 0; t < l.tasks.size(); ++t) {
-                const int64_t w = int64_t(l.tasks[t].nchunks) * l.tasks[t].n_pad + 1;
-                for (int rt = 0; rt < q->n_rtiles; ++rt) tiles.push_back(W8{w, TcTile{int32_t(k), int32_t(t), rt, 0}});
-            }
         }
-        // heaviest tiles first over the whole mix; r-tiles of a task stay adjacent
-        std::stable_sort(tiles.begin(), tiles.end(), [](const W8& a, const W8& b) { return a.w > b.w; });
-        const int slot = E.ring_pos;
-        E.ring_pos = (E.ring_pos + 1) % Engine::kRing;
-        if (E.ring_used[slot]) CUDA_OK(cudaEventSynchronize(E.ring_ev[slot]));  // staging slot free again
-        if (tiles.size() > E.tile_cap[slot]) {
-            CUDA_OK(cudaFreeHost(E.h_tiles[slot]));
-            dfree(E.d_tiles[slot]);
-            E.tile_cap[slot] = tiles.size() * 2;
-            CUDA_OK(cudaMallocHost(&E.h_tiles[slot], E.tile_cap[slot] * sizeof(TcTile)));
-            E.d_tiles[slot] = dalloc<TcTile>(E.tile_cap[slot]);
-        }
-        for (size_t i = 0; i < tiles.size(); ++i) E.h_tiles[slot][i] = tiles[i].t;
-        CUDA_OK(cudaMemcpyAsync(E.d_tiles[slot], E.h_tiles[slot], tiles.size() * sizeof(TcTile),
-                                cudaMemcpyHostToDevice, s));
-        p.tiles = E.d_tiles[slot];
-        p.ntiles = int(tiles.size());
+        p.ntiles = total;
         launch_gemm_mode(E.mode, piece, p, E.num_sms, s);
-        CUDA_OK(cudaEventRecord(E.ring_ev[slot], s));
-        E.ring_used[slot] = true;
         ++E.launches;
     }
     CUDA_OK(cudaMemcpyAsync(E.h_err, E.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -356,11 +323,6 @@ void engine_destroy(Engine* E) {
         if (q->done_ev) cudaEventDestroy(q->done_ev);
         --q->H->inflight;
         delete q;
-    }
-    for (int i = 0; i < Engine::kRing; ++i) {
-        if (E->h_tiles[i]) cudaFreeHost(E->h_tiles[i]);
-        dfree(E->d_tiles[i]);
-        if (E->ring_ev[i]) cudaEventDestroy(E->ring_ev[i]);
     }
     dfree(E->pool);
     dfree(E->d_err);

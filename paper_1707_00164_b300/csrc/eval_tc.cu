@@ -188,6 +188,17 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// Tile t of a launch: from the merged list, or (segment tile lists) from the
+// list of the segment whose range holds t.
+__device__ __forceinline__ TcTile fetch_tile(const TcParams& p, int t) {
+    if (p.tiles) return p.tiles[t];
+    int k = 0;
+    while (k + 1 < p.nsegs && t >= p.segs[k + 1].tile_base) ++k;
+    TcTile tt = p.segs[k].tiles[t - p.segs[k].tile_base];
+    tt.seg = k;
+    return tt;
+}
+
 // Epilogue of one tile: the accumulator rows of this thread (one column j
 // of r) for the task's n_pad block rows, read from TMEM at taddr and written
 // as U rows (scattered to the original order, FP32) or as the next stage's
@@ -347,7 +358,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
                     t += gridDim.x;
                 }
                 if (t >= ntiles) break;
-                const TcTile tt = p.tiles[t];
+                const TcTile tt = fetch_tile(p, t);
                 const TcSeg& sg = p.segs[tt.seg];
                 const TcTask tk = sg.tasks[tt.task];
                 const int rt = tt.rt;
@@ -407,7 +418,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
                     if (t < 0) break;
                 }
                 if (t >= ntiles) break;
-                const TcTile tt = p.tiles[t];
+                const TcTile tt = fetch_tile(p, t);
                 const TcTask tk = p.segs[tt.seg].tasks[tt.task];
                 const int acc = i & 1;
                 if (!mbar_wait(tempty_bar(acc), uint32_t(((i >> 1) & 1) ^ 1), p.err, kErrMma)) break;
@@ -455,7 +466,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
                 if (t < 0) break;
             }
             if (t >= ntiles) break;
-            const TcTile tt = p.tiles[t];
+            const TcTile tt = fetch_tile(p, t);
             const TcSeg& sg = p.segs[tt.seg];
             const TcTask tk = sg.tasks[tt.task];
             const int rt = tt.rt;
@@ -654,7 +665,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
             uint32_t phase = 0;
             bool ok = true;
             for (int t = pair; t < ntiles && ok; t += npairs) {
-                const TcTile tt = p.tiles[t];
+                const TcTile tt = fetch_tile(p, t);
                 const TcSeg& sg = p.segs[tt.seg];
                 const TcTask tk = sg.tasks[tt.task];
                 const int rt = 2 * tt.rt + int(crank);
@@ -702,7 +713,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
             uint32_t phase = 0;
             bool ok = true;
             for (int t = pair; t < ntiles && ok; t += npairs, ++i) {
-                const TcTile tt = p.tiles[t];
+                const TcTile tt = fetch_tile(p, t);
                 const TcTask tk = p.segs[tt.seg].tasks[tt.task];
                 const int acc = i & 1;
                 if (!mbar_wait_cluster(tempty_bar(acc), uint32_t(((i >> 1) & 1) ^ 1), p.err, kErrMma)) break;
@@ -743,7 +754,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
             uint32_t phase = 0;
             bool ok = true;
             for (int t = pair; t < ntiles && ok; t += npairs) {
-                const TcTile tt = p.tiles[t];
+                const TcTile tt = fetch_tile(p, t);
                 const TcTask tk = p.segs[tt.seg].tasks[tt.task];
                 for (int q = 0; q < tk.nchunks; ++q) {
                     if (!mbar_wait(full_bar(stage), phase, p.err, kErrMma)) { ok = false; break; }
@@ -759,7 +770,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
         const uint32_t tempty_leader = peer_addr(tempty_bar(0), 0);  // + 8 bytes for accumulator 1
         int i = 0;
         for (int t = pair; t < ntiles; t += npairs, ++i) {
-            const TcTile tt = p.tiles[t];
+            const TcTile tt = fetch_tile(p, t);
             const TcSeg& sg = p.segs[tt.seg];
             const TcTask tk = sg.tasks[tt.task];
             const int rt = 2 * tt.rt + int(crank);
@@ -1186,7 +1197,7 @@ static void set_smem_attr() {
 // share most of their far or near lists and re-read operands from L2.
 // With pair = true the list holds pairs of r-tiles (rt = pair index) for the
 // SM-pair kernel.
-static std::pair<TcTile*, int> launch_tiles(TcLaunch& l, int n_rtiles, int order, bool pair = false) {
+std::pair<TcTile*, int> launch_tiles(TcLaunch& l, int n_rtiles, int order, bool pair) {
     if (pair) n_rtiles = (n_rtiles + 1) / 2;
     const int key = n_rtiles * 4 + (order == GOFMM_ORDER_LOCAL ? 1 : 0) + (pair ? 2 : 0);
     auto it = l.tiles.find(key);
@@ -1252,8 +1263,10 @@ TcPrec& tc_plan(Handle& H, DeviceState& D, int precision) {
 void tc_prepare(Handle& H, DeviceState& D, int64_t r_max, int precision) {
     TcPrec* T = &tc_plan(H, D, precision);
     const int64_t r_pad = (r_max + 127) / 128 * 128;
+    // every r-tile count up to the prepared one (the serving engine mixes r)
     for (TcLaunch& l : T->launches)
-        launch_tiles(l, int(r_pad / 128), H.tc_order[T->mode], H.tc_schedule[T->mode] == GOFMM_SCHED_PAIR);
+        for (int nrt = 1; nrt <= int(r_pad / 128); ++nrt)
+            launch_tiles(l, nrt, H.tc_order[T->mode], H.tc_schedule[T->mode] == GOFMM_SCHED_PAIR);
     TcFused& F = T->fused;
     if (F.counters_nrt < int(r_pad / 128)) {
         dfree(F.d_counters);

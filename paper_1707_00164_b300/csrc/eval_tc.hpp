@@ -35,6 +35,10 @@ struct TcTask {
     int32_t out_cols;  // RT outputs: columns of the output segment this task writes (zeros past m)
 };
 
+struct TcTile {
+    int32_t seg, task, rt, pad;
+};
+
 // One (evaluation, launch) pair inside a tensor-core launch: the tasks and
 // slabs of that launch of one compressed matrix, its B tiles, the RT buffers
 // of that evaluation, and its output.
@@ -50,16 +54,14 @@ struct TcSeg {
     int64_t ldu;
     const int64_t* perm;
     int32_t r;
-    int32_t pad;
+    int32_t tile_base;    // segment tile lists: first global tile index of this segment
+    const TcTile* tiles;  // segment tile lists (TcParams::tiles == nullptr): this segment's tiles
 };
 constexpr int kMaxSegs = 64;  // segments per launch (kernel parameters, by value)
 
-struct TcTile {
-    int32_t seg, task, rt, pad;
-};
 
 struct TcParams {
-    const TcTile* tiles;
+    const TcTile* tiles;  // merged tile list; nullptr: every segment brings its own (TcSeg::tiles)
     int ntiles;
     int nsegs;
     int* err;
@@ -142,6 +144,8 @@ TcPrec& tc_plan(Handle& H, DeviceState& D, int precision);  // plan + B tiles (a
 TcSeg make_seg(const TcPrec& T, const TcLaunch& l, uint8_t* const* rt_hi, uint8_t* const* rt_lo, float* U,
                int64_t ldu, const int64_t* perm, int r);
 void launch_gemm_mode(int mode, int piece, const TcParams& p, int num_sms, cudaStream_t s);
+// device tile list of one launch alone for n_rtiles r-tiles (cached in the launch)
+std::pair<TcTile*, int> launch_tiles(TcLaunch& l, int n_rtiles, int order, bool pair = false);
 void tc_drop_plan(DeviceState& D, int precision);  // frees one mode's plan, stores and buffers
 void launch_gather(int mode, const TcPrec& T, const float* W, int64_t ldw, const int64_t* perm, uint8_t* wt_hi,
                    uint8_t* wt_lo, int r, cudaStream_t s);
