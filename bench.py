@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched form")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
     ap.add_argument("--no-precision", action="store_true", help="skip the precision workload")
+    ap.add_argument("--no-generated", action="store_true",
+                    help="skip the run without cached blocks (entries generated in the kernels)")
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default tensor-core configuration instead of autotuning it")
     ap.add_argument("--config", default="",
@@ -570,10 +572,13 @@ def native_arm(args):
     golden = np.load(GOLDEN) if (os.path.exists(GOLDEN) and w is WORKLOAD and rank == 0) else None
 
     def accuracy(pr):
+        return accuracy_of(h, pr)
+
+    def accuracy_of(hh, pr):
         if golden is None:
             return None
-        G.evaluate(h, W, U, pr, stream)
-        G.synchronize(h, stream)
+        G.evaluate(hh, W, U, pr, stream)
+        G.synchronize(hh, stream)
         g = golden
         got = U[torch.from_numpy(g["rows"]).to(dev)][:, : g["u_oracle"].shape[1]].double().cpu().numpy()
         return {"eps2_vs_oracle_fp64": float(np.linalg.norm(got - g["u_oracle"]) / np.linalg.norm(g["u_oracle"])),
@@ -669,6 +674,36 @@ def native_arm(args):
         dense = dense_reference(torch, K, W, dev)
 
     bg.join()
+    # the same matrix with no cached blocks (GOFMM_CACHE_NONE): every K block
+    # generated inside the GEMM kernels, on the tensor cores (split BF16x3,
+    # autotuned) and on the CUDA cores (plain FP32)
+    generated = None
+    if rank == 0 and world == 1 and not args.n and not args.no_generated:
+        try:
+            hg = G.compress(entries, G.default_params(**w.params(), device=local, cache_mode=G.CACHE_NONE))
+            generated = {"cache": "none: block entries generated in the GEMM kernels"}
+            for name in ("bf16x3", "fp32"):
+                pr = G.PRECISIONS[name]
+                G.prepare(hg, r, pr)
+                tg = G.autotune(hg, r, pr, None, stream) if name != "fp32" else None
+                for _ in range(2):
+                    G.evaluate(hg, W, U, pr, stream)
+                G.synchronize(hg, stream)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                nst = max(3, min(args.steps, 10))
+                a.record(stream)
+                for _ in range(nst):
+                    G.evaluate(hg, W, U, pr, stream)
+                b.record(stream)
+                G.synchronize(hg, stream)
+                gms = a.elapsed_time(b) / nst
+                ent = {"ms": gms, "value": w.n * r / (gms / 1e3), "accuracy": accuracy_of(hg, pr)}
+                if tg is not None:
+                    ent["config"] = {k: tg[k] for k in ("piece", "schedule", "order")}
+                generated[name] = ent
+            G.free(hg)
+        except Exception as e:
+            generated = {"error": repr(e)[:300]}
     # compression of the throughput workload with the sampled blocks K_{I'a}
     # generated on the host and on the GPU (not part of any timed number)
     compression = None
@@ -718,7 +753,7 @@ def native_arm(args):
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches * args.steps,
             "autotune": tune, "accuracy": acc, "modes": modes, "dense_cublas": dense, "precision_workload": precision, "batching": batching,
             "serving": serving,
-            "compress_seconds": round(compress_s, 2), "compression": compression,
+            "compress_seconds": round(compress_s, 2), "compression": compression, "generated_blocks": generated,
             "structure": {k: st[k] for k in ("depth", "mean_rank", "max_rank", "near_pairs", "far_pairs",
                                               "near_entries", "far_entries")},
         }))

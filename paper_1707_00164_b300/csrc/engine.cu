@@ -226,6 +226,7 @@ int64_t engine_step(Engine& E, cudaStream_t s) {
         p.err = E.d_err;
         p.tiles = nullptr;
         int piece = 0, total = 0;
+        bool gen = false;
         for (size_t k = 0; k < nb; ++k) {
             EngineRequest* q = gemm[b0 + k];
             TcLaunch& l = q->T->launches[q->next - 1];
@@ -235,9 +236,10 @@ int64_t engine_step(Engine& E, cudaStream_t s) {
             p.segs[k].tile_base = total;
             total += tl.second;
             piece = std::max(piece, q->T->piece);
+            gen = gen || q->T->gen;
         }
         p.ntiles = total;
-        launch_gemm_mode(E.mode, piece, p, E.num_sms, s);
+        launch_gemm_mode(E.mode, piece, p, E.num_sms, s, gen);
         ++E.launches;
     }
     CUDA_OK(cudaMemcpyAsync(E.h_err, E.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -356,6 +358,7 @@ struct BatchStep {
         TcTile* d_tiles = nullptr;
         int ntiles = 0;
         int piece = 0;  // tallest task piece of the segments' plans
+        bool gen = false;  // some segment generates its block tiles
     };
     std::vector<Launch> launches;
 };
@@ -434,6 +437,7 @@ Batch* batch_create(Handle* const* hs, const int64_t* r, int count, int precisio
                 const TcLaunch& l = B->items[i].T->launches[next[i] - 1];
                 bl.segs.emplace_back(i, next[i] - 1);
                 bl.piece = std::max(bl.piece, B->items[i].T->piece);
+                bl.gen = bl.gen || B->items[i].T->gen;
                 for (size_t t = 0; t < l.tasks.size(); ++t) {
                     const int64_t w = int64_t(l.tasks[t].nchunks) * l.tasks[t].n_pad + 1;
                     for (int rt = 0; rt < B->items[i].n_rtiles; ++rt)
@@ -482,7 +486,7 @@ static void batch_launch(Batch& B, const float* const* W, const int64_t* ldw, fl
                 p.segs[k] = make_seg(*it.T, it.T->launches[bl.segs[k].second], it.rt_hi, it.rt_lo, U[i], ldu[i],
                                      it.H->dev->d_idx, it.r);
             }
-            launch_gemm_mode(B.mode, bl.piece, p, B.num_sms, s);
+            launch_gemm_mode(B.mode, bl.piece, p, B.num_sms, s, bl.gen);
         }
     }
     CUDA_OK(cudaMemcpyAsync(B.h_err, B.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -48,7 +48,37 @@ int mode_of(int precision) {
 namespace {
 
 constexpr long long kSpinLimit = 2000000000LL;  // clock cycles (about a second) before a wait gives up
-constexpr int kErrProducer = 1, kErrMma = 2, kErrEpilogue = 3, kErrDependency = 4, kErrTmemPair = 5;
+constexpr int kErrProducer = 1, kErrMma = 2, kErrEpilogue = 3, kErrDependency = 4, kErrTmemPair = 5,
+              kErrGenerator = 6;
+constexpr int kGenWarps = 8;      // generator warps of the in-kernel entry generation
+// their shared-memory area: job ring, barriers and flags (1 KB), the row
+// points of the current task piece (256 x 16 floats), one chunk's column
+// points (64 x 16 floats)
+constexpr int kGenSmem = 1024 + (kMaxN + 64) * kGenMaxDpad * 4;
+
+// Named barrier 1 over the eight generator warps.
+__device__ __forceinline__ void gen_bar_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kGenWarps * 32) : "memory");
+}
+// ... and its reduction form: true iff every generator thread passes true.
+__device__ __forceinline__ int gen_bar_and(bool pred) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, %2, p;\n\tselp.b32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(int(pred)), "n"(kGenWarps * 32)
+        : "memory");
+    return r;
+}
+
+// One chunk of a generated block tile: rows perm[rows .. rows + m) (the
+// rest of the n_pad rows zero), columns perm[cols .. cols + kvalid) (the rest
+// of the chunk zero), written into stage `stage`.
+struct GenJob {
+    int64_t rows, cols;
+    int32_t seg, stage, m, kvalid, n_pad, stop;
+};
 
 // NMAX: the tallest task piece the kernel accepts (MMA N ceiling, 128 or
 // 256).  A stage holds one 128 x 128 B tile of right-hand sides and one
@@ -290,12 +320,23 @@ __device__ __forceinline__ void write_tile(const TcSeg& sg, const TcTask& tk, in
 // ring runs on across tiles and the accumulator is double-buffered in TMEM
 // (2 x 256 columns), so the epilogue of one tile overlaps the MMAs of the
 // next.
-template <int MODE, int NMAX>
-__global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
+template <int MODE, int NMAX, bool GEN>
+__global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
     using C = Cfg<MODE, NMAX>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + C::kStages * C::kStageBytes);
+    // generation (GEN): job ring from the producer to the generator warps,
+    // per-stage "block tile written" barriers, per-stage generated flags
+    uint8_t* gen_area = base + C::kStages * C::kStageBytes + 256;
+    uint64_t* gbars = reinterpret_cast<uint64_t*>(gen_area);
+    uint8_t* stage_isgen = gen_area + 3 * 8 * C::kStages;
+    GenJob* jobs = reinterpret_cast<GenJob*>(gen_area + 256);
+    float* rowpts = reinterpret_cast<float*>(gen_area + 1024);
+    float* colpts = rowpts + kMaxN * kGenMaxDpad;
+    auto genq_full = [&](int j) { return smem_u32(&gbars[j]); };
+    auto genq_empty = [&](int j) { return smem_u32(&gbars[C::kStages + j]); };
+    auto gen_done = [&](int s) { return smem_u32(&gbars[2 * C::kStages + s]); };
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::kStages + 9);
     int* tid_slot = reinterpret_cast<int*>(tmem_slot + 1);  // [2]: tile ids handed from producer to consumers
     const uint32_t s_base = smem_u32(base);
@@ -328,6 +369,13 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
             mbar_init(idfull_bar(a), 1);
             mbar_init(idempty_bar(a), 5);  // MMA thread + four epilogue warps
         }
+        if constexpr (GEN) {
+            for (int j = 0; j < C::kStages; ++j) {
+                mbar_init(genq_full(j), 1);        // the producer posts a job
+                mbar_init(genq_empty(j), kGenWarps);  // every generator warp is done with it
+                mbar_init(gen_done(j), kGenWarps);    // every generator warp wrote its part of the stage
+            }
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -344,7 +392,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
     if (warp == 0) {
         if (lane == 0) {
             // ---- producer: stream chunk tiles of every tile of this CTA
-            int stage = 0, issued = 0;
+            int stage = 0, issued = 0, gseq = 0;
             uint32_t phase = 0;
             bool ok = true;
             for (int i = 0, t = blockIdx.x; ok; ++i) {
@@ -375,9 +423,49 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
                     const TcSlab sl = sg.slabs[si];
                     const int64_t a_off = (int64_t(rt) * sg.rt_chunks[sl.a_buf] + sl.a_chunk0) * kTileBytes;
                     const uint8_t* a_hi = sg.rt_hi[sl.a_buf] + a_off;
+                    if constexpr (GEN) {
+                        if (sl.gen) {
+                            // block tiles generated by the generator warps; only
+                            // the right-hand-side tiles are copied
+                            for (int c = 0; c < sl.nchunks; ++c) {
+                                if (!mbar_wait(empty_bar(stage), phase ^ 1u, p.err, kErrProducer)) { ok = false; break; }
+                                const int j = gseq % C::kStages;
+                                if (!mbar_wait(genq_empty(j), uint32_t(((gseq / C::kStages) & 1) ^ 1), p.err,
+                                               kErrProducer)) { ok = false; break; }
+                                GenJob& jb = jobs[j];
+                                jb.rows = sl.b_off;
+                                jb.cols = sl.gen_cols + int64_t(c) * C::kKc;
+                                jb.seg = tt.seg;
+                                jb.stage = stage;
+                                jb.m = tk.m;
+                                jb.kvalid = min(C::kKc, sl.k - c * C::kKc);
+                                jb.n_pad = tk.n_pad;
+                                jb.stop = 0;
+                                mbar_arrive(genq_full(j));
+                                ++gseq;
+                                stage_isgen[stage] = 1;
+                                mbar_expect_tx(full_bar(stage), (C::kSplit ? 2u : 1u) * kTileBytes);
+                                bulk_g2s(sA(stage, 0), a_hi + int64_t(c) * kTileBytes, kTileBytes, full_bar(stage));
+                                if constexpr (C::kSplit)
+                                    bulk_g2s(sA(stage, 1), sg.rt_lo[sl.a_buf] + a_off + int64_t(c) * kTileBytes,
+                                             kTileBytes, full_bar(stage));
+                                ++issued;
+                                if (++stage == C::kStages) { stage = 0; phase ^= 1u; }
+                            }
+                            continue;
+                        }
+                    }
+                    if constexpr (!GEN) {
+                        if (sl.gen) {  // the host launches the generator variant for these; never read as tiles
+                            atomicCAS(p.err, 0, kErrGenerator);
+                            ok = false;
+                            break;
+                        }
+                    }
                     const uint8_t* b_hi = sg.b_hi + sl.b_off;
                     for (int c = 0; c < sl.nchunks; ++c) {
                         if (!mbar_wait(empty_bar(stage), phase ^ 1u, p.err, kErrProducer)) { ok = false; break; }
+                        if constexpr (GEN) stage_isgen[stage] = 0;
                         mbar_expect_tx(full_bar(stage), (C::kSplit ? 2u : 1u) * (kTileBytes + b_bytes));
                         bulk_g2s(sA(stage, 0), a_hi + int64_t(c) * kTileBytes, kTileBytes, full_bar(stage));
                         bulk_g2s(sB(stage, 0), b_hi + int64_t(c) * b_bytes, b_bytes, full_bar(stage));
@@ -390,6 +478,14 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
                         ++issued;
                         if (++stage == C::kStages) { stage = 0; phase ^= 1u; }
                     }
+                }
+            }
+            if constexpr (GEN) {
+                // release the generator warps (bounded: they may have stopped on an error)
+                const int j = gseq % C::kStages;
+                if (mbar_wait(genq_empty(j), uint32_t(((gseq / C::kStages) & 1) ^ 1), p.err, kErrProducer)) {
+                    jobs[j].stop = 1;
+                    mbar_arrive(genq_full(j));
                 }
             }
             if (!ok) {
@@ -408,7 +504,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
         if (lane == 0) {
             // ---- MMA issuer (one thread)
             int stage = 0, i = 0;
-            uint32_t phase = 0;
+            uint32_t phase = 0, genpar = 0;
             bool ok = true;
             for (int t = blockIdx.x; ok; t += gridDim.x, ++i) {
                 if (dyn) {
@@ -427,6 +523,15 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
                 const uint32_t idesc = make_idesc(MODE == TC_TF32 ? 2 : 1, tk.n_pad);
                 for (int q = 0; q < tk.nchunks; ++q) {
                     if (!mbar_wait(full_bar(stage), phase, p.err, kErrMma)) { ok = false; break; }
+                    if constexpr (GEN) {
+                        if (stage_isgen[stage]) {  // block tile written by the generator warps
+                            if (!mbar_wait(gen_done(stage), (genpar >> stage) & 1u, p.err, kErrMma)) {
+                                ok = false;
+                                break;
+                            }
+                            genpar ^= 1u << stage;
+                        }
+                    }
                     tc_fence_after();
                     const uint64_t da = sw128_desc(sA(stage, 0)), db = sw128_desc(sB(stage, 0));
 #pragma unroll
@@ -450,7 +555,7 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
             while (!mbar_try_wait(drain_bar, 0) && clock64() - t0 < kSpinLimit) {
             }
         }
-    } else {
+    } else if (warp < 6) {
         // ---- epilogue: warps 2..5 own TMEM lane quarters (warp % 4)
         const int q4 = warp & 3;
         const int row = q4 * 32 + lane;  // row of the MMA tile = column of r
@@ -497,6 +602,112 @@ __global__ void __launch_bounds__(192, 1) tc_gemm_kernel(const __grid_constant__
                         if (s0 >= 0) atomicAdd(p.counters + int64_t(s0) * p.dep_nrt + rt, 1);
                         if (s1 >= 0) atomicAdd(p.counters + int64_t(s1) * p.dep_nrt + rt, 1);
                     }
+                }
+            }
+        }
+    } else {
+        if constexpr (GEN) {
+            // ---- generator warps 6..13: block tiles of generated slabs,
+            // written into the stage's B region in the MMA layout (row n,
+            // 16-byte group g of 8 BF16 / 4 TF32 columns, 128-byte swizzle).
+            // The eight warps work on one chunk at a time (named barrier 1):
+            // the task piece's row points stay in shared memory across its
+            // chunks, each chunk brings its column points.
+            const int gt = threadIdx.x - 192;
+            int64_t cur_rows = -1;
+            int cur_seg = -1;
+            for (int seq = 0;; ++seq) {
+                const int j = seq % C::kStages;
+                bool ok = true;
+                if (lane == 0) ok = mbar_wait(genq_full(j), uint32_t((seq / C::kStages) & 1), p.err, kErrGenerator);
+                ok = __shfl_sync(0xffffffffu, ok, 0) != 0;  // lane 0 waited for the whole warp
+                __syncwarp();
+                const int all_ok = gen_bar_and(ok);
+                if (!all_ok) break;
+                const GenJob jb = jobs[j];
+                if (jb.stop) break;
+                const TcSeg& sg = p.segs[jb.seg];
+                const int dp = sg.dpad;
+                const float4* tab = reinterpret_cast<const float4*>(sg.pts);
+                if (jb.rows != cur_rows || jb.seg != cur_seg) {
+                    // row points transposed (coordinate-major), so the 32
+                    // rows a warp handles read 32 consecutive words
+                    for (int e = gt; e < jb.m * dp / 4; e += kGenWarps * 32) {
+                        const float4 x = tab[jb.rows * (dp / 4) + e];
+                        const int n = e / (dp / 4), d0 = (e % (dp / 4)) * 4;
+                        rowpts[(d0 + 0) * kMaxN + n] = x.x;
+                        rowpts[(d0 + 1) * kMaxN + n] = x.y;
+                        rowpts[(d0 + 2) * kMaxN + n] = x.z;
+                        rowpts[(d0 + 3) * kMaxN + n] = x.w;
+                    }
+                    cur_rows = jb.rows;
+                    cur_seg = jb.seg;
+                }
+                for (int e = gt; e < jb.kvalid * dp / 4; e += kGenWarps * 32)
+                    reinterpret_cast<float4*>(colpts)[e] = tab[jb.cols * (dp / 4) + e];
+                gen_bar_sync();  // points in shared memory
+                uint8_t* bh = base + jb.stage * C::kStageBytes + kTileBytes;
+                uint8_t* bl = bh + kTileBytes + NMAX * 128;  // split BF16x3: the lo copy of the stage
+                constexpr int kPer = MODE == TC_TF32 ? 4 : 8;  // columns per 16-byte group
+                for (int it = gt; it < jb.n_pad * 8; it += kGenWarps * 32) {
+                    // a warp: 32 consecutive rows of one column group (the
+                    // column points are then the same word for the whole warp)
+                    const int n = it % jb.n_pad, g = it / jb.n_pad;
+                    float v[kPer];
+#pragma unroll
+                    for (int e = 0; e < kPer; ++e) v[e] = 0.f;
+                    if (n < jb.m) {
+                        // the row point in registers; coordinates past dim are
+                        // zero in both points, so all dp of them can be summed
+                        float xr[kGenMaxDpad];
+#pragma unroll
+                        for (int d = 0; d < kGenMaxDpad; ++d) xr[d] = d < dp ? rowpts[d * kMaxN + n] : 0.f;
+#pragma unroll
+                        for (int e = 0; e < kPer; ++e) {
+                            const int k = g * kPer + e;
+                            const float4* cp = reinterpret_cast<const float4*>(colpts + k * dp);
+                            float acc = 0.f;
+#pragma unroll
+                            for (int q4 = 0; q4 < kGenMaxDpad / 4; ++q4) {
+                                if (q4 * 4 < dp) {
+                                    const float4 c = cp[q4];  // the same address for the whole warp
+                                    const float t0 = xr[4 * q4] - c.x, t1 = xr[4 * q4 + 1] - c.y;
+                                    const float t2 = xr[4 * q4 + 2] - c.z, t3 = xr[4 * q4 + 3] - c.w;
+                                    acc += t0 * t0 + t1 * t1 + t2 * t2 + t3 * t3;
+                                }
+                            }
+                            if (k < jb.kvalid) {
+                                float x = sg.gen_kind == GOFMM_GEN_GAUSSIAN ? __expf(-acc * sg.gen_inv)
+                                                                           : rsqrtf(1.f + acc * sg.gen_inv);
+                                if (jb.rows + n == jb.cols + k) x += sg.gen_shift;  // the same index: K_ii
+                                v[e] = x;
+                            }
+                        }
+                    }
+                    const uint32_t pos = swz(uint32_t(n), uint32_t(g * 16));
+                    if constexpr (MODE == TC_TF32) {
+                        *reinterpret_cast<float4*>(bh + pos) =
+                            make_float4(round_tf32(v[0]), round_tf32(v[1]), round_tf32(v[2]), round_tf32(v[3]));
+                    } else {
+                        uint4 oh, ol;
+                        __nv_bfloat16* hh = reinterpret_cast<__nv_bfloat16*>(&oh);
+                        __nv_bfloat16* ll = reinterpret_cast<__nv_bfloat16*>(&ol);
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            hh[e] = __float2bfloat16_rn(v[e]);
+                            ll[e] = __float2bfloat16_rn(v[e] - __bfloat162float(hh[e]));
+                        }
+                        *reinterpret_cast<uint4*>(bh + pos) = oh;
+                        if constexpr (C::kSplit) *reinterpret_cast<uint4*>(bl + pos) = ol;
+                    }
+                }
+                gen_bar_sync();  // every warp done with this chunk's points before the next overwrites them
+                // generic writes -> visible to the MMAs (async proxy)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(gen_done(jb.stage));
+                    mbar_arrive(genq_empty(j));
                 }
             }
         }
@@ -674,6 +885,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
                 const uint32_t a_bytes = live ? uint32_t(kTileBytes) : 0u;
                 for (int si = tk.slab0; si < tk.slab1 && ok; ++si) {
                     const TcSlab sl = sg.slabs[si];
+                    if (sl.gen) {  // the pair schedule runs cached blocks only (the host refuses generated plans)
+                        atomicCAS(p.err, 0, kErrGenerator);
+                        ok = false;
+                        break;
+                    }
                     const int64_t a_off = (int64_t(rt) * sg.rt_chunks[sl.a_buf] + sl.a_chunk0) * kTileBytes;
                     const int64_t b_row = int64_t(tk.n_pad) * 128;
                     const int64_t b_off = sl.b_off + int64_t(crank) * half;
@@ -1089,10 +1305,23 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
                 tt.out_cols = okind == OUT_U ? tt.n_pad : int32_t(std::min<int64_t>(P, padk(t.m) - q * P));
                 for (int si = t.slab0; si < t.slab1; ++si) {
                     const Slab& s = l.slabs[si];
-                    if (s.a_src == A_GEN)
-                        fail(GOFMM_ERR_UNSUPPORTED, "tensor-core precisions need cached K blocks (GOFMM_CACHE_BLOCKS)");
                     TcSlab ts{};
                     ts.a_buf = s.b_src;
+                    if (s.a_src == A_GEN) {
+                        // block entries generated in the kernel from the row
+                        // list (this piece's rows) and the column list
+                        const int64_t a = s.b_src == B_WT ? leaf_at_pos.at(s.b_row) : node_at_skel.at(s.b_row);
+                        ts.a_chunk0 = int32_t(s.b_src == B_WT ? leaf_chunk[a] : node_chunk[a]);
+                        ts.nchunks = int32_t(padk(s.k) / kc);
+                        ts.gen = 1;
+                        ts.b_off = s.a_off + q * P;
+                        ts.gen_cols = s.a_col;
+                        ts.k = s.k;
+                        T.gen = true;
+                        tt.nchunks += ts.nchunks;
+                        tl.slabs.push_back(ts);
+                        continue;
+                    }
                     int64_t ksplit = s.k, kgap = 0, kpad;
                     if (s.b_src == B_WT) {
                         const int64_t a = leaf_at_pos.at(s.b_row);
@@ -1159,7 +1388,15 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
                 const TcSlab& sl = l.slabs[si];
                 check(sl.a_buf >= 0 && sl.a_buf < 3, "operand buffer");
                 check(sl.a_chunk0 >= 0 && sl.a_chunk0 + sl.nchunks <= chunks[sl.a_buf], "operand chunks");
-                check(sl.b_off % 16 == 0 && sl.b_off + int64_t(sl.nchunks) * t.n_pad * 128 <= T.b_bytes, "B tiles");
+                if (sl.gen) {
+                    const int64_t n_idx = st.n + D.S_tot;
+                    check(sl.b_off >= 0 && sl.b_off + t.m <= n_idx && sl.gen_cols >= 0 && sl.gen_cols + sl.k <= n_idx &&
+                              sl.k >= 1 && int64_t(sl.nchunks) * kc >= sl.k && int64_t(sl.nchunks - 1) * kc < sl.k,
+                          "generated slab");
+                } else {
+                    check(sl.b_off % 16 == 0 && sl.b_off + int64_t(sl.nchunks) * t.n_pad * 128 <= T.b_bytes,
+                          "B tiles");
+                }
                 total += sl.nchunks;
             }
             check(total == t.nchunks, "chunk count");
@@ -1180,10 +1417,14 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
 
 template <int MODE>
 static void set_smem_attr() {
-    CUDA_OK(cudaFuncSetAttribute(tc_gemm_kernel<MODE, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CUDA_OK(cudaFuncSetAttribute(tc_gemm_kernel<MODE, 256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  Cfg<MODE, 256>::kSmem));
-    CUDA_OK(cudaFuncSetAttribute(tc_gemm_kernel<MODE, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CUDA_OK(cudaFuncSetAttribute(tc_gemm_kernel<MODE, 128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  Cfg<MODE, 128>::kSmem));
+    CUDA_OK(cudaFuncSetAttribute(tc_gemm_kernel<MODE, 256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 Cfg<MODE, 256>::kSmem + kGenSmem));
+    CUDA_OK(cudaFuncSetAttribute(tc_gemm_kernel<MODE, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 Cfg<MODE, 128>::kSmem + kGenSmem));
     CUDA_OK(cudaFuncSetAttribute(tc_gemm_pair_kernel<MODE, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  Cfg2<MODE, 256>::kSmem));
     CUDA_OK(cudaFuncSetAttribute(tc_gemm_pair_kernel<MODE, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1230,6 +1471,22 @@ TcPrec& tc_plan(Handle& H, DeviceState& D, int precision) {
         t->piece = H.tc_piece[mode];
         std::vector<TileJob> jobs;
         build_tc_plan(H.st, D, *t, jobs);
+        if (t->gen) {
+            // point table in index-list order for the generator warps
+            if (H.K.dim > kGenMaxDpad)
+                fail(GOFMM_ERR_UNSUPPORTED, "in-kernel generation on the tensor cores supports at most 16 coordinates");
+            const int dp = (H.K.dim + 3) / 4 * 4;
+            std::vector<float> tab(D.idx.size() * size_t(dp), 0.f);
+            for (size_t q = 0; q < D.idx.size(); ++q)
+                for (int d = 0; d < H.K.dim; ++d)
+                    tab[q * size_t(dp) + size_t(d)] = float(H.K.pts[size_t(D.idx[q]) * size_t(H.K.dim) + size_t(d)]);
+            t->gen_pts = dupload(tab);
+            t->gen_dim = H.K.dim;
+            t->gen_dpad = dp;
+            t->gen_kind = H.K.kind;
+            t->gen_inv = float(H.K.kind == GOFMM_GEN_GAUSSIAN ? 1.0 / (2.0 * H.K.h * H.K.h) : 1.0 / (H.K.h * H.K.h));
+            t->gen_shift = float(H.K.shift);
+        }
         t->b_hi = dalloc<uint8_t>(size_t(std::max<int64_t>(t->b_bytes, 16)));
         if (t->split) t->b_lo = dalloc<uint8_t>(size_t(std::max<int64_t>(t->b_bytes, 16)));
         if (!jobs.empty()) {
@@ -1320,44 +1577,58 @@ TcSeg make_seg(const TcPrec& T, const TcLaunch& l, uint8_t* const* rt_hi, uint8_
     g.ldu = ldu;
     g.perm = perm;
     g.r = r;
+    g.pts = T.gen_pts;
+    g.dim = T.gen_dim;
+    g.dpad = T.gen_dpad;
+    g.gen_kind = T.gen_kind;
+    g.gen_inv = T.gen_inv;
+    g.gen_shift = T.gen_shift;
     return g;
 }
 
-template <int MODE, int NMAX>
+template <int MODE, int NMAX, bool GEN>
 static void launch_gemm(const TcParams& p, int num_sms, cudaStream_t s) {
     const int grid = std::min(p.ntiles, num_sms);
-    tc_gemm_kernel<MODE, NMAX><<<unsigned(grid), 192, Cfg<MODE, NMAX>::kSmem, s>>>(p);
+    tc_gemm_kernel<MODE, NMAX, GEN>
+        <<<unsigned(grid), GEN ? 448 : 192, Cfg<MODE, NMAX>::kSmem + (GEN ? kGenSmem : 0), s>>>(p);
     CUDA_OK(cudaGetLastError());
 }
 
 // Cooperative launch: every CTA of the persistent grid is resident at once,
 // so tiles waiting on counters bumped by other CTAs always make progress.
-template <int MODE, int NMAX>
+template <int MODE, int NMAX, bool GEN>
 static void launch_gemm_coop(const TcParams& p, int num_sms, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(std::min(p.ntiles, num_sms)));
-    cfg.blockDim = dim3(192);
-    cfg.dynamicSmemBytes = Cfg<MODE, NMAX>::kSmem;
+    cfg.blockDim = dim3(GEN ? 448 : 192);
+    cfg.dynamicSmemBytes = Cfg<MODE, NMAX>::kSmem + (GEN ? kGenSmem : 0);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    CUDA_OK(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<MODE, NMAX>, p));
+    CUDA_OK(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<MODE, NMAX, GEN>, p));
 }
 
-// piece: the tallest task piece among the launch's segments (128 or 256)
-void launch_gemm_mode(int mode, int piece, const TcParams& p, int num_sms, cudaStream_t s) {
+template <bool GEN>
+static void launch_gemm_sel(int mode, int piece, const TcParams& p, int num_sms, cudaStream_t s) {
     if (piece <= 128) {
-        if (mode == TC_TF32) launch_gemm<TC_TF32, 128>(p, num_sms, s);
-        else if (mode == TC_BF16) launch_gemm<TC_BF16, 128>(p, num_sms, s);
-        else launch_gemm<TC_BF16X3, 128>(p, num_sms, s);
+        if (mode == TC_TF32) launch_gemm<TC_TF32, 128, GEN>(p, num_sms, s);
+        else if (mode == TC_BF16) launch_gemm<TC_BF16, 128, GEN>(p, num_sms, s);
+        else launch_gemm<TC_BF16X3, 128, GEN>(p, num_sms, s);
     } else {
-        if (mode == TC_TF32) launch_gemm<TC_TF32, 256>(p, num_sms, s);
-        else if (mode == TC_BF16) launch_gemm<TC_BF16, 256>(p, num_sms, s);
-        else launch_gemm<TC_BF16X3, 256>(p, num_sms, s);
+        if (mode == TC_TF32) launch_gemm<TC_TF32, 256, GEN>(p, num_sms, s);
+        else if (mode == TC_BF16) launch_gemm<TC_BF16, 256, GEN>(p, num_sms, s);
+        else launch_gemm<TC_BF16X3, 256, GEN>(p, num_sms, s);
     }
+}
+
+// piece: the tallest task piece among the launch's segments (128 or 256);
+// gen: some segment generates its block tiles (the variant with generator warps)
+void launch_gemm_mode(int mode, int piece, const TcParams& p, int num_sms, cudaStream_t s, bool gen) {
+    if (gen) launch_gemm_sel<true>(mode, piece, p, num_sms, s);
+    else launch_gemm_sel<false>(mode, piece, p, num_sms, s);
 }
 
 // SM-pair kernel: clusters of two CTAs (static tiles).  The grid is the
@@ -1412,16 +1683,22 @@ static void launch_gemm_pair_mode(int mode, int piece, const TcParams& p, int nu
     }
 }
 
-static void launch_gemm_coop_mode(int mode, int piece, const TcParams& p, int num_sms, cudaStream_t s) {
+template <bool GEN>
+static void launch_gemm_coop_sel(int mode, int piece, const TcParams& p, int num_sms, cudaStream_t s) {
     if (piece <= 128) {
-        if (mode == TC_TF32) launch_gemm_coop<TC_TF32, 128>(p, num_sms, s);
-        else if (mode == TC_BF16) launch_gemm_coop<TC_BF16, 128>(p, num_sms, s);
-        else launch_gemm_coop<TC_BF16X3, 128>(p, num_sms, s);
+        if (mode == TC_TF32) launch_gemm_coop<TC_TF32, 128, GEN>(p, num_sms, s);
+        else if (mode == TC_BF16) launch_gemm_coop<TC_BF16, 128, GEN>(p, num_sms, s);
+        else launch_gemm_coop<TC_BF16X3, 128, GEN>(p, num_sms, s);
     } else {
-        if (mode == TC_TF32) launch_gemm_coop<TC_TF32, 256>(p, num_sms, s);
-        else if (mode == TC_BF16) launch_gemm_coop<TC_BF16, 256>(p, num_sms, s);
-        else launch_gemm_coop<TC_BF16X3, 256>(p, num_sms, s);
+        if (mode == TC_TF32) launch_gemm_coop<TC_TF32, 256, GEN>(p, num_sms, s);
+        else if (mode == TC_BF16) launch_gemm_coop<TC_BF16, 256, GEN>(p, num_sms, s);
+        else launch_gemm_coop<TC_BF16X3, 256, GEN>(p, num_sms, s);
     }
+}
+
+static void launch_gemm_coop_mode(int mode, int piece, const TcParams& p, int num_sms, cudaStream_t s, bool gen) {
+    if (gen) launch_gemm_coop_sel<true>(mode, piece, p, num_sms, s);
+    else launch_gemm_coop_sel<false>(mode, piece, p, num_sms, s);
 }
 
 void launch_gather(int mode, const TcPrec& T, const float* W, int64_t ldw, const int64_t* perm,
@@ -1452,6 +1729,8 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
     p.nsegs = 1;
     p.err = T.d_err;
     const int sched = H.tc_schedule[T.mode];
+    if (sched == GOFMM_SCHED_PAIR && T.gen)
+        fail(GOFMM_ERR_UNSUPPORTED, "the SM-pair schedule needs cached K blocks (GOFMM_CACHE_BLOCKS)");
     if (H.timing == 1 || sched != GOFMM_SCHED_FUSED) {
         // one launch per stage (stage timing, or a staged schedule)
         D.last_fused = false;
@@ -1465,7 +1744,7 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
             p.ntiles = tl.second;
             p.segs[0] = make_seg(T, l, T.rt_hi, T.rt_lo, U, ldu, D.d_idx, r);
             if (pair) launch_gemm_pair_mode(T.mode, T.piece, p, T.num_sms, s);
-            else launch_gemm_mode(T.mode, T.piece, p, T.num_sms, s);
+            else launch_gemm_mode(T.mode, T.piece, p, T.num_sms, s, T.gen);
             ++launches;
         }
         while (stage_done < 5) CUDA_OK(cudaEventRecord(D.ev[++stage_done], s));
@@ -1492,7 +1771,7 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
         g.tasks = F.d_tasks;
         g.slabs = F.d_slabs;
         p.segs[0] = g;
-        launch_gemm_coop_mode(T.mode, T.piece, p, T.num_sms, s);
+        launch_gemm_coop_mode(T.mode, T.piece, p, T.num_sms, s, T.gen);
         ++launches;
         if (timing)
             for (int i = 2; i <= 5; ++i) CUDA_OK(cudaEventRecord(D.ev[i], s));
@@ -1547,6 +1826,7 @@ static void free_prec(TcPrec*& T) {
             for (auto& kv : l.tiles) dfree(kv.second.first);
         }
         dfree(T->d_chunk_pos); dfree(T->d_chunk_valid); dfree(T->b_hi); dfree(T->b_lo); dfree(T->d_err);
+        dfree(T->gen_pts);
         {
             TcFused& F = T->fused;
             dfree(F.d_tasks); dfree(F.d_slabs); dfree(F.d_dep_off); dfree(F.d_deps); dfree(F.d_sig);

@@ -17,10 +17,14 @@ enum TcMode : int { TC_TF32 = 0, TC_BF16 = 1, TC_BF16X3 = 2 };
 
 
 struct TcSlab {
-    int64_t b_off;     // byte offset of the slab's first chunk tile in the B store
+    int64_t b_off;     // cached: byte offset of the slab's first chunk tile in the B store;
+                       // generated: offset in idx[] of the piece's row list
     int32_t a_buf;     // 0 WT, 1 WTIL, 2 UTIL
     int32_t a_chunk0;  // first chunk of the slab's K range in that RT buffer
     int32_t nchunks;
+    int32_t gen;       // 1: the block tiles are generated in the kernel (K(row list, column list))
+    int64_t gen_cols;  // generated: offset in idx[] of the column list
+    int32_t k;         // generated: columns (the rest of the last chunk is zero)
     int32_t pad;
 };
 
@@ -56,7 +60,16 @@ struct TcSeg {
     int32_t r;
     int32_t tile_base;    // segment tile lists: first global tile index of this segment
     const TcTile* tiles;  // segment tile lists (TcParams::tiles == nullptr): this segment's tiles
+    // in-kernel entry generation (generated slabs): point table in index-list
+    // order (row t = the point of perm[t], tree order then skeleton lists),
+    // dpad floats per point (dim padded to a multiple of 4);
+    // GOFMM_GEN_GAUSSIAN exp(-d2 inv) or GOFMM_GEN_IMQ 1/sqrt(1 + d2 inv),
+    // plus shift where the row and column are the same index-list position
+    const float* pts;
+    int32_t dim, dpad, gen_kind, pad2;
+    float gen_inv, gen_shift;
 };
+constexpr int kGenMaxDpad = 16;  // generated blocks: at most 16 coordinates per point
 constexpr int kMaxSegs = 64;  // segments per launch (kernel parameters, by value)
 
 
@@ -117,6 +130,10 @@ struct TcFused {
 struct TcPrec {
     int mode = 0, kc = 0, es = 0;
     int piece = kMaxN;  // task piece height: tasks taller than this are split (MMA N ceiling)
+    bool gen = false;   // some slabs generate their block tiles in the kernel (no cached blocks)
+    float* gen_pts = nullptr;  // generator: point table (index-list order), kind, 1/(2h^2) or 1/h^2, shift
+    int gen_dim = 0, gen_dpad = 0, gen_kind = 0;
+    float gen_inv = 0.f, gen_shift = 0.f;
     bool split = false;
     std::vector<TcLaunch> launches;
     int64_t wt_chunks = 0, sk_chunks = 0;
@@ -143,7 +160,7 @@ int mode_of(int precision);
 TcPrec& tc_plan(Handle& H, DeviceState& D, int precision);  // plan + B tiles (allocates, synchronises)
 TcSeg make_seg(const TcPrec& T, const TcLaunch& l, uint8_t* const* rt_hi, uint8_t* const* rt_lo, float* U,
                int64_t ldu, const int64_t* perm, int r);
-void launch_gemm_mode(int mode, int piece, const TcParams& p, int num_sms, cudaStream_t s);
+void launch_gemm_mode(int mode, int piece, const TcParams& p, int num_sms, cudaStream_t s, bool gen = false);
 // device tile list of one launch alone for n_rtiles r-tiles (cached in the launch)
 std::pair<TcTile*, int> launch_tiles(TcLaunch& l, int n_rtiles, int order, bool pair = false);
 void tc_drop_plan(DeviceState& D, int precision);  // frees one mode's plan, stores and buffers

@@ -433,9 +433,11 @@ TuneResult autotune(Handle& H, int64_t r, int precision, const char* cache_path,
                              {GOFMM_SCHED_STAGED, GOFMM_ORDER_CRITICAL}, {GOFMM_SCHED_STAGED, GOFMM_ORDER_LOCAL},
                              {GOFMM_SCHED_PAIR, GOFMM_ORDER_CRITICAL},   {GOFMM_SCHED_PAIR, GOFMM_ORDER_LOCAL}};
     float best = 0.f;
+    const bool gen_plan = H.st.prm.cache_mode == GOFMM_CACHE_NONE;  // blocks generated in the kernel
     try {
         for (int piece : {256, 128})
             for (const auto& c : cands) {
+                if (gen_plan && c[0] == GOFMM_SCHED_PAIR) continue;  // the pair kernel reads cached blocks
                 device_set_tc_config(H, precision, piece, c[0], c[1]);
                 device_prepare(H, r, precision);
                 const float ms = time_median(
