@@ -502,7 +502,7 @@ def native_arm(args):
     tune = None
     if prec_name in ("tf32", "bf16", "bf16x3") and args.config:
         pc, sc, oc = args.config.split("/")
-        G.set_tc_config(h, prec, int(pc), ["fused", "staged", "pair"].index(sc), ["critical", "local"].index(oc))
+        G.set_tc_config(h, prec, int(pc), ["fused", "staged", "pair", "hybrid"].index(sc), ["critical", "local"].index(oc))
         tune = dict(G.get_tc_config(h, prec), forced=True, candidates=[])
     elif prec_name in ("tf32", "bf16", "bf16x3") and not args.no_tune:
         tune = G.autotune(h, r, prec, None, stream)
@@ -645,7 +645,7 @@ def native_arm(args):
         current = (tr.get("precision") == prec_name and os.path.exists(src) and tr.get("workload") == w.name
                    and hashlib.sha256(open(src, "rb").read()).hexdigest() == tr.get("sha256"))
         if current and tune is not None:
-            cfg = (f"{tune['piece']}/{['fused', 'staged', 'pair'][tune['schedule']]}/"
+            cfg = (f"{tune['piece']}/{['fused', 'staged', 'pair', 'hybrid'][tune['schedule']]}/"
                    f"{['critical', 'local'][tune['order']]}")
             traffic = float(tr[cfg]) if cfg in tr else None
     if prec_name in ("fp32", "fp64"):

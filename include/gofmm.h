@@ -73,6 +73,9 @@ extern "C" {
 #define GOFMM_SCHED_STAGED 1   /* one persistent launch per stage            */
 #define GOFMM_SCHED_PAIR 2     /* one launch per stage on SM pairs: M = 256
                                   MMAs over two r-tiles (tcgen05 cta_group::2) */
+#define GOFMM_SCHED_HYBRID 3   /* upward pass in one dependency-driven launch,
+                                  S2S in one launch, downward pass and leaves
+                                  in one dependency-driven launch             */
 #define GOFMM_ORDER_CRITICAL 0 /* fused launch: longest dependent chain first;
                                   staged launches: heaviest task first       */
 #define GOFMM_ORDER_LOCAL 1    /* fused: topological, (stage, level) groups by
@@ -421,8 +424,9 @@ typedef struct {
 /*
  * Autotuner.  Times gofmm_evaluate of h with r right-hand sides in a
  * tensor-core precision under each candidate configuration (piece 256 and
- * 128, each with the FUSED, STAGED and PAIR schedules in CRITICAL and in
- * LOCAL order: 12 candidates; 3 warm-up and 7 timed calls each, CUDA events on
+ * 128, each with the FUSED, STAGED, PAIR and HYBRID schedules in CRITICAL and
+ * in LOCAL order: 16 candidates, 12 without cached blocks (no PAIR); 3
+ * warm-up and 7 timed calls each, CUDA events on
  * `stream`, on scratch W = 0 and U the library allocates), applies the
  * fastest with gofmm_set_tc_config and reports all of them in *out.
  * cache_path (may be NULL): a JSON file of earlier choices.  If it holds

@@ -1088,9 +1088,11 @@ __global__ void tc_tile_kernel(const TileJob* __restrict__ jobs, const float* __
 // it reads and bumps the counters of what it writes; tasks are ordered by
 // the length of the dependent work that follows them (critical path first),
 // which is a topological order.
-static void build_fused(const Structure& st, TcPrec& T) {
+// stage_mask selects the stages (bit 1 N2S, 2 S2S, 3 S2N, 4 leaves) whose
+// tasks the launch runs; a dependency on a counter that no selected task
+// bumps was satisfied by an earlier launch and is dropped.
+static void build_fused(const Structure& st, TcPrec& T, TcFused& F, unsigned stage_mask) {
     const int64_t nn = st.n_nodes();
-    TcFused& F = T.fused;
     std::vector<int> pn2s(nn, 0), ps2s(nn, 0), ppush(nn, 0);
     for (const TcLaunch& l : T.launches)
         for (size_t k = 0; k < l.tasks.size(); ++k) {
@@ -1104,6 +1106,19 @@ static void build_fused(const Structure& st, TcPrec& T) {
     auto cUF = [&](int64_t h) { return int32_t(2 * nn + h); };
     auto final_pieces = [&](int64_t h) { return ppush[h] ? ppush[h] : ps2s[h]; };
     F.ncounters = int(3 * nn);
+    // counters bumped inside this launch
+    std::vector<char> internal(size_t(3 * nn), 0);
+    for (const TcLaunch& l : T.launches) {
+        if (!((stage_mask >> l.stage) & 1u)) continue;
+        for (size_t k = 0; k < l.tasks.size(); ++k) {
+            const int64_t h = l.task_node[k];
+            if (l.stage == 1) internal[size_t(cWT(h))] = 1;
+            else if (l.stage == 2) {
+                internal[size_t(cS2S(h))] = 1;
+                if (!ppush[h]) internal[size_t(cUF(h))] = 1;
+            } else if (l.stage == 3) internal[size_t(cUF(h))] = 1;
+        }
+    }
     std::vector<int> cdepth(size_t(3 * nn), 0);
     std::vector<int32_t> dep_off{0}, deps, sig;
     std::vector<int> depth;
@@ -1112,7 +1127,8 @@ static void build_fused(const Structure& st, TcPrec& T) {
     std::vector<int64_t> node_of;
     F.tasks.clear();
     F.slabs.clear();
-    for (const TcLaunch& l : T.launches)
+    for (const TcLaunch& l : T.launches) {
+        if (!((stage_mask >> l.stage) & 1u)) continue;
         for (size_t k = 0; k < l.tasks.size(); ++k) {
             TcTask t = l.tasks[k];
             const int32_t base = int32_t(F.slabs.size());
@@ -1140,6 +1156,9 @@ static void build_fused(const Structure& st, TcPrec& T) {
             } else if (ps2s[h] > 0) {  // leaf output reading u~ of the leaf
                 d.emplace_back(cUF(h), 4 * final_pieces(h));
             }
+            d.erase(std::remove_if(d.begin(), d.end(),
+                                   [&](const std::pair<int32_t, int32_t>& x) { return !internal[size_t(x.first)]; }),
+                    d.end());
             std::sort(d.begin(), d.end());
             d.erase(std::unique(d.begin(), d.end()), d.end());
             int dp = 0;
@@ -1163,6 +1182,7 @@ static void build_fused(const Structure& st, TcPrec& T) {
             }
             F.tasks.push_back(t);
         }
+    }
     // priority: the longest chain of dependent work from a task to the end of
     // the evaluation (critical path first).  A producer's chain is longer
     // than any of its consumers', so the order stays topological.
@@ -1412,7 +1432,9 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
         l.d_tasks = dupload(l.tasks);
         l.d_slabs = dupload(l.slabs);
     }
-    build_fused(st, T);
+    build_fused(st, T, T.fused, 0x1Eu);               // every stage
+    build_fused(st, T, T.fused_up, 1u << 1);          // the upward pass
+    build_fused(st, T, T.fused_down, (1u << 3) | (1u << 4));  // the downward pass and the leaves
 }
 
 template <int MODE>
@@ -1524,13 +1546,14 @@ void tc_prepare(Handle& H, DeviceState& D, int64_t r_max, int precision) {
     for (TcLaunch& l : T->launches)
         for (int nrt = 1; nrt <= int(r_pad / 128); ++nrt)
             launch_tiles(l, nrt, H.tc_order[T->mode], H.tc_schedule[T->mode] == GOFMM_SCHED_PAIR);
-    TcFused& F = T->fused;
-    if (F.counters_nrt < int(r_pad / 128)) {
-        dfree(F.d_counters);
-        F.d_counters = dalloc<int>(size_t(F.ncounters) * size_t(r_pad / 128) + 1);  // + tile counter
-        F.counters_nrt = int(r_pad / 128);
+    for (TcFused* F : {&T->fused, &T->fused_up, &T->fused_down}) {
+        if (F->counters_nrt < int(r_pad / 128)) {
+            dfree(F->d_counters);
+            F->d_counters = dalloc<int>(size_t(F->ncounters) * size_t(r_pad / 128) + 1);  // + tile counter
+            F->counters_nrt = int(r_pad / 128);
+        }
+        for (int nrt = 1; nrt <= int(r_pad / 128); ++nrt) fused_tiles(*F, nrt, H.tc_order[T->mode]);
     }
-    for (int nrt = 1; nrt <= int(r_pad / 128); ++nrt) fused_tiles(F, nrt, H.tc_order[T->mode]);
     if (T->r_cap < r_pad) {
         for (int i = 0; i < 3; ++i) {
             dfree(T->rt_hi[i]);
@@ -1731,7 +1754,54 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
     const int sched = H.tc_schedule[T.mode];
     if (sched == GOFMM_SCHED_PAIR && T.gen)
         fail(GOFMM_ERR_UNSUPPORTED, "the SM-pair schedule needs cached K blocks (GOFMM_CACHE_BLOCKS)");
-    if (H.timing == 1 || sched != GOFMM_SCHED_FUSED) {
+    // one dependency-driven launch of the tasks of plan F
+    auto run_fused = [&](TcFused& F) {
+        if (F.tasks.empty()) return;
+        if (F.counters_nrt < n_rtiles) fail(GOFMM_ERR_ARG, "fused plan not prepared for this r");
+        CUDA_OK(cudaMemsetAsync(F.d_counters, 0, (size_t(F.ncounters) * n_rtiles + 1) * sizeof(int), s));
+        const auto tl = fused_tiles(F, n_rtiles, H.tc_order[T.mode]);
+        TcParams q{};
+        q.nsegs = 1;
+        q.err = T.d_err;
+        q.tiles = tl.first;
+        q.ntiles = tl.second;
+        q.dep_off = F.d_dep_off;
+        q.deps = F.d_deps;
+        if (F.stall_next) {  // diagnostic: one dependency nothing satisfies
+            q.deps = F.d_deps_stall;
+            F.stall_next = false;
+        }
+        q.sig = F.d_sig;
+        q.counters = F.d_counters;
+        q.dep_nrt = n_rtiles;
+        q.tile_next = F.d_counters + size_t(F.ncounters) * n_rtiles;
+        TcSeg g = make_seg(T, T.launches.front(), T.rt_hi, T.rt_lo, U, ldu, D.d_idx, r);
+        g.tasks = F.d_tasks;
+        g.slabs = F.d_slabs;
+        q.segs[0] = g;
+        launch_gemm_coop_mode(T.mode, T.piece, q, T.num_sms, s, T.gen);
+        ++launches;
+    };
+    if (H.timing != 1 && sched == GOFMM_SCHED_HYBRID) {
+        // upward pass in one dependency-driven launch, S2S in one launch,
+        // downward pass and leaves in one dependency-driven launch
+        D.last_fused = false;
+        run_fused(T.fused_up);
+        if (timing) CUDA_OK(cudaEventRecord(D.ev[2], s));
+        for (TcLaunch& l : T.launches) {
+            if (l.stage != 2 || l.tasks.empty()) continue;
+            const auto tl = launch_tiles(l, n_rtiles, H.tc_order[T.mode]);
+            p.tiles = tl.first;
+            p.ntiles = tl.second;
+            p.segs[0] = make_seg(T, l, T.rt_hi, T.rt_lo, U, ldu, D.d_idx, r);
+            launch_gemm_mode(T.mode, T.piece, p, T.num_sms, s, T.gen);
+            ++launches;
+        }
+        if (timing) CUDA_OK(cudaEventRecord(D.ev[3], s));
+        run_fused(T.fused_down);
+        if (timing)
+            for (int i = 4; i <= 5; ++i) CUDA_OK(cudaEventRecord(D.ev[i], s));
+    } else if (H.timing == 1 || sched != GOFMM_SCHED_FUSED) {
         // one launch per stage (stage timing, or a staged schedule)
         D.last_fused = false;
         const bool pair = sched == GOFMM_SCHED_PAIR;
@@ -1751,28 +1821,7 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
     } else {
         // every grouped GEMM in one dependency-driven launch
         D.last_fused = true;
-        TcFused& F = T.fused;
-        if (F.counters_nrt < n_rtiles) fail(GOFMM_ERR_ARG, "fused plan not prepared for this r");
-        CUDA_OK(cudaMemsetAsync(F.d_counters, 0, (size_t(F.ncounters) * n_rtiles + 1) * sizeof(int), s));
-        const auto tl = fused_tiles(F, n_rtiles, H.tc_order[T.mode]);
-        p.tiles = tl.first;
-        p.ntiles = tl.second;
-        p.dep_off = F.d_dep_off;
-        p.deps = F.d_deps;
-        if (F.stall_next) {  // diagnostic: one dependency nothing satisfies
-            p.deps = F.d_deps_stall;
-            F.stall_next = false;
-        }
-        p.sig = F.d_sig;
-        p.counters = F.d_counters;
-        p.dep_nrt = n_rtiles;
-        p.tile_next = F.d_counters + size_t(F.ncounters) * n_rtiles;
-        TcSeg g = make_seg(T, T.launches.front(), T.rt_hi, T.rt_lo, U, ldu, D.d_idx, r);
-        g.tasks = F.d_tasks;
-        g.slabs = F.d_slabs;
-        p.segs[0] = g;
-        launch_gemm_coop_mode(T.mode, T.piece, p, T.num_sms, s, T.gen);
-        ++launches;
+        run_fused(T.fused);
         if (timing)
             for (int i = 2; i <= 5; ++i) CUDA_OK(cudaEventRecord(D.ev[i], s));
     }
@@ -1827,12 +1876,11 @@ static void free_prec(TcPrec*& T) {
         }
         dfree(T->d_chunk_pos); dfree(T->d_chunk_valid); dfree(T->b_hi); dfree(T->b_lo); dfree(T->d_err);
         dfree(T->gen_pts);
-        {
-            TcFused& F = T->fused;
-            dfree(F.d_tasks); dfree(F.d_slabs); dfree(F.d_dep_off); dfree(F.d_deps); dfree(F.d_sig);
-            dfree(F.d_deps_stall);
-            dfree(F.d_counters);
-            for (auto& kv : F.tiles) dfree(kv.second.first);
+        for (TcFused* F : {&T->fused, &T->fused_up, &T->fused_down}) {
+            dfree(F->d_tasks); dfree(F->d_slabs); dfree(F->d_dep_off); dfree(F->d_deps); dfree(F->d_sig);
+            dfree(F->d_deps_stall);
+            dfree(F->d_counters);
+            for (auto& kv : F->tiles) dfree(kv.second.first);
         }
         for (int i = 0; i < 3; ++i) { dfree(T->rt_hi[i]); dfree(T->rt_lo[i]); }
         if (T->h_err) cudaFreeHost(T->h_err);

@@ -148,7 +148,9 @@ struct TcPrec {
     int* d_err = nullptr;
     int* h_err = nullptr;  // pinned
     int num_sms = 148;     // persistent grid size
-    TcFused fused;
+    TcFused fused;       // every stage in one launch
+    TcFused fused_up;    // N2S levels in one launch (hybrid schedule)
+    TcFused fused_down;  // S2N levels and leaves in one launch (hybrid schedule)
 };
 
 struct TcState {

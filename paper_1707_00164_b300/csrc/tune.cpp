@@ -429,9 +429,10 @@ TuneResult autotune(Handle& H, int64_t r, int precision, const char* cache_path,
     DevBuf W(size_t(n) * size_t(r) * sizeof(float)), U(size_t(n) * size_t(r) * sizeof(float));
     const int saved_timing = H.timing;
     H.timing = 0;  // the production path, graph replay included
-    const int cands[6][2] = {{GOFMM_SCHED_FUSED, GOFMM_ORDER_CRITICAL}, {GOFMM_SCHED_FUSED, GOFMM_ORDER_LOCAL},
+    const int cands[8][2] = {{GOFMM_SCHED_FUSED, GOFMM_ORDER_CRITICAL},  {GOFMM_SCHED_FUSED, GOFMM_ORDER_LOCAL},
                              {GOFMM_SCHED_STAGED, GOFMM_ORDER_CRITICAL}, {GOFMM_SCHED_STAGED, GOFMM_ORDER_LOCAL},
-                             {GOFMM_SCHED_PAIR, GOFMM_ORDER_CRITICAL},   {GOFMM_SCHED_PAIR, GOFMM_ORDER_LOCAL}};
+                             {GOFMM_SCHED_PAIR, GOFMM_ORDER_CRITICAL},   {GOFMM_SCHED_PAIR, GOFMM_ORDER_LOCAL},
+                             {GOFMM_SCHED_HYBRID, GOFMM_ORDER_CRITICAL}, {GOFMM_SCHED_HYBRID, GOFMM_ORDER_LOCAL}};
     float best = 0.f;
     const bool gen_plan = H.st.prm.cache_mode == GOFMM_CACHE_NONE;  // blocks generated in the kernel
     try {

@@ -33,7 +33,9 @@ def test_config_defaults_and_validation():
     assert G.get_tc_config(h, G.PREC_TF32)["schedule"] == G.SCHED_FUSED
     G.set_tc_config(h, G.PREC_BF16, 128, G.SCHED_PAIR, G.ORDER_CRITICAL)
     assert G.get_tc_config(h, G.PREC_BF16)["schedule"] == G.SCHED_PAIR
-    for args in [(G.PREC_BF16, 64, 0, 0), (G.PREC_BF16, 256, 3, 0), (G.PREC_BF16, 256, 0, 5),
+    G.set_tc_config(h, G.PREC_BF16, 256, G.SCHED_HYBRID, G.ORDER_LOCAL)
+    assert G.get_tc_config(h, G.PREC_BF16)["schedule"] == G.SCHED_HYBRID
+    for args in [(G.PREC_BF16, 64, 0, 0), (G.PREC_BF16, 256, 4, 0), (G.PREC_BF16, 256, 0, 5),
                  (G.PREC_FP32, 256, 0, 0), (G.PREC_FP64, 128, 0, 0)]:
         with pytest.raises(G.GofmmError) as e:
             G.set_tc_config(h, *args)

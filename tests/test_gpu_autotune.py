@@ -24,7 +24,7 @@ pytestmark = pytest.mark.gpu
 PRECS = [G.PREC_TF32, G.PREC_BF16, G.PREC_BF16X3]
 NAMES = {G.PREC_TF32: "tf32", G.PREC_BF16: "bf16", G.PREC_BF16X3: "bf16x3"}
 TOL = {G.PREC_TF32: 5e-3, G.PREC_BF16: 2e-2, G.PREC_BF16X3: 1e-4}
-CONFIGS = [(p, s, o) for p in (256, 128) for s in (G.SCHED_FUSED, G.SCHED_STAGED, G.SCHED_PAIR)
+CONFIGS = [(p, s, o) for p in (256, 128) for s in (G.SCHED_FUSED, G.SCHED_STAGED, G.SCHED_PAIR, G.SCHED_HYBRID)
            for o in (G.ORDER_CRITICAL, G.ORDER_LOCAL)]
 
 
@@ -77,7 +77,7 @@ def test_autotune_measures_applies_and_caches(tall, tmp_path):
     prec = G.PREC_BF16X3
     path = tmp_path / "tune.json"
     t = G.autotune(h, 300, prec, str(path))
-    assert not t["from_cache"] and len(t["candidates"]) == 12
+    assert not t["from_cache"] and len(t["candidates"]) == 16
     ms = [c["ms"] for c in t["candidates"]]
     assert all(m > 0 for m in ms)
     best = t["candidates"][int(np.argmin(ms))]
@@ -86,7 +86,7 @@ def test_autotune_measures_applies_and_caches(tall, tmp_path):
     doc = json.loads(path.read_text())
     assert doc["format"] == "gofmm-autotune" and len(doc["entries"]) == 1
     e = doc["entries"][0]
-    assert e["key"] == t["key"] and e["piece"] == t["piece"] and len(e["candidates"]) == 12
+    assert e["key"] == t["key"] and e["piece"] == t["piece"] and len(e["candidates"]) == 16
     # the tuned configuration evaluates correctly
     Wt = torch.from_numpy(W.astype(np.float32)).cuda()
     assert rel(run(h, Wt, prec), ref) <= 1e-4

@@ -61,7 +61,7 @@ def test_generated_blocks_every_configuration_bitwise_equal():
     G.prepare(h, 200, prec)
     out = []
     for piece in (256, 128):
-        for sched in (G.SCHED_FUSED, G.SCHED_STAGED):
+        for sched in (G.SCHED_FUSED, G.SCHED_STAGED, G.SCHED_HYBRID):
             for order in (G.ORDER_CRITICAL, G.ORDER_LOCAL):
                 G.set_tc_config(h, prec, piece, sched, order)
                 out.append(run(h, W, prec))
