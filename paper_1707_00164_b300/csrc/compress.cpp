@@ -640,20 +640,39 @@ static void skeletonize(const Ctx& c, Structure& st, const std::vector<int64_t>&
                 rows[t] = sample_rows(st, knn, kappa, h);
                 A[t].resize(rows[t].size() * cols[t].size());
             });
-            std::vector<SampleJob> jobs(nc);
-            for (int64_t t = 0; t < cnt; ++t)
-                jobs[t] = SampleJob{rows[t].data(), int64_t(rows[t].size()), cols[t].data(), int64_t(cols[t].size()),
-                                    A[t].data()};
-            sampler->sample(jobs);
-            parallel_for(cnt, c.par, [&](int64_t t) {
-                const int64_t h = first + t;
-                const int64_t m = int64_t(rows[t].size()), n = int64_t(cols[t].size());
-                IdResult id = interpolative_decomposition(A[t], m, n, st.prm.s, st.prm.tau);
-                std::vector<int64_t> sk(id.s);
-                for (int64_t u = 0; u < id.s; ++u) sk[u] = cols[t][id.perm[u]];
-                st.skel[h] = std::move(sk);
-                st.P[h] = std::move(id.P);
-            });
+            // batches of about 8 M entries: the GPU samples batch b + 1
+            // while the host decomposes batch b
+            std::vector<std::pair<int64_t, int64_t>> batches;  // node ranges [t0, t1)
+            for (int64_t t0 = 0; t0 < cnt;) {
+                int64_t t1 = t0, e = 0;
+                while (t1 < cnt && (t1 == t0 || e + int64_t(A[t1].size()) <= (int64_t(1) << 23))) e += int64_t(A[t1++].size());
+                batches.emplace_back(t0, t1);
+                t0 = t1;
+            }
+            auto jobs_of = [&](size_t b) {
+                std::vector<SampleJob> jobs;
+                for (int64_t t = batches[b].first; t < batches[b].second; ++t)
+                    jobs.push_back(SampleJob{rows[t].data(), int64_t(rows[t].size()), cols[t].data(),
+                                             int64_t(cols[t].size()), nullptr});
+                return jobs;
+            };
+            int slot = sampler->submit(jobs_of(0));
+            for (size_t b = 0; b < batches.size(); ++b) {
+                const std::vector<const double*> blk = sampler->wait(slot);
+                if (b + 1 < batches.size()) slot = sampler->submit(jobs_of(b + 1));
+                const int64_t t0 = batches[b].first;
+                parallel_for(batches[b].second - t0, c.par, [&](int64_t u) {
+                    const int64_t t = t0 + u, h = first + t;
+                    const int64_t m = int64_t(rows[t].size()), n = int64_t(cols[t].size());
+                    std::copy(blk[size_t(u)], blk[size_t(u)] + m * n, A[t].begin());
+                    IdResult id = interpolative_decomposition(A[t], m, n, st.prm.s, st.prm.tau);
+                    std::vector<int64_t> sk(id.s);
+                    for (int64_t v = 0; v < id.s; ++v) sk[v] = cols[t][id.perm[v]];
+                    st.skel[h] = std::move(sk);
+                    st.P[h] = std::move(id.P);
+                    std::vector<double>().swap(A[t]);
+                });
+            }
             continue;
         }
         parallel_for(cnt, c.par, [&](int64_t t) {

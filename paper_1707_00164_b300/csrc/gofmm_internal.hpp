@@ -123,12 +123,24 @@ public:
     ~DeviceSampler();
     DeviceSampler(const DeviceSampler&) = delete;
     DeviceSampler& operator=(const DeviceSampler&) = delete;
+    // Synchronous: every job's block written to job.out.
     void sample(const std::vector<SampleJob>& jobs);
+    // Asynchronous, double-buffered: submit() queues the blocks of a batch
+    // (job.out unused) and returns at once; wait(slot) blocks until they are
+    // in pinned host memory and returns, per job, a pointer to its block
+    // (valid until the slot is submitted again).  At most two batches in
+    // flight; submit(b + 1) may run while the caller works on batch b.
+    int submit(const std::vector<SampleJob>& jobs);
+    std::vector<const double*> wait(int slot);
 
 private:
+    struct Slot;
     const Entries& K_;
     int device_;
     double* d_pts_ = nullptr;
+    void* stream_ = nullptr;
+    Slot* slots_[2] = {nullptr, nullptr};
+    int next_ = 0;
 };
 
 int tree_depth(int64_t n, int64_t m);

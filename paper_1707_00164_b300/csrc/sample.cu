@@ -48,18 +48,126 @@ __global__ void sample_blocks_kernel(const SampleDesc* __restrict__ jobs, const 
 
 }  // namespace
 
+// One buffer set of the asynchronous path: descriptors and index lists
+// (pinned, uploaded), the blocks (device, then pinned), and the event that
+// marks them landed.
+struct DeviceSampler::Slot {
+    SampleDesc* h_desc = nullptr;
+    int64_t* h_idx = nullptr;
+    double* h_out = nullptr;
+    SampleDesc* d_desc = nullptr;
+    int64_t* d_idx = nullptr;
+    double* d_out = nullptr;
+    size_t cap_desc = 0, cap_idx = 0, cap_out = 0;
+    cudaEvent_t done = nullptr;
+    std::vector<int64_t> offs;
+};
+
 DeviceSampler::DeviceSampler(const Entries& K, int device) : K_(K), device_(device) {
     if (!K.is_generator()) fail(GOFMM_ERR_ARG, "device sampling needs a generator kind (Gaussian or IMQ)");
     DeviceGuard g(device_);
     d_pts_ = dupload(K.pts);
+    cudaStream_t s = nullptr;
+    CUDA_OK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    stream_ = s;
+    for (Slot*& sl : slots_) {
+        sl = new Slot();
+        CUDA_OK(cudaEventCreateWithFlags(&sl->done, cudaEventDisableTiming));
+    }
 }
 
 DeviceSampler::~DeviceSampler() {
     int old = -1;
     cudaGetDevice(&old);
     cudaSetDevice(device_);
+    if (stream_) cudaStreamSynchronize(static_cast<cudaStream_t>(stream_));
+    for (Slot* sl : slots_) {
+        if (!sl) continue;
+        if (sl->h_desc) cudaFreeHost(sl->h_desc);
+        if (sl->h_idx) cudaFreeHost(sl->h_idx);
+        if (sl->h_out) cudaFreeHost(sl->h_out);
+        dfree(sl->d_desc);
+        dfree(sl->d_idx);
+        dfree(sl->d_out);
+        if (sl->done) cudaEventDestroy(sl->done);
+        delete sl;
+    }
+    if (stream_) cudaStreamDestroy(static_cast<cudaStream_t>(stream_));
     dfree(d_pts_);
     if (old >= 0) cudaSetDevice(old);
+}
+
+int DeviceSampler::submit(const std::vector<SampleJob>& jobs) {
+    DeviceGuard g(device_);
+    const int id = next_;
+    next_ ^= 1;
+    Slot& sl = *slots_[id];
+    CUDA_OK(cudaEventSynchronize(sl.done));  // the slot's previous batch was consumed
+    size_t n_idx = 0, n_out = 0;
+    for (const SampleJob& jb : jobs) {
+        n_idx += size_t(jb.m + jb.n);
+        n_out += size_t(jb.m * jb.n);
+    }
+    auto grow_host = [](auto*& p, size_t& cap, size_t need) {
+        if (need <= cap) return;
+        if (p) CUDA_OK(cudaFreeHost(p));
+        p = nullptr;
+        CUDA_OK(cudaMallocHost(reinterpret_cast<void**>(&p), need * sizeof(*p)));
+        cap = need;
+    };
+    size_t c1 = sl.cap_desc, c2 = sl.cap_idx, c3 = sl.cap_out;
+    grow_host(sl.h_desc, c1, std::max<size_t>(jobs.size(), 1));
+    grow_host(sl.h_idx, c2, std::max<size_t>(n_idx, 1));
+    grow_host(sl.h_out, c3, std::max<size_t>(n_out, 1));
+    if (c1 > sl.cap_desc) { dfree(sl.d_desc); sl.d_desc = dalloc<SampleDesc>(c1); }
+    if (c2 > sl.cap_idx) { dfree(sl.d_idx); sl.d_idx = dalloc<int64_t>(c2); }
+    if (c3 > sl.cap_out) { dfree(sl.d_out); sl.d_out = dalloc<double>(c3); }
+    sl.cap_desc = c1;
+    sl.cap_idx = c2;
+    sl.cap_out = c3;
+    sl.offs.assign(jobs.size(), 0);
+    size_t pi = 0, po = 0;
+    for (size_t k = 0; k < jobs.size(); ++k) {
+        const SampleJob& jb = jobs[k];
+        for (int64_t t = 0; t < jb.m; ++t)
+            if (jb.rows[t] < 0 || jb.rows[t] >= K_.n) fail(GOFMM_ERR_ARG, "sample row out of range");
+        for (int64_t t = 0; t < jb.n; ++t)
+            if (jb.cols[t] < 0 || jb.cols[t] >= K_.n) fail(GOFMM_ERR_ARG, "sample column out of range");
+        SampleDesc d{};
+        d.roff = int64_t(pi);
+        std::copy(jb.rows, jb.rows + jb.m, sl.h_idx + pi);
+        pi += size_t(jb.m);
+        d.coff = int64_t(pi);
+        std::copy(jb.cols, jb.cols + jb.n, sl.h_idx + pi);
+        pi += size_t(jb.n);
+        d.out = int64_t(po);
+        d.m = int32_t(jb.m);
+        d.n = int32_t(jb.n);
+        sl.h_desc[k] = d;
+        sl.offs[k] = int64_t(po);
+        po += size_t(jb.m * jb.n);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream_);
+    if (!jobs.empty() && po > 0) {
+        CUDA_OK(cudaMemcpyAsync(sl.d_desc, sl.h_desc, jobs.size() * sizeof(SampleDesc), cudaMemcpyHostToDevice, s));
+        CUDA_OK(cudaMemcpyAsync(sl.d_idx, sl.h_idx, pi * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+        dim3 grid(unsigned(jobs.size()), 16);
+        sample_blocks_kernel<<<grid, 256, 0, s>>>(sl.d_desc, sl.d_idx, d_pts_, K_.dim, K_.kind, K_.h, K_.shift,
+                                                  sl.d_out);
+        CUDA_OK(cudaGetLastError());
+        CUDA_OK(cudaMemcpyAsync(sl.h_out, sl.d_out, po * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    CUDA_OK(cudaEventRecord(sl.done, s));
+    return id;
+}
+
+std::vector<const double*> DeviceSampler::wait(int slot) {
+    DeviceGuard g(device_);
+    Slot& sl = *slots_[slot];
+    CUDA_OK(cudaEventSynchronize(sl.done));
+    std::vector<const double*> out(sl.offs.size());
+    for (size_t k = 0; k < out.size(); ++k) out[k] = sl.h_out + sl.offs[k];
+    return out;
 }
 
 void DeviceSampler::sample(const std::vector<SampleJob>& jobs) {
