@@ -665,11 +665,10 @@ def native_arm(args):
     # per stage (one launch per stage, timing level 1): algorithmic flops and
     # bytes of the stage against the tensor (or ALU) and HBM peaks
     hbm = peaks.get("hbm_gbs", 6400.0)
-    ent = st["near_entries"] + st["far_entries"]
     stage_work = {
-        "upward": (r * st["flops_n2s"], st["interp_entries"] / 2 * be + w.n * r * be + st["skel_total"] * r * be),
+        "upward": (r * st["flops_n2s"], st["interp_entries"] * be + w.n * r * be + st["skel_total"] * r * be),
         "s2s": (r * st["flops_s2s"], st["far_entries"] * be + 2 * st["skel_total"] * r * be),
-        "s2n": (r * st["flops_s2n"], st["interp_entries"] / 2 * be + 2 * st["skel_total"] * r * be),
+        "s2n": (r * st["flops_s2n"], st["interp_entries"] * be + 2 * st["skel_total"] * r * be),
         "leaf": (r * st["flops_l2l"], st["near_entries"] * be + w.n * r * be + w.n * r * 4),
     }
     per_stage = {}
@@ -678,7 +677,6 @@ def native_arm(args):
         if t > 0:
             per_stage[k] = {"ms": round(st_ms[k], 4), "tflops": fl / t / 1e12, "frac_compute": fl / t / 1e12 / peak,
                             "gbs": by / t / 1e9, "frac_hbm": by / t / 1e9 / hbm}
-    del ent
     roofline = {"kernel": kdesc, "bound": bound, "algorithmic_bytes": alg_bytes, "per_stage": per_stage,
                 "per_stage_note": ("one launch per stage (timing level 1); flops per stage from the structure; bytes "
                                    "= cached blocks / interpolation tiles of the stage once + right-hand sides read "
