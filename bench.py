@@ -64,6 +64,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batched form")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving run")
     ap.add_argument("--no-precision", action="store_true", help="skip the precision workload")
+    ap.add_argument("--cache", default="blocks", choices=["blocks", "none"],
+                    help="main workload with cached K blocks (default) or with every entry generated in the kernels")
     ap.add_argument("--no-generated", action="store_true",
                     help="skip the run without cached blocks (entries generated in the kernels)")
     ap.add_argument("--no-tune", action="store_true",
@@ -219,11 +221,13 @@ def reference_arm(args):
     }))
 
 
-def config_dict(w, precision):
+def config_dict(w, precision, cache="blocks"):
     return {"workload": w.name, "N": w.n, "r": w.r, "dim": w.dim, "kernel": "gaussian",
             "h": w.bandwidth, "m": w.leaf_size, "s": w.max_rank, "tau": w.tau, "kappa": w.kappa,
-            "budget": w.budget, "precision": precision, "cache": "blocks",
-            "l2": "inputs larger than L2: the cached K blocks (>= 4 GB in FP32) are read every step"}
+            "budget": w.budget, "precision": precision, "cache": cache,
+            "l2": ("inputs larger than L2: the cached K blocks (>= 4 GB in FP32) are read every step"
+                   if cache == "blocks" else "no cached blocks: entries generated in the GEMM kernels; "
+                   "W and the skeleton weights (>= 0.6 GB) are larger than L2")}
 
 
 # ------------------------------------------------------------ multi-rank --
@@ -238,7 +242,7 @@ def shared_handle(G, entries, params, rank, world, barrier, path, device=0):
         G.export(h, path)
     barrier()
     if rank != 0:
-        h = G.import_(path, entries, G.CACHE_BLOCKS, device)
+        h = G.import_(path, entries, params.cache_mode, device)
     return h
 
 
@@ -484,7 +488,8 @@ def native_arm(args):
     prec = G.PRECISIONS[prec_name]
     K = w.matrix()
     entries = G.Entries.gaussian(K.points, w.bandwidth, w.shift)
-    params = G.default_params(**w.params(), device=local)
+    params = G.default_params(**w.params(), device=local,
+                              cache_mode=G.CACHE_NONE if args.cache == "none" else G.CACHE_BLOCKS)
     t0 = time.perf_counter()
     h = shared_handle(G, entries, params, rank, world,
                       (lambda: torch.distributed.barrier()) if world > 1 else (lambda: None),
@@ -643,6 +648,7 @@ def native_arm(args):
                 tr[k.strip()] = v.strip()
         src = os.path.join(ROOT, "paper_1707_00164_b300", "csrc", tr.get("source", "-"))
         current = (tr.get("precision") == prec_name and os.path.exists(src) and tr.get("workload") == w.name
+                   and args.cache == "blocks"
                    and hashlib.sha256(open(src, "rb").read()).hexdigest() == tr.get("sha256"))
         if current and tune is not None:
             cfg = (f"{tune['piece']}/{['fused', 'staged', 'pair', 'hybrid'][tune['schedule']]}/"
@@ -768,7 +774,7 @@ def native_arm(args):
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPE_NAME[prec_name],
             "data": "synthetic: seeded 6-D standard-normal points, Gaussian kernel; seeded N(0,1) W",
-            "config": config_dict(w, prec_name), "roofline": roofline, "cpu_baseline": cpu,
+            "config": config_dict(w, prec_name, args.cache), "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches * args.steps,
             "autotune": tune, "accuracy": acc, "modes": modes, "dense_cublas": dense, "precision_workload": precision, "batching": batching,
             "serving": serving,
