@@ -76,7 +76,7 @@ __device__ __forceinline__ int gen_bar_and(bool pred) {
 // rest of the n_pad rows zero), columns perm[cols .. cols + kvalid) (the rest
 // of the chunk zero), written into stage `stage`.
 struct GenJob {
-    int64_t rows, cols;
+    int64_t rows, cols, cols_end;  // cols_end: end of the slab's column list
     int32_t seg, stage, m, kvalid, n_pad, stop;
 };
 
@@ -435,6 +435,7 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
                                 GenJob& jb = jobs[j];
                                 jb.rows = sl.b_off;
                                 jb.cols = sl.gen_cols + int64_t(c) * C::kKc;
+                                jb.cols_end = sl.gen_cols + sl.k;
                                 jb.seg = tt.seg;
                                 jb.stage = stage;
                                 jb.m = tk.m;
@@ -616,6 +617,11 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
             const int gt = threadIdx.x - 192;
             int64_t cur_rows = -1;
             int cur_seg = -1;
+            // column points of the slab's next chunk, loaded while this chunk
+            // is computed (one float4 per thread: 64 columns x 16 floats at most)
+            float4 pf = make_float4(0.f, 0.f, 0.f, 0.f);
+            int64_t pf_cols = -1;
+            int pf_seg = -1;
             for (int seq = 0;; ++seq) {
                 const int j = seq % C::kStages;
                 bool ok = true;
@@ -643,8 +649,19 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
                     cur_rows = jb.rows;
                     cur_seg = jb.seg;
                 }
-                for (int e = gt; e < jb.kvalid * dp / 4; e += kGenWarps * 32)
-                    reinterpret_cast<float4*>(colpts)[e] = tab[jb.cols * (dp / 4) + e];
+                if (gt < jb.kvalid * dp / 4)
+                    reinterpret_cast<float4*>(colpts)[gt] =
+                        (jb.cols == pf_cols && jb.seg == pf_seg) ? pf : tab[jb.cols * (dp / 4) + gt];
+                pf_cols = -1;
+                {
+                    const int64_t nc = jb.cols + C::kKc;
+                    if (nc < jb.cols_end) {
+                        const int nk = int(jb.cols_end - nc < C::kKc ? jb.cols_end - nc : C::kKc);
+                        if (gt < nk * dp / 4) pf = tab[nc * (dp / 4) + gt];
+                        pf_cols = nc;
+                        pf_seg = jb.seg;
+                    }
+                }
                 gen_bar_sync();  // points in shared memory
                 uint8_t* bh = base + jb.stage * C::kStageBytes + kTileBytes;
                 uint8_t* bl = bh + kTileBytes + NMAX * 128;  // split BF16x3: the lo copy of the stage
