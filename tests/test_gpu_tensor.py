@@ -88,6 +88,17 @@ def test_full_size_tensor_core_against_oracle_rows(prec):
     G.synchronize(h)
     got = U[torch.from_numpy(g["rows"]).cuda()][:, : g["u_oracle"].shape[1]].double().cpu().numpy()
     assert rel(got, g["u_oracle"]) <= TOL[prec]
+    # the configuration the benchmark times (autotuned) and every other one
+    # the tuner measured give bitwise this result at full size
+    ref = U.clone()
+    t = G.autotune(h, 512, prec, None)
+    for cfg in [(t["piece"], t["schedule"], t["order"])] + [(c["piece"], c["schedule"], c["order"])
+                                                            for c in t["candidates"][::3]]:
+        G.set_tc_config(h, prec, *cfg)
+        U.fill_(float("nan"))
+        G.evaluate(h, W, U, prec)
+        G.synchronize(h)
+        assert torch.equal(U, ref), cfg
 
 
 @pytest.mark.parametrize("prec", [G.PREC_FP32, G.PREC_BF16X3], ids=["fp32", "bf16x3"])
