@@ -363,17 +363,18 @@ def precision_bench(G, torch, dev, w, h, steps, tuning=True):
     return out
 
 
-def serving_bench(G, torch, dev, works, handles, loads=(0.5, 0.8, 1.0)):
+def serving_bench(G, torch, dev, works, handles, loads=(0.5, 0.8, 1.0), prec_name="bf16"):
     """Continuous batching over 8 resident matrices: seeded Poisson arrivals,
-    matrix uniform, r uniform in [1, 512], BF16 tensor cores; admission by
-    a workspace pool sized from free HBM.  Saturation throughput from a
+    matrix uniform, r uniform in [1, 512], tensor cores in `prec_name` (BF16
+    as the serving workload states; split BF16x3 for eps2 <= 1e-4); admission
+    by a workspace pool sized from free HBM.  Saturation throughput from a
     closed run (all requests at t = 0), then open-loop runs at fractions of
     it with p50/p99 latency (arrival to completion, host clock)."""
     import time as _t
-    prec = G.PREC_BF16
+    prec = G.PRECISIONS[prec_name]
     for h in handles:
         G.prepare(h, 512, prec)
-        G.trim(h)  # keep only the BF16 tensor-core tiles resident
+        G.trim(h)  # keep only the tensor-core tiles resident
     Wfull = [torch.from_numpy(w.rhs(512).astype(np.float32)).to(dev) for w in works]
     free, _ = torch.cuda.mem_get_info(dev)
     reserve = 16 << 30
@@ -433,7 +434,7 @@ def serving_bench(G, torch, dev, works, handles, loads=(0.5, 0.8, 1.0)):
     lat0, t_sat = run(np.zeros(len(mats)))
     sat_rate = len(mats) / t_sat
     out = {"workload": "8 resident matrices (N 16384..262144, Gaussian h 0.8 / IMQ l 0.5, d 3..6, m 256, "
-                       "s 256, tau 1e-5); 2000 seeded requests, matrix uniform, r U[1, 512]; BF16",
+                       f"s 256, tau 1e-5); 2000 seeded requests, matrix uniform, r U[1, 512]; {prec_name}",
            "pool_bytes": pool, "output_budget_bytes": out_budget, "saturation": {"requests_per_s": sat_rate, "value": units.sum() / t_sat,
                                                "unit": UNIT, "seconds": t_sat},
            "loads": {}}
@@ -760,6 +761,10 @@ def native_arm(args):
             serving = serving_bench(G, torch, dev, *extra["serve"])
         except Exception as e:
             serving = {"error": repr(e)[:300]}
+        try:  # the served form at eps2 <= 1e-4 against the FP64 oracle
+            serving["bf16x3"] = serving_bench(G, torch, dev, *extra["serve"], prec_name="bf16x3")
+        except Exception as e:
+            serving["bf16x3"] = {"error": repr(e)[:300]}
         extra.pop("serve")
     if "error" in extra:
         batching = batching or {"error": extra["error"]}
