@@ -201,7 +201,11 @@ int gofmm_evaluate(gofmm_handle* h, const void* W, int64_t ldw, void* U, int64_t
 /*
  * As gofmm_evaluate, but W and U are HOST pointers (pinned memory gives the
  * fastest copies).  Copies W to the device, evaluates, copies U back and
- * synchronises `stream` before returning.
+ * synchronises `stream` before returning.  With r >= 256 (and stage timing
+ * off) the columns run as two chunks of whole 128-column tiles: chunk 2 is
+ * copied in while chunk 1 is evaluated and chunk 1 copied out while chunk 2
+ * is evaluated (two library-owned copy streams); the result is bitwise that
+ * of gofmm_evaluate (columns are independent).
  */
 int gofmm_evaluate_host(gofmm_handle* h, const void* W, int64_t ldw, void* U, int64_t ldu,
                         int64_t r, int dtype, int precision, void* stream);

@@ -500,6 +500,12 @@ static void ensure_staging(Handle& H, int fi, int64_t r) {
 
 static int family_of(int precision) { return precision == GOFMM_PREC_FP64 ? 0 : 1; }
 
+// Column chunks of the copy / compute pipeline of host-buffer evaluations:
+// two chunks of whole 128-column r-tiles (more chunks re-read every cached
+// block once per chunk, which costs more than the overlap gains).
+constexpr int64_t kHostChunk = 128;
+static int64_t host_chunk(int64_t r) { return (r / 2 + kHostChunk - 1) / kHostChunk * kHostChunk; }
+
 static void clear_graphs(DeviceState& D) {
     for (auto& kv : D.graphs)
         if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -675,11 +681,14 @@ void device_evaluate(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu
     const void* Wd = W;
     void* Ud = U;
     int64_t ldw_d = ldw, ldu_d = ldu;
+    const bool pipelined = host_buffers && H.timing == 0 && r >= 2 * kHostChunk;
+    const int64_t chunk = host_chunk(r);
     if (host_buffers) {
         if (fi == 0) ensure_staging<double>(H, 0, r);
         else ensure_staging<float>(H, 1, r);
-        CUDA_OK(cudaMemcpy2DAsync(F->dW, size_t(r) * es, W, size_t(ldw) * es, size_t(r) * es, size_t(D.n),
-                                  cudaMemcpyHostToDevice, s));
+        if (!pipelined)
+            CUDA_OK(cudaMemcpy2DAsync(F->dW, size_t(r) * es, W, size_t(ldw) * es, size_t(r) * es, size_t(D.n),
+                                      cudaMemcpyHostToDevice, s));
         Wd = F->dW;
         Ud = F->dU;
         ldw_d = ldu_d = r;
@@ -694,6 +703,59 @@ void device_evaluate(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu
         return tc_run(H, D, static_cast<const float*>(Wd), ldw_d, static_cast<float*>(Ud), ldu_d, int(r),
                       precision, st);
     };
+    if (pipelined) {
+        // Host buffers: the columns of W and U are independent, so the
+        // evaluation runs over column chunks while chunk k + 1 is copied in
+        // and chunk k - 1 copied out on two copy streams.
+        F = &D.fam[fi];
+        if (!D.h2d_stream) {
+            CUDA_OK(cudaStreamCreateWithFlags(&D.h2d_stream, cudaStreamNonBlocking));
+            CUDA_OK(cudaStreamCreateWithFlags(&D.d2h_stream, cudaStreamNonBlocking));
+        }
+        const int64_t nch = (r + chunk - 1) / chunk;
+        while (int64_t(D.pipe_events.size()) < 2 * nch + 1) {
+            cudaEvent_t e = nullptr;
+            CUDA_OK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            D.pipe_events.push_back(e);
+        }
+        cudaEvent_t start = D.pipe_events[2 * size_t(nch)];
+        CUDA_OK(cudaEventRecord(start, s));  // the copies follow the caller's earlier work
+        CUDA_OK(cudaStreamWaitEvent(D.h2d_stream, start, 0));
+        char* dW = static_cast<char*>(F->dW);
+        char* dU = static_cast<char*>(F->dU);
+        for (int64_t k = 0; k < nch; ++k) {
+            const int64_t c0 = k * chunk, ck = std::min<int64_t>(chunk, r - c0);
+            CUDA_OK(cudaMemcpy2DAsync(dW + size_t(c0) * es, size_t(r) * es, static_cast<const char*>(W) + size_t(c0) * es,
+                                      size_t(ldw) * es, size_t(ck) * es, size_t(D.n), cudaMemcpyHostToDevice,
+                                      D.h2d_stream));
+            CUDA_OK(cudaEventRecord(D.pipe_events[2 * size_t(k)], D.h2d_stream));
+        }
+        int launches = 0;
+        for (int64_t k = 0; k < nch; ++k) {
+            const int64_t c0 = k * chunk, ck = std::min<int64_t>(chunk, r - c0);
+            CUDA_OK(cudaStreamWaitEvent(s, D.pipe_events[2 * size_t(k)], 0));
+            Wd = dW + size_t(c0) * es;
+            Ud = dU + size_t(c0) * es;
+            if (precision == GOFMM_PREC_FP64)
+                launches += run_simt<double, 4, 4>(H, static_cast<const double*>(Wd), r, static_cast<double*>(Ud), r,
+                                                   int(ck), s);
+            else if (precision == GOFMM_PREC_FP32)
+                launches += run_simt<float, 8, 8>(H, static_cast<const float*>(Wd), r, static_cast<float*>(Ud), r,
+                                                  int(ck), s);
+            else
+                launches += tc_run(H, D, static_cast<const float*>(Wd), r, static_cast<float*>(Ud), r, int(ck),
+                                   precision, s);
+            CUDA_OK(cudaEventRecord(D.pipe_events[2 * size_t(k) + 1], s));
+            CUDA_OK(cudaStreamWaitEvent(D.d2h_stream, D.pipe_events[2 * size_t(k) + 1], 0));
+            CUDA_OK(cudaMemcpy2DAsync(static_cast<char*>(U) + size_t(c0) * es, size_t(ldu) * es, dU + size_t(c0) * es,
+                                      size_t(r) * es, size_t(ck) * es, size_t(D.n), cudaMemcpyDeviceToHost,
+                                      D.d2h_stream));
+        }
+        D.last_launches = launches;
+        CUDA_OK(cudaStreamSynchronize(D.d2h_stream));
+        CUDA_OK(cudaStreamSynchronize(s));
+        return;
+    }
     if (H.timing != 0 || host_buffers) {
         D.last_launches = launch_all(s);
     } else {
@@ -829,6 +891,9 @@ void device_destroy(Handle& H) {
     cudaDeviceSynchronize();
     clear_graphs(*D);
     if (D->capture_stream) cudaStreamDestroy(D->capture_stream);
+    if (D->h2d_stream) cudaStreamDestroy(D->h2d_stream);
+    if (D->d2h_stream) cudaStreamDestroy(D->d2h_stream);
+    for (cudaEvent_t e : D->pipe_events) cudaEventDestroy(e);
     tc_destroy(*D);
     for (Launch& l : D->launches) {
         dfree(l.d_tasks);

@@ -107,6 +107,10 @@ struct DeviceState {
     };
     std::map<std::tuple<int, int64_t, const void*, int64_t, void*, int64_t>, GraphEntry> graphs;
     cudaStream_t capture_stream = nullptr;
+    // host-buffer evaluations: copy streams and per-chunk events of the
+    // copy / compute pipeline over column chunks of W and U
+    cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr;
+    std::vector<cudaEvent_t> pipe_events;
     bool ev_ok = false;
     bool last_fused = false;  // the last tensor-core call ran as one dependency-driven launch
     int last_launches = 0;

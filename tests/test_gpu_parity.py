@@ -150,3 +150,29 @@ def test_full_size_fp32_against_oracle_rows():
     lhs = (V.double().T @ U.double())
     rhs = (KV.double().T @ W.double())
     assert float(torch.linalg.norm(lhs - rhs) / torch.linalg.norm(lhs)) <= 1e-5
+
+
+@pytest.mark.parametrize("prec,dt", [(G.PREC_FP64, np.float64), (G.PREC_FP32, np.float32),
+                                     (G.PREC_BF16X3, np.float32)], ids=["fp64", "fp32", "bf16x3"])
+def test_host_buffer_pipeline_is_bitwise_the_device_evaluation(prec, dt):
+    """Host buffers with r >= 256 run over 128-column chunks with the copies
+    overlapped; columns are independent, so the result equals the
+    device-buffer evaluation bit for bit (ragged last chunk, padded host
+    leading dimensions)."""
+    w = wl.scaled(wl.C1, 3000)
+    h, st, K = both(w, leaf_size=64, callback=False)
+    r = 300
+    W = w.rhs(r).astype(dt)
+    Wt = torch.from_numpy(W).cuda()
+    Ut = torch.empty_like(Wt)
+    G.evaluate(h, Wt, Ut, prec)
+    G.synchronize(h)
+    ref = Ut.cpu().numpy()
+    Wpad = np.zeros((w.n, r + 5), dtype=dt)
+    Wpad[:, :r] = W
+    Upad = np.full((w.n, r + 7), np.nan, dtype=dt)
+    G.evaluate_host(h, Wpad[:, :r], Upad[:, :r], prec)
+    assert np.array_equal(Upad[:, :r], ref)
+    assert np.all(np.isnan(Upad[:, r:]))  # nothing written past r
+    if prec == G.PREC_FP64:
+        assert np.linalg.norm(Upad[:, :r] - O.evaluate(st, K, W)) <= 1e-12 * np.linalg.norm(ref)
