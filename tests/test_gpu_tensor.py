@@ -5,7 +5,10 @@ Tolerances follow the operand rounding: each MMA input is rounded to the
 mode's format (unit roundoff u: TF32 2^-11, BF16 2^-9; split BF16 keeps
 about 2^-16 of the FP32 value) and the result passes through up to four
 rounded stages (N2S, S2S, S2N, L2L), so the relative Frobenius error is a
-few u: TF32 <= 5e-3, BF16 <= 2e-2, BF16x3 <= 1e-4."""
+few u times the condition of the sums, kappa = || |K| |W| || / || K W ||:
+TF32 <= 5e-3, BF16 <= 2e-2, BF16x3 <= 1e-4 at kappa <= 25 (the Gaussian
+cases), scaled by kappa / 25 above it (an inverse multiquadric with random
+right-hand sides cancels much more: kappa 180 for one column)."""
 import os
 
 import numpy as np
@@ -36,6 +39,16 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
+def sum_condition(K, W):
+    """kappa = || |K| |W| ||_F / || K W ||_F (dense K; the test sizes allow it)."""
+    Kd = K.dense()
+    return float(np.linalg.norm(np.abs(Kd) @ np.abs(W)) / np.linalg.norm(Kd @ W))
+
+
+def tol(prec, K, W):
+    return TOL[prec] * max(1.0, sum_condition(K, W) / 25.0)
+
+
 CASES = [
     ("c2_recipe_n8192_r300", wl.scaled(wl.C2, 8192), 300, dict(knn_exact_max=20000)),
     ("ragged_n1000_r37", wl.scaled(wl.C1, 1000), 37, dict(leaf_size=32, callback=False)),
@@ -43,6 +56,11 @@ CASES = [
                                                                callback=False)),
     ("hss_n512_r5", wl.scaled(wl.C1, 512), 5, dict(leaf_size=32, budget=0.0, callback=False)),
     ("tall_blocks_n3000_m400", wl.scaled(wl.C3, 3000), 64, dict(leaf_size=400, max_rank=300, tau=1e-6)),
+    # degenerate shapes: one leaf (no skeletons, no far field), one column,
+    # fewer points than one MMA tile row block
+    ("single_leaf_n50_r7", wl.scaled(wl.C1, 50), 7, dict(leaf_size=64, callback=False)),
+    ("imq_angle_n777_r1", wl.scaled(wl.C3, 777), 1, dict(leaf_size=50, max_rank=40, distance=O.ANGLE, tau=1e-4)),
+    ("tiny_n9_r3", wl.scaled(wl.C1, 9), 3, dict(leaf_size=4, max_rank=2, callback=False)),
 ]
 
 
@@ -57,7 +75,7 @@ def test_tensor_core_evaluate_matches_oracle(name, w, r, over, prec):
     ref = O.evaluate(st, K, W)
     U = run(h, W, prec)
     assert np.all(np.isfinite(U))
-    assert rel(U, ref) <= TOL[prec], rel(U, ref)
+    assert rel(U, ref) <= tol(prec, K, W), (rel(U, ref), sum_condition(K, W))
 
 
 def test_tensor_core_is_deterministic_and_r_independent():
