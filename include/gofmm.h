@@ -342,7 +342,9 @@ int gofmm_batch_info(const gofmm_batch* b, int64_t* out, int n);
 int gofmm_batch_free(gofmm_batch* b);
 
 /* Release the handle and all its host and device memory (synchronises the
- * device first).  NULL is accepted. */
+ * device first).  NULL is accepted.  Fails with ERR_ARG (and frees nothing)
+ * while a serving engine holds requests of the handle.  Batches made from
+ * the handle must be freed first. */
 int gofmm_free(gofmm_handle* h);
 
 /*

@@ -491,6 +491,8 @@ int gofmm_batch_free(gofmm_batch* b) {
 
 int gofmm_free(gofmm_handle* h) {
     if (!h) return GOFMM_OK;
+    if (h->h.inflight > 0)
+        return set_error(GOFMM_ERR_ARG, "a serving engine holds requests of this handle: drain the engine first");
     int rc = guarded([&] { gofmm::device_destroy(h->h); });
     delete h;
     return rc;

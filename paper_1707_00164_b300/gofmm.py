@@ -295,7 +295,8 @@ def synchronize(h: Handle, stream=None):
 def free(h: Handle):
     if h.ptr:
         rc = LIB.gofmm_free(h.ptr)
-        h.ptr = None
+        if rc == OK:  # refused (requests in flight): the handle stays valid
+            h.ptr = None
         _check(rc)
 
 

@@ -140,6 +140,7 @@ def test_engine_in_flight_blocks_replanning():
     with pytest.raises(G.GofmmError) as e:
         G.set_tc_config(h, G.PREC_BF16, 128)
     assert e.value.code == G.ERR_ARG
+    assert G.LIB.gofmm_free(h.ptr) == G.ERR_ARG  # nor freed while in flight
     G.set_tc_config(h, G.PREC_BF16, 256, G.SCHED_STAGED)  # same plan: allowed
     eng.drain()
     G.set_tc_config(h, G.PREC_BF16, 128)  # nothing in flight any more
