@@ -311,12 +311,20 @@ def batching_bench(G, torch, dev, works, handles, steps, warmup, tuning=True):
     seq_ms = a.elapsed_time(b) / max(1, steps // 2)
     same = all(torch.equal(U, R) for U, R in zip(Us, seq_ref))
     nr = sum(w.n * w.r for w in works)
+    flops = 0.0
+    for w, h in zip(works, handles):
+        st = G.stats(h)
+        flops += w.r * (st["flops_n2s"] + st["flops_s2s"] + st["flops_s2n"] + st["flops_l2l"])
+    peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
+    peak = peaks.get("bf16_tflops", 1800.0) * NOMINAL_RATIO["bf16x3"]
     info = B.info()
     B.free()
     return {"workload": "64 Gaussian instances, N log-uniform [2048, 65536], d U{2..8}, h U[0.3, 1], "
                         "r U{16..256}, m 256, s 256, tau 1e-5; split BF16x3",
             "instances": len(works), "sum_N_r": nr, "ms_per_batch": ms, "value": nr / (ms / 1e3),
             "unit": UNIT, "launches_per_batch": info["launches"], "graph": True,
+            "flops_per_batch": flops, "tflops": flops / (ms / 1e3) / 1e12,
+            "frac_of_split_bf16_peak": flops / (ms / 1e3) / 1e12 / peak,
             "sequential_ms": seq_ms, "sequential_value": nr / (seq_ms / 1e3),
             "bitwise_equal_to_sequential": bool(same),
             "autotune": None if tune is None else {
