@@ -118,3 +118,20 @@ def test_device_sampling_needs_a_generator_and_a_gpu():
     with pytest.raises(G.GofmmError) as e:
         G.compress(G.Entries.gaussian(K.points, 0.3, 1e-3), G.default_params(leaf_size=32, sample_device=2))
     assert e.value.code == G.ERR_ARG
+
+
+def test_header_and_library_from_plain_c(tmp_path):
+    """include/gofmm.h compiles as C99 and the library links and runs from C."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    exe = str(tmp_path / "abi_from_c")
+    lib = G.gofmm.LIB_PATH
+    subprocess.check_call([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                           os.path.join(ROOT, "tests", "c", "abi_from_c.c"), lib, "-lm",
+                           "-Wl,-rpath," + os.path.dirname(lib), "-o", exe])
+    out = subprocess.run([exe, str(tmp_path / "c.bin")], capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0, out.stdout + out.stderr
+    assert out.stdout.startswith("c abi ok")
