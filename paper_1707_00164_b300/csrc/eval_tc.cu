@@ -412,15 +412,26 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
                 const int rt = tt.rt;
                 const uint32_t b_bytes = uint32_t(tk.n_pad) * 128u;
                 if (p.dep_off) {
-                    // operands written earlier in this launch by other tiles
+                    // results of other tiles of this launch the task needs
+                    // before it starts (the operands are waited for slab by slab)
                     for (int d = p.dep_off[tt.task]; d < p.dep_off[tt.task + 1] && ok; ++d)
                         ok = wait_counter(p.counters + int64_t(p.deps[2 * d]) * p.dep_nrt + rt, p.deps[2 * d + 1],
                                           p.err);
                     if (!ok) break;
-                    asm volatile("fence.proxy.async.global;" ::: "memory");  // generic writes -> bulk copies
                 }
                 for (int si = tk.slab0; si < tk.slab1 && ok; ++si) {
                     const TcSlab sl = sg.slabs[si];
+                    if (p.dep_off) {
+                        // this slab's right-hand sides, written earlier in the
+                        // launch by other tiles: wait (bounded), then make the
+                        // generic writes visible to the bulk copies
+                        if (sl.dep_c0 >= 0)
+                            ok = wait_counter(p.counters + int64_t(sl.dep_c0) * p.dep_nrt + rt, sl.dep_n0, p.err);
+                        if (ok && sl.dep_c1 >= 0)
+                            ok = wait_counter(p.counters + int64_t(sl.dep_c1) * p.dep_nrt + rt, sl.dep_n1, p.err);
+                        if (!ok) break;
+                        asm volatile("fence.proxy.async.global;" ::: "memory");
+                    }
                     const int64_t a_off = (int64_t(rt) * sg.rt_chunks[sl.a_buf] + sl.a_chunk0) * kTileBytes;
                     const uint8_t* a_hi = sg.rt_hi[sl.a_buf] + a_off;
                     if constexpr (GEN) {
@@ -1110,6 +1121,7 @@ __global__ void tc_tile_kernel(const TileJob* __restrict__ jobs, const float* __
 // bumps was satisfied by an earlier launch and is dropped.
 static void build_fused(const Structure& st, TcPrec& T, TcFused& F, unsigned stage_mask) {
     const int64_t nn = st.n_nodes();
+    constexpr int32_t E = 4;  // arrivals per task piece and r-tile: one per epilogue warp
     std::vector<int> pn2s(nn, 0), ps2s(nn, 0), ppush(nn, 0);
     for (const TcLaunch& l : T.launches)
         for (size_t k = 0; k < l.tasks.size(); ++k) {
@@ -1138,6 +1150,7 @@ static void build_fused(const Structure& st, TcPrec& T, TcFused& F, unsigned sta
     }
     std::vector<int> cdepth(size_t(3 * nn), 0);
     std::vector<int32_t> dep_off{0}, deps, sig;
+    std::vector<int32_t> all_off{0}, all_deps;  // task and slab dependencies together (ordering only)
     std::vector<int> depth;
     std::vector<int64_t> work;
     std::vector<std::pair<int, int>> group;  // (stage, tree level) of every task
@@ -1149,7 +1162,29 @@ static void build_fused(const Structure& st, TcPrec& T, TcFused& F, unsigned sta
         for (size_t k = 0; k < l.tasks.size(); ++k) {
             TcTask t = l.tasks[k];
             const int32_t base = int32_t(F.slabs.size());
-            for (int si = t.slab0; si < t.slab1; ++si) F.slabs.push_back(l.slabs[si]);
+            // the counter that says a node's right-hand-side segment in a
+            // buffer is complete: w~ after its N2S pieces, u~ when final
+            auto operand_dep = [&](int32_t buf, int32_t node) -> std::pair<int32_t, int32_t> {
+                if (node < 0 || buf == B_WT) return {-1, 0};
+                if (buf == B_WTIL) return {cWT(node), E * pn2s[node]};
+                return {cUF(node), E * final_pieces(node)};
+            };
+            std::vector<std::pair<int32_t, int32_t>> slab_deps;
+            for (int si = t.slab0; si < t.slab1; ++si) {
+                TcSlab sl = l.slabs[si];
+                const auto d0 = operand_dep(sl.a_buf, sl.a_node0), d1 = operand_dep(sl.a_buf, sl.a_node1);
+                if (d0.first >= 0 && internal[size_t(d0.first)]) {
+                    sl.dep_c0 = d0.first;
+                    sl.dep_n0 = d0.second;
+                    slab_deps.push_back(d0);
+                }
+                if (d1.first >= 0 && internal[size_t(d1.first)]) {
+                    sl.dep_c1 = d1.first;
+                    sl.dep_n1 = d1.second;
+                    slab_deps.push_back(d1);
+                }
+                F.slabs.push_back(sl);
+            }
             t.slab1 = base + (t.slab1 - t.slab0);
             t.slab0 = base;
             const int64_t h = l.task_node[k];
@@ -1157,34 +1192,51 @@ static void build_fused(const Structure& st, TcPrec& T, TcFused& F, unsigned sta
             int32_t s0 = -1, s1 = -1;
             if (l.stage == 1) {
                 if (!st.is_leaf(h)) {
-                    d.emplace_back(cWT(2 * h + 1), 4 * pn2s[2 * h + 1]);
-                    d.emplace_back(cWT(2 * h + 2), 4 * pn2s[2 * h + 2]);
+                    d.emplace_back(cWT(2 * h + 1), E * pn2s[2 * h + 1]);
+                    d.emplace_back(cWT(2 * h + 2), E * pn2s[2 * h + 2]);
                 }
                 s0 = cWT(h);
             } else if (l.stage == 2) {
-                for (int64_t a : st.far[h]) d.emplace_back(cWT(a), 4 * pn2s[a]);
+                for (int64_t a : st.far[h]) d.emplace_back(cWT(a), E * pn2s[a]);
                 s0 = cS2S(h);
                 if (!ppush[h]) s1 = cUF(h);
             } else if (l.stage == 3) {
                 const int64_t par = (h - 1) / 2;
-                d.emplace_back(cS2S(h), 4 * ps2s[h]);
-                d.emplace_back(cUF(par), 4 * final_pieces(par));
+                d.emplace_back(cS2S(h), E * ps2s[h]);
+                d.emplace_back(cUF(par), E * final_pieces(par));
                 s0 = cUF(h);
             } else if (ps2s[h] > 0) {  // leaf output reading u~ of the leaf
-                d.emplace_back(cUF(h), 4 * final_pieces(h));
+                d.emplace_back(cUF(h), E * final_pieces(h));
             }
             d.erase(std::remove_if(d.begin(), d.end(),
                                    [&](const std::pair<int32_t, int32_t>& x) { return !internal[size_t(x.first)]; }),
                     d.end());
             std::sort(d.begin(), d.end());
             d.erase(std::unique(d.begin(), d.end()), d.end());
+            // every dependency of the task: the slabs' operand dependencies
+            // are waited for slab by slab in the kernel; the rest (an S2N push
+            // waiting for its node's S2S result) before the first copy
+            std::vector<std::pair<int32_t, int32_t>> all = d;
+            for (const auto& x : slab_deps)
+                if (!std::binary_search(d.begin(), d.end(), x)) all.push_back(x);
             int dp = 0;
+            for (auto& x : all) dp = std::max(dp, cdepth[x.first]);
             for (auto& x : d) {
+                if (std::find(slab_deps.begin(), slab_deps.end(), x) != slab_deps.end()) continue;
                 deps.push_back(x.first);
                 deps.push_back(x.second);
-                dp = std::max(dp, cdepth[x.first]);
             }
             dep_off.push_back(int32_t(deps.size() / 2));
+            for (auto& x : slab_deps) {  // all dependencies, for the orders computed below
+                all_deps.push_back(x.first);
+                all_deps.push_back(x.second);
+            }
+            for (auto& x : d) {
+                if (std::find(slab_deps.begin(), slab_deps.end(), x) != slab_deps.end()) continue;
+                all_deps.push_back(x.first);
+                all_deps.push_back(x.second);
+            }
+            all_off.push_back(int32_t(all_deps.size() / 2));
             sig.push_back(s0);
             sig.push_back(s1);
             depth.push_back(dp + 1);
@@ -1206,7 +1258,8 @@ static void build_fused(const Structure& st, TcPrec& T, TcFused& F, unsigned sta
     const size_t nt = F.tasks.size();
     std::vector<std::vector<int32_t>> consumers(size_t(F.ncounters));
     for (size_t t = 0; t < nt; ++t)
-        for (int32_t d = dep_off[t]; d < dep_off[t + 1]; ++d) consumers[size_t(deps[2 * d])].push_back(int32_t(t));
+        for (int32_t d = all_off[t]; d < all_off[t + 1]; ++d)
+            consumers[size_t(all_deps[2 * d])].push_back(int32_t(t));
     std::vector<int64_t> tail(nt, 0);
     for (size_t t = nt; t-- > 0;) {
         int64_t best = 0;
@@ -1241,8 +1294,8 @@ static void build_fused(const Structure& st, TcPrec& T, TcFused& F, unsigned sta
         std::vector<int32_t> indeg(nt, 0);
         for (size_t t = 0; t < nt; ++t) {
             std::vector<int32_t> pre;
-            for (int32_t d = dep_off[t]; d < dep_off[t + 1]; ++d)
-                for (int32_t u : producers[size_t(deps[2 * d])]) pre.push_back(u);
+            for (int32_t d = all_off[t]; d < all_off[t + 1]; ++d)
+                for (int32_t u : producers[size_t(all_deps[2 * d])]) pre.push_back(u);
             std::sort(pre.begin(), pre.end());
             pre.erase(std::unique(pre.begin(), pre.end()), pre.end());
             for (int32_t u : pre) succ[size_t(u)].push_back(int32_t(t));
@@ -1344,6 +1397,13 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
                     const Slab& s = l.slabs[si];
                     TcSlab ts{};
                     ts.a_buf = s.b_src;
+                    ts.a_node0 = ts.a_node1 = -1;
+                    ts.dep_c0 = ts.dep_c1 = -1;
+                    if (s.b_src != B_WT) {
+                        const int64_t a = node_at_skel.at(s.b_row);
+                        ts.a_node0 = int32_t(a);
+                        if (s.k != int64_t(st.skel[a].size())) ts.a_node1 = int32_t(a + 1);  // [w~_l; w~_r]
+                    }
                     if (s.a_src == A_GEN) {
                         // block entries generated in the kernel from the row
                         // list (this piece's rows) and the column list
@@ -1784,8 +1844,10 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
         q.ntiles = tl.second;
         q.dep_off = F.d_dep_off;
         q.deps = F.d_deps;
+        const TcSlab* slabs = F.d_slabs;
         if (F.stall_next) {  // diagnostic: one dependency nothing satisfies
-            q.deps = F.d_deps_stall;
+            if (F.d_slabs_stall) slabs = F.d_slabs_stall;
+            else q.deps = F.d_deps_stall;
             F.stall_next = false;
         }
         q.sig = F.d_sig;
@@ -1794,7 +1856,7 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
         q.tile_next = F.d_counters + size_t(F.ncounters) * n_rtiles;
         TcSeg g = make_seg(T, T.launches.front(), T.rt_hi, T.rt_lo, U, ldu, D.d_idx, r);
         g.tasks = F.d_tasks;
-        g.slabs = F.d_slabs;
+        g.slabs = slabs;
         q.segs[0] = g;
         launch_gemm_coop_mode(T.mode, T.piece, q, T.num_sms, s, T.gen);
         ++launches;
@@ -1858,11 +1920,25 @@ void tc_stall_next(DeviceState& D, int precision) {
     if (!D.tc || !D.tc->prec[mode_of(precision)])
         fail(GOFMM_ERR_ARG, "handle not prepared for this precision: call gofmm_prepare first");
     TcFused& F = D.tc->prec[mode_of(precision)]->fused;
-    if (!F.d_deps_stall) {
-        std::vector<int32_t> deps(F.deps_host);
-        if (deps.size() < 2) fail(GOFMM_ERR_UNSUPPORTED, "the plan has no dependency to stall");
-        deps[1] = 1 << 30;  // an arrival count no counter reaches
-        F.d_deps_stall = dupload(deps);
+    if (!F.d_deps_stall && !F.d_slabs_stall) {
+        // one dependency of the plan gets an arrival count no counter reaches:
+        // a slab's operand dependency, else a task's
+        std::vector<TcSlab> slabs(F.slabs);
+        bool done = false;
+        for (TcSlab& sl : slabs)
+            if (sl.dep_c0 >= 0) {
+                sl.dep_n0 = 1 << 30;
+                done = true;
+                break;
+            }
+        if (done) {
+            F.d_slabs_stall = dupload(slabs);
+        } else {
+            std::vector<int32_t> deps(F.deps_host);
+            if (deps.size() < 2) fail(GOFMM_ERR_UNSUPPORTED, "the plan has no dependency to stall");
+            deps[1] = 1 << 30;
+            F.d_deps_stall = dupload(deps);
+        }
     }
     F.stall_next = true;
 }
@@ -1896,6 +1972,7 @@ static void free_prec(TcPrec*& T) {
         for (TcFused* F : {&T->fused, &T->fused_up, &T->fused_down}) {
             dfree(F->d_tasks); dfree(F->d_slabs); dfree(F->d_dep_off); dfree(F->d_deps); dfree(F->d_sig);
             dfree(F->d_deps_stall);
+            dfree(F->d_slabs_stall);
             dfree(F->d_counters);
             for (auto& kv : F->tiles) dfree(kv.second.first);
         }

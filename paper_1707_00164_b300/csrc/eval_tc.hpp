@@ -25,7 +25,10 @@ struct TcSlab {
     int32_t gen;       // 1: the block tiles are generated in the kernel (K(row list, column list))
     int64_t gen_cols;  // generated: offset in idx[] of the column list
     int32_t k;         // generated: columns (the rest of the last chunk is zero)
-    int32_t pad;
+    int32_t a_node0, a_node1;  // tree nodes whose skeleton rows the slab's right-hand sides are (-1: none)
+    // dependency-driven launch: the counters (and arrival counts) the slab's
+    // right-hand sides wait for before they are copied (-1: none)
+    int32_t dep_c0, dep_n0, dep_c1, dep_n1;
 };
 
 struct TcTask {
@@ -122,7 +125,8 @@ struct TcFused {
     int* d_counters = nullptr;  // ncounters x r-tiles of the largest r prepared (+ tile counter)
     int counters_nrt = 0;
     std::vector<int32_t> deps_host;
-    int32_t* d_deps_stall = nullptr;  // diagnostic copy with one unreachable arrival count
+    int32_t* d_deps_stall = nullptr;  // diagnostic copies with one unreachable arrival count
+    TcSlab* d_slabs_stall = nullptr;
     bool stall_next = false;
     std::map<int, std::pair<TcTile*, int>> tiles;  // 2 x r-tiles + order -> ordered tile list
 };
