@@ -257,6 +257,9 @@ def whole_job_value(n, r, world, ms_per_rank, reduce_max):
 
 
 # -------------------------------------------------------- batching/serving --
+SCHED_NAMES = ["fused", "staged", "pair", "hybrid"]  # GOFMM_SCHED_*
+
+
 def compress_many(G, works, device):
     """Native host compression of several workloads (no GPU work)."""
     out = []
@@ -270,9 +273,10 @@ def compress_many(G, works, device):
 
 def batching_bench(G, torch, dev, works, handles, steps, warmup, tuning=True):
     """64 uneven instances (N log-uniform in [2048, 65536], r in {16..256})
-    as one static batch: one persistent grouped launch per step for all of
-    them, replayed as a CUDA graph; compared with the same 64 evaluations
-    issued one after another."""
+    as one static batch, replayed as a CUDA graph: either one
+    dependency-driven launch for every stage of all of them or one grouped
+    launch per stage step (the batch autotuner's choice); compared with the
+    same 64 evaluations issued one after another."""
     prec = G.PREC_BF16X3
     stream = torch.cuda.current_stream(dev)
     for w, h in zip(works, handles):
@@ -327,8 +331,9 @@ def batching_bench(G, torch, dev, works, handles, steps, warmup, tuning=True):
             "sequential_ms": seq_ms, "sequential_value": nr / (seq_ms / 1e3),
             "bitwise_equal_to_sequential": bool(same),
             "autotune": None if tune is None else {
-                "piece": tune["piece"], "candidates_ms": {str(c["piece"]): round(c["ms"], 4)
-                                                          for c in tune["candidates"]}}}
+                "piece": tune["piece"], "schedule": SCHED_NAMES[tune["schedule"]],
+                "candidates_ms": {f'{c["piece"]}/{SCHED_NAMES[c["schedule"]]}': round(c["ms"], 4)
+                                  for c in tune["candidates"]}}}
 
 
 def precision_bench(G, torch, dev, w, h, steps, tuning=True):
@@ -515,7 +520,7 @@ def native_arm(args):
     tune = None
     if prec_name in ("tf32", "bf16", "bf16x3") and args.config:
         pc, sc, oc = args.config.split("/")
-        G.set_tc_config(h, prec, int(pc), ["fused", "staged", "pair", "hybrid"].index(sc), ["critical", "local"].index(oc))
+        G.set_tc_config(h, prec, int(pc), SCHED_NAMES.index(sc), ["critical", "local"].index(oc))
         tune = dict(G.get_tc_config(h, prec), forced=True, candidates=[])
     elif prec_name in ("tf32", "bf16", "bf16x3") and not args.no_tune:
         tune = G.autotune(h, r, prec, None, stream)
@@ -659,7 +664,7 @@ def native_arm(args):
                    and args.cache == "blocks"
                    and hashlib.sha256(open(src, "rb").read()).hexdigest() == tr.get("sha256"))
         if current and tune is not None:
-            cfg = (f"{tune['piece']}/{['fused', 'staged', 'pair', 'hybrid'][tune['schedule']]}/"
+            cfg = (f"{tune['piece']}/{SCHED_NAMES[tune['schedule']]}/"
                    f"{['critical', 'local'][tune['order']]}")
             traffic = float(tr[cfg]) if cfg in tr else None
     if prec_name in ("fp32", "fp64"):

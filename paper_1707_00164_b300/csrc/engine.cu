@@ -363,10 +363,26 @@ struct BatchStep {
     std::vector<Launch> launches;
 };
 
+// Dependency-driven form: up to kMaxSegs items in one cooperative launch
+// that runs every stage of all of them; each item's tiles in its own
+// topological order, the items interleaved task by task.
+struct BatchFused {
+    std::vector<int> items;
+    TcTile* d_tiles = nullptr;
+    int ntiles = 0;
+    int* d_counters = nullptr;          // the items' counters, then the tile counter
+    std::vector<size_t> counter_off;    // per item
+    size_t counter_ints = 0;
+    int piece = 0;
+    bool gen = false;
+};
+
 struct Batch {
     int device = 0, precision = 0, mode = 0, num_sms = 148;
     std::vector<BatchItem> items;
     std::vector<BatchStep> steps;
+    bool fused = false;                 // every handle configured for the fused schedule
+    std::vector<BatchFused> fused_launches;
     uint8_t* ws = nullptr;
     int* d_err = nullptr;
     int* h_err = nullptr;
@@ -417,6 +433,45 @@ Batch* batch_create(Handle* const* hs, const int64_t* r, int count, int precisio
         }
         off += sizes[i];
     }
+    B->fused = true;
+    for (int i = 0; i < count; ++i) B->fused = B->fused && hs[i]->tc_schedule[B->mode] == GOFMM_SCHED_FUSED;
+    if (B->fused) {
+        for (int c0 = 0; c0 < count; c0 += kMaxSegs) {
+            BatchFused bf;
+            const int c1 = std::min(count, c0 + kMaxSegs);
+            size_t off = 0;
+            std::vector<const std::vector<int32_t>*> orders;
+            for (int i = c0; i < c1; ++i) {
+                const BatchItem& it = B->items[i];
+                const TcFused& F = it.T->fused;
+                bf.items.push_back(i);
+                bf.counter_off.push_back(off);
+                off += size_t(F.ncounters) * size_t(it.n_rtiles);
+                bf.piece = std::max(bf.piece, it.T->piece);
+                bf.gen = bf.gen || it.T->gen;
+                orders.push_back(it.H->tc_order[B->mode] == GOFMM_ORDER_LOCAL ? &F.order_local : &F.order);
+            }
+            bf.counter_ints = off + 1;  // + the tile counter
+            bf.d_counters = dalloc<int>(bf.counter_ints);
+            // interleave the items task by task; each keeps its own order
+            std::vector<TcTile> tiles;
+            std::vector<size_t> pos(orders.size(), 0);
+            for (bool more = true; more;) {
+                more = false;
+                for (size_t k = 0; k < orders.size(); ++k) {
+                    if (pos[k] >= orders[k]->size()) continue;
+                    more = true;
+                    const int32_t task = (*orders[k])[pos[k]++];
+                    for (int rt = 0; rt < B->items[bf.items[k]].n_rtiles; ++rt)
+                        tiles.push_back(TcTile{int32_t(k), task, rt, 0});
+                }
+            }
+            bf.d_tiles = dupload(tiles);
+            bf.ntiles = int(tiles.size());
+            B->launches_per_call += (c1 - c0) + 1;  // gathers + one GEMM launch
+            B->fused_launches.push_back(std::move(bf));
+        }
+    }
     // the step sequence: every item advances one stage per step
     std::vector<int> next(count, 0);
     for (;;) {
@@ -456,7 +511,7 @@ Batch* batch_create(Handle* const* hs, const int64_t* r, int count, int precisio
         }
         for (int i : st.gathers) next[i] = 1;
         for (int i : gemm) ++next[i];
-        B->launches_per_call += int(st.gathers.size() + st.launches.size());
+        if (!B->fused) B->launches_per_call += int(st.gathers.size() + st.launches.size());
         B->steps.push_back(std::move(st));
     }
     B->d_err = dalloc<int>(1);
@@ -469,6 +524,36 @@ Batch* batch_create(Handle* const* hs, const int64_t* r, int count, int precisio
 
 static void batch_launch(Batch& B, const float* const* W, const int64_t* ldw, float* const* U, const int64_t* ldu,
                          cudaStream_t s) {
+    if (B.fused) {
+        for (const BatchFused& bf : B.fused_launches) {
+            TcParams p{};
+            p.nsegs = int(bf.items.size());
+            p.err = B.d_err;
+            p.tiles = bf.d_tiles;
+            p.ntiles = bf.ntiles;
+            for (size_t k = 0; k < bf.items.size(); ++k) {
+                const int i = bf.items[k];
+                const BatchItem& it = B.items[i];
+                launch_gather(B.mode, *it.T, W[i], ldw[i], it.H->dev->d_idx, it.rt_hi[0], it.rt_lo[0], it.r, s);
+                const TcFused& F = it.T->fused;
+                TcSeg g = make_seg(*it.T, it.T->launches.front(), it.rt_hi, it.rt_lo, U[i], ldu[i],
+                                   it.H->dev->d_idx, it.r);
+                g.tasks = F.d_tasks;
+                g.slabs = F.d_slabs;
+                g.dep_off = F.d_dep_off;
+                g.deps = F.d_deps;
+                g.sig = F.d_sig;
+                g.counters = bf.d_counters + bf.counter_off[k];
+                g.dep_nrt = it.n_rtiles;
+                p.segs[k] = g;
+            }
+            CUDA_OK(cudaMemsetAsync(bf.d_counters, 0, bf.counter_ints * sizeof(int), s));
+            p.tile_next = bf.d_counters + (bf.counter_ints - 1);
+            launch_gemm_coop_mode(B.mode, bf.piece, p, B.num_sms, s, bf.gen);
+        }
+        CUDA_OK(cudaMemcpyAsync(B.h_err, B.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        return;
+    }
     for (const BatchStep& st : B.steps) {
         for (int i : st.gathers) {
             const BatchItem& it = B.items[i];
@@ -543,6 +628,10 @@ void batch_destroy(Batch* B) {
         if (kv.second.second) cudaGraphExecDestroy(kv.second.second);
     for (BatchStep& st : B->steps)
         for (auto& bl : st.launches) dfree(bl.d_tiles);
+    for (BatchFused& bf : B->fused_launches) {
+        dfree(bf.d_tiles);
+        dfree(bf.d_counters);
+    }
     dfree(B->ws);
     dfree(B->d_err);
     if (B->h_err) cudaFreeHost(B->h_err);

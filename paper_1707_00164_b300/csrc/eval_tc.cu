@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
     const uint32_t drain_bar = smem_u32(&bars[2 * C::kStages + 4]);
     auto idfull_bar = [&](int a) { return smem_u32(&bars[2 * C::kStages + 5 + a]); };
     auto idempty_bar = [&](int a) { return smem_u32(&bars[2 * C::kStages + 7 + a]); };
-    const bool dyn = p.dep_off != nullptr;  // dynamic tile order (dependency mode)
+    const bool dyn = p.tile_next != nullptr;  // dynamic tile order (dependency mode)
     // stage s: A_hi | B_hi | (A_lo | B_lo)
     auto sA = [&](int s, int lo) { return s_base + s * C::kStageBytes + lo * (kTileBytes + NMAX * 128); };
     auto sB = [&](int s, int lo) { return sA(s, lo) + kTileBytes; };
@@ -411,24 +411,24 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
                 const TcTask tk = sg.tasks[tt.task];
                 const int rt = tt.rt;
                 const uint32_t b_bytes = uint32_t(tk.n_pad) * 128u;
-                if (p.dep_off) {
+                if (dyn) {
                     // results of other tiles of this launch the task needs
                     // before it starts (the operands are waited for slab by slab)
-                    for (int d = p.dep_off[tt.task]; d < p.dep_off[tt.task + 1] && ok; ++d)
-                        ok = wait_counter(p.counters + int64_t(p.deps[2 * d]) * p.dep_nrt + rt, p.deps[2 * d + 1],
+                    for (int d = sg.dep_off[tt.task]; d < sg.dep_off[tt.task + 1] && ok; ++d)
+                        ok = wait_counter(sg.counters + int64_t(sg.deps[2 * d]) * sg.dep_nrt + rt, sg.deps[2 * d + 1],
                                           p.err);
                     if (!ok) break;
                 }
                 for (int si = tk.slab0; si < tk.slab1 && ok; ++si) {
                     const TcSlab sl = sg.slabs[si];
-                    if (p.dep_off) {
+                    if (dyn) {
                         // this slab's right-hand sides, written earlier in the
                         // launch by other tiles: wait (bounded), then make the
                         // generic writes visible to the bulk copies
                         if (sl.dep_c0 >= 0)
-                            ok = wait_counter(p.counters + int64_t(sl.dep_c0) * p.dep_nrt + rt, sl.dep_n0, p.err);
+                            ok = wait_counter(sg.counters + int64_t(sl.dep_c0) * sg.dep_nrt + rt, sl.dep_n0, p.err);
                         if (ok && sl.dep_c1 >= 0)
-                            ok = wait_counter(p.counters + int64_t(sl.dep_c1) * p.dep_nrt + rt, sl.dep_n1, p.err);
+                            ok = wait_counter(sg.counters + int64_t(sl.dep_c1) * sg.dep_nrt + rt, sl.dep_n1, p.err);
                         if (!ok) break;
                         asm volatile("fence.proxy.async.global;" ::: "memory");
                     }
@@ -602,17 +602,17 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty_bar(acc));
-            if (p.dep_off) {
+            if (dyn) {
                 // publish this warp's 32 rows of the tile: consumers wait for
                 // four arrivals (one per epilogue warp) per task piece
-                const int s0 = p.sig[2 * tt.task], s1 = p.sig[2 * tt.task + 1];
+                const int s0 = sg.sig[2 * tt.task], s1 = sg.sig[2 * tt.task + 1];
                 if (s0 >= 0 || s1 >= 0) {
                     asm volatile("fence.proxy.async.global;" ::: "memory");
                     __syncwarp();
                     if (lane == 0) {
                         __threadfence();
-                        if (s0 >= 0) atomicAdd(p.counters + int64_t(s0) * p.dep_nrt + rt, 1);
-                        if (s1 >= 0) atomicAdd(p.counters + int64_t(s1) * p.dep_nrt + rt, 1);
+                        if (s0 >= 0) atomicAdd(sg.counters + int64_t(s0) * sg.dep_nrt + rt, 1);
+                        if (s1 >= 0) atomicAdd(sg.counters + int64_t(s1) * sg.dep_nrt + rt, 1);
                     }
                 }
             }
@@ -1796,7 +1796,7 @@ static void launch_gemm_coop_sel(int mode, int piece, const TcParams& p, int num
     }
 }
 
-static void launch_gemm_coop_mode(int mode, int piece, const TcParams& p, int num_sms, cudaStream_t s, bool gen) {
+void launch_gemm_coop_mode(int mode, int piece, const TcParams& p, int num_sms, cudaStream_t s, bool gen) {
     if (gen) launch_gemm_coop_sel<true>(mode, piece, p, num_sms, s);
     else launch_gemm_coop_sel<false>(mode, piece, p, num_sms, s);
 }
@@ -1842,21 +1842,20 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
         q.err = T.d_err;
         q.tiles = tl.first;
         q.ntiles = tl.second;
-        q.dep_off = F.d_dep_off;
-        q.deps = F.d_deps;
-        const TcSlab* slabs = F.d_slabs;
-        if (F.stall_next) {  // diagnostic: one dependency nothing satisfies
-            if (F.d_slabs_stall) slabs = F.d_slabs_stall;
-            else q.deps = F.d_deps_stall;
-            F.stall_next = false;
-        }
-        q.sig = F.d_sig;
-        q.counters = F.d_counters;
-        q.dep_nrt = n_rtiles;
-        q.tile_next = F.d_counters + size_t(F.ncounters) * n_rtiles;
         TcSeg g = make_seg(T, T.launches.front(), T.rt_hi, T.rt_lo, U, ldu, D.d_idx, r);
         g.tasks = F.d_tasks;
-        g.slabs = slabs;
+        g.slabs = F.d_slabs;
+        g.dep_off = F.d_dep_off;
+        g.deps = F.d_deps;
+        if (F.stall_next) {  // diagnostic: one dependency nothing satisfies
+            if (F.d_slabs_stall) g.slabs = F.d_slabs_stall;
+            else g.deps = F.d_deps_stall;
+            F.stall_next = false;
+        }
+        g.sig = F.d_sig;
+        g.counters = F.d_counters;
+        g.dep_nrt = n_rtiles;
+        q.tile_next = F.d_counters + size_t(F.ncounters) * n_rtiles;
         q.segs[0] = g;
         launch_gemm_coop_mode(T.mode, T.piece, q, T.num_sms, s, T.gen);
         ++launches;

@@ -71,6 +71,16 @@ struct TcSeg {
     const float* pts;
     int32_t dim, dpad, gen_kind, pad2;
     float gen_inv, gen_shift;
+    // dependency-driven launch (TcParams::tile_next set): tile (task, rt)
+    // waits until counters[c * dep_nrt + rt] >= e for every (c, e) in
+    // deps[dep_off[task] .. dep_off[task+1]) and for its slabs' operand
+    // counters, and adds one to counters[sig[2 task + i] * dep_nrt + rt]
+    // (i = 0, 1; -1 = none) per epilogue warp when done
+    const int32_t* dep_off;
+    const int32_t* deps;
+    const int32_t* sig;
+    int* counters;
+    int32_t dep_nrt, pad3;
 };
 constexpr int kGenMaxDpad = 16;  // generated blocks: at most 16 coordinates per point
 constexpr int kMaxSegs = 64;  // segments per launch (kernel parameters, by value)
@@ -81,16 +91,10 @@ struct TcParams {
     int ntiles;
     int nsegs;
     int* err;
-    // dependency-driven mode (one launch for a whole evaluation; segment 0
-    // only): tile (task, rt) waits until counters[c * dep_nrt + rt] >= e for
-    // every (c, e) in deps[dep_off[task] .. dep_off[task+1]), and adds one to
-    // counters[sig[2 task + i] * dep_nrt + rt] (i = 0, 1; -1 = none) when done
-    const int32_t* dep_off;  // nullptr: no dependencies
-    const int32_t* deps;
-    const int32_t* sig;
-    int* counters;
-    int dep_nrt;
-    int* tile_next;  // dependency mode: tiles are taken in order from this counter (dynamic)
+    // dependency-driven mode (one launch for whole evaluations, each segment
+    // with its own dependency arrays and counters): tiles are taken in list
+    // order from this counter (dynamic); nullptr: static tiles, no waits
+    int* tile_next;
     TcSeg segs[kMaxSegs];
 };
 
@@ -167,6 +171,8 @@ TcPrec& tc_plan(Handle& H, DeviceState& D, int precision);  // plan + B tiles (a
 TcSeg make_seg(const TcPrec& T, const TcLaunch& l, uint8_t* const* rt_hi, uint8_t* const* rt_lo, float* U,
                int64_t ldu, const int64_t* perm, int r);
 void launch_gemm_mode(int mode, int piece, const TcParams& p, int num_sms, cudaStream_t s, bool gen = false);
+// cooperative launch (every CTA resident): the dependency-driven mode
+void launch_gemm_coop_mode(int mode, int piece, const TcParams& p, int num_sms, cudaStream_t s, bool gen);
 // device tile list of one launch alone for n_rtiles r-tiles (cached in the launch)
 std::pair<TcTile*, int> launch_tiles(TcLaunch& l, int n_rtiles, int order, bool pair = false);
 void tc_drop_plan(DeviceState& D, int precision);  // frees one mode's plan, stores and buffers

@@ -473,15 +473,13 @@ TuneResult autotune_batch(Handle* const* hs, const int64_t* r, int count, int pr
     if (!tensor_precision(precision)) fail(GOFMM_ERR_ARG, "autotuning is for the tensor-core precisions");
     TuneResult res;
     res.key = tune_key_batch(hs, r, count, precision);
-    const int mode = precision == GOFMM_PREC_TF32 ? 0 : precision == GOFMM_PREC_BF16 ? 1 : 2;
-    auto apply_piece = [&](int piece) {
-        for (int i = 0; i < count; ++i) {
-            Handle& H = *hs[i];
-            device_set_tc_config(H, precision, piece, H.tc_schedule[mode], H.tc_order[mode]);
-        }
+    // a batch runs either as one dependency-driven launch per 64 items (every
+    // handle on the fused schedule) or as one launch per stage step
+    auto apply = [&](int piece, int schedule, int order) {
+        for (int i = 0; i < count; ++i) device_set_tc_config(*hs[i], precision, piece, schedule, order);
     };
     if (cached_choice(cache_path, res.key, res)) {
-        apply_piece(res.piece);
+        apply(res.piece, res.schedule, res.order);
         return res;
     }
     DeviceGuard g(hs[0]->st.prm.device);
@@ -497,8 +495,11 @@ TuneResult autotune_batch(Handle* const* hs, const int64_t* r, int count, int pr
         U[size_t(i)] = static_cast<float*>(bufs.back()->p);
     }
     float best = 0.f;
-    for (int piece : {256, 128}) {
-        apply_piece(piece);
+    static const int cands[4][2] = {{256, GOFMM_SCHED_FUSED}, {256, GOFMM_SCHED_STAGED},
+                                    {128, GOFMM_SCHED_FUSED}, {128, GOFMM_SCHED_STAGED}};
+    for (const auto& c : cands) {
+        const int piece = c[0], schedule = c[1];
+        apply(piece, schedule, GOFMM_ORDER_LOCAL);
         for (int i = 0; i < count; ++i) device_prepare(*hs[i], r[i], precision);
         Batch* B = batch_create(hs, r, count, precision);
         float ms = 0.f;
@@ -513,18 +514,18 @@ TuneResult autotune_batch(Handle* const* hs, const int64_t* r, int count, int pr
         }
         batch_destroy(B);
         res.cand_piece[res.n] = piece;
-        res.cand_schedule[res.n] = hs[0]->tc_schedule[mode];
-        res.cand_order[res.n] = hs[0]->tc_order[mode];
+        res.cand_schedule[res.n] = schedule;
+        res.cand_order[res.n] = GOFMM_ORDER_LOCAL;
         res.cand_ms[res.n] = ms;
         if (res.n == 0 || ms < best) {
             best = ms;
             res.piece = piece;
+            res.schedule = schedule;
+            res.order = GOFMM_ORDER_LOCAL;
         }
         ++res.n;
     }
-    res.schedule = hs[0]->tc_schedule[mode];
-    res.order = hs[0]->tc_order[mode];
-    apply_piece(res.piece);
+    apply(res.piece, res.schedule, res.order);
     for (int i = 0; i < count; ++i) device_prepare(*hs[i], r[i], precision);
     remember(cache_path, res, precision, r[0], count, device_tag(hs[0]->st.prm.device));
     return res;

@@ -111,8 +111,10 @@ def test_batch_autotune_and_stale_batch(tmp_path):
     rs = [w.r for w in insts]
     singles = [run(h, W, G.PREC_BF16) for h, W in zip(hs, Ws)]
     t = G.autotune_batch(hs, rs, G.PREC_BF16, str(tmp_path / "b.json"))
-    assert len(t["candidates"]) == 2 and t["piece"] in (128, 256)
+    assert len(t["candidates"]) == 4 and t["piece"] in (128, 256)
+    assert t["schedule"] in (G.SCHED_FUSED, G.SCHED_STAGED)
     assert all(G.get_tc_config(h, G.PREC_BF16)["piece"] == t["piece"] for h in hs)
+    assert all(G.get_tc_config(h, G.PREC_BF16)["schedule"] == t["schedule"] for h in hs)
     b = G.Batch(hs, rs, G.PREC_BF16)
     Us = [torch.full_like(W, float("nan")) for W in Ws]
     b.evaluate(Ws, Us)

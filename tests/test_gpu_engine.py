@@ -131,12 +131,21 @@ def test_engine_errors(instances):
     assert e.value.code == G.ERR_NOMEM
 
 
-def test_static_batch_matches_single_evaluations_and_replays(instances):
+@pytest.mark.parametrize("schedules", [(G.SCHED_FUSED,) * 5, (G.SCHED_STAGED,) * 5,
+                                       (G.SCHED_FUSED, G.SCHED_STAGED, G.SCHED_FUSED, G.SCHED_HYBRID,
+                                        G.SCHED_FUSED)], ids=["fused", "staged", "mixed"])
+def test_static_batch_matches_single_evaluations_and_replays(instances, schedules):
+    """All handles on the fused schedule: one dependency-driven launch runs
+    every stage of every instance; otherwise one launch per stage step.
+    Both give each instance's single evaluation bit for bit."""
     rs = [16, 256, 100, 129, 37]
     hs = [hd for _, hd in instances]
+    for hd, sc in zip(hs, schedules):
+        G.set_tc_config(hd, PREC, 256, sc, G.ORDER_LOCAL)
     Ws = [torch.from_numpy(w.rhs(r).astype(np.float32)).cuda() for (w, _), r in zip(instances, rs)]
     refs = [_single(hd, W) for hd, W in zip(hs, Ws)]
     B = G.Batch(hs, rs, PREC)
+    fused = all(sc == G.SCHED_FUSED for sc in schedules)
     Us = [torch.full_like(W, float("nan")) for W in Ws]
     for _ in range(3):  # first call direct, later calls replay the captured graph
         for U in Us:
@@ -144,5 +153,32 @@ def test_static_batch_matches_single_evaluations_and_replays(instances):
         B.evaluate(Ws, Us)
         torch.cuda.synchronize()
         assert B.info()["error"] == 0
+        # kernels per call: a gather per instance + 1 fused GEMM launch, or one per stage step
+        assert (B.info()["launches"] == len(hs) + 1) == fused
         for U, ref in zip(Us, refs):
             assert torch.equal(U, ref)
+
+
+def test_fused_batch_of_more_than_64_instances():
+    """More instances than one launch holds: one fused launch per 64, each
+    instance bitwise its single evaluation."""
+    hs, Ws = [], []
+    for i in range(67):
+        w = wl.Workload(f"b{i}", 300 + 7 * i, 3, "normal", wl.GAUSSIAN, 0.6, 1e-2, leaf_size=32, max_rank=32,
+                        tau=1e-5, kappa=8, budget=0.03, r=1, point_seed=100 + i, w_seed=900 + i)
+        K = w.matrix()
+        hd = G.compress(G.Entries.gaussian(K.points, w.bandwidth, w.shift),
+                        G.default_params(leaf_size=32, max_rank=32, tau=1e-5, kappa=8, budget=0.03))
+        G.prepare(hd, 24, PREC)
+        G.set_tc_config(hd, PREC, 128, G.SCHED_FUSED, G.ORDER_LOCAL)
+        hs.append(hd)
+        Ws.append(torch.from_numpy(w.rhs(1 + i % 24).astype(np.float32)).cuda())
+    refs = [_single(hd, W) for hd, W in zip(hs, Ws)]
+    B = G.Batch(hs, [W.shape[1] for W in Ws], PREC)
+    Us = [torch.full_like(W, float("nan")) for W in Ws]
+    B.evaluate(Ws, Us)
+    torch.cuda.synchronize()
+    assert B.info()["error"] == 0 and B.info()["launches"] == len(hs) + 2
+    for U, ref in zip(Us, refs):
+        assert torch.equal(U, ref)
+    B.free()
