@@ -462,8 +462,8 @@ Batch* batch_create(Handle* const* hs, const int64_t* r, int count, int precisio
                     if (pos[k] >= orders[k]->size()) continue;
                     more = true;
                     const int32_t task = (*orders[k])[pos[k]++];
-                    for (int rt = 0; rt < B->items[bf.items[k]].n_rtiles; ++rt)
-                        tiles.push_back(TcTile{int32_t(k), task, rt, 0});
+                    const BatchItem& it = B->items[bf.items[k]];
+                    task_tiles(tiles, int32_t(k), task, it.T->fused.tasks[size_t(task)], it.n_rtiles, it.T->piece);
                 }
             }
             bf.d_tiles = dupload(tiles);
@@ -494,9 +494,10 @@ Batch* batch_create(Handle* const* hs, const int64_t* r, int count, int precisio
                 bl.piece = std::max(bl.piece, B->items[i].T->piece);
                 bl.gen = bl.gen || B->items[i].T->gen;
                 for (size_t t = 0; t < l.tasks.size(); ++t) {
-                    const int64_t w = int64_t(l.tasks[t].nchunks) * l.tasks[t].n_pad + 1;
-                    for (int rt = 0; rt < B->items[i].n_rtiles; ++rt)
-                        tiles.emplace_back(w, TcTile{int32_t(k), int32_t(t), rt, 0});
+                    std::vector<TcTile> tt;
+                    task_tiles(tt, int32_t(k), int32_t(t), l.tasks[t], B->items[i].n_rtiles, B->items[i].T->piece);
+                    for (const TcTile& x : tt)
+                        tiles.emplace_back(int64_t(l.tasks[t].nchunks) * l.tasks[t].n_pad * x.pad + 1, x);
                 }
             }
             std::stable_sort(tiles.begin(), tiles.end(),

@@ -10,21 +10,23 @@
 // so the 128-row MMA dimension M is a tile of the r right-hand sides (always
 // full) and the ragged block height m (a skeleton or leaf size) is the MMA's
 // N (padded to a multiple of 16, at most 256; taller tasks are split).
-// Both MMA operands are K-major and 128-byte swizzled:
+// Both MMA operands are K-major:
 //   MMA A = right-hand sides in "RT" layout: for every 128 columns of r and
 //           every chunk of KC rows (128 bytes of K), one 128 x 128 B tile;
 //           node segments are padded to whole chunks (padding stays zero);
 //   MMA B = the blocks, per block and chunk one n_pad x 128 B tile.
-// Every tile sits in HBM exactly as the MMA reads it from shared memory, so
-// a single linear cp.async.bulk stages it (no tensor maps).
+// A chunk tile is stored as its two K-halves (rows x 64 B each, 64-byte
+// swizzle), one after the other.  Every half sits in HBM exactly as the MMA
+// reads it from shared memory, so a single linear cp.async.bulk stages it
+// (no tensor maps).
 //
 // Kernel: persistent, one CTA per SM looping over (task, 128-column tile of
-// r) tiles, 6 warps.  Warp 0 streams A/B chunk tiles into a ring of
-// shared-memory stages (mbarrier complete_tx); warp 1 allocates TMEM (two
-// 256-column accumulators) and one thread issues the MMAs (4 per chunk, 12
-// for BF16x3) and commits each stage back to the producer; warps 2-5 read
-// the other accumulator (tcgen05.ld) meanwhile and write the outputs: the next
-// stage's RT operand (rounded to TF32 / BF16 / BF16 hi+lo) or, for the
+// r) tiles, 6 warps.  Warp 0 streams the K-halves of the A/B chunk tiles into
+// a ring of shared-memory stages (mbarrier complete_tx); warp 1 allocates
+// TMEM (two 256-column accumulators) and one thread issues the MMAs (2 per
+// stage, 6 for BF16x3) and commits each stage back to the producer; warps 2-5
+// read the other accumulator (tcgen05.ld) meanwhile and write the outputs:
+// the next stage's RT operand (rounded to TF32 / BF16 / BF16 hi+lo) or, for the
 // leaves, U scattered to the original order in FP32.  Every wait is bounded;
 // on timeout the kernel records an error code, drains what it issued and
 // returns.
@@ -81,21 +83,38 @@ struct GenJob {
 };
 
 // NMAX: the tallest task piece the kernel accepts (MMA N ceiling, 128 or
-// 256).  A stage holds one 128 x 128 B tile of right-hand sides and one
-// NMAX x 128 B block tile (twice for split BF16x3); as many stages as fit in
-// about 200 KB of shared memory, so a lower ceiling buys a deeper pipeline.
+// 256).  A stage holds one K-half of a chunk (64 bytes of every row): the
+// halves of two 128-row right-hand-side tiles and of one NMAX-row block tile
+// (twice for split BF16x3); as many stages as fit in about 200 KB of shared
+// memory, so a lower ceiling buys a deeper pipeline.
 template <int MODE, int NMAX = kMaxN>
 struct Cfg {
     static constexpr bool kSplit = MODE == TC_BF16X3;
-    static constexpr int kStageBytes = (kSplit ? 2 : 1) * (kTileBytes + NMAX * 128);
+    // K-halves per stage: one for split BF16x3 (a stage of two r-tiles and a
+    // 256-row block is then 64 KB), both (the whole chunk) otherwise
+    static constexpr int kSub = kSplit ? 1 : 2;
+    static constexpr int kHalfA = 128 * 64;      // one K-half of a right-hand-side tile
+    static constexpr int kAUnit = kSub * kHalfA;  // one r-tile's part of a stage
+    static constexpr int kPart = 2 * kAUnit + kSub * NMAX * 64;  // hi (or lo) part of a stage
+    static constexpr int kStageBytes = (kSplit ? 2 : 1) * kPart;
     static constexpr int kStages = (200 * 1024 / kStageBytes) < 8 ? (200 * 1024 / kStageBytes) : 8;
     static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;  // + alignment slack, barriers
-    static constexpr int kKc = MODE == TC_TF32 ? 32 : 64;
+    static constexpr int kKc = MODE == TC_TF32 ? 32 : 64;  // columns per chunk
+    static constexpr int kStageK = kKc / 2 * kSub;          // columns per stage
     static constexpr int kEs = MODE == TC_TF32 ? 4 : 2;
     static constexpr int kTmemCols = 2 * NMAX;  // two accumulators
     static_assert(kStages >= 2, "at least a double-buffered stage ring");
+    // epilogue staging tile (hi and lo) of the kernels without generator warps
+    static constexpr int kEpiBytes = (kSplit ? 2 : 1) * kTileBytes;
     static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
+    static_assert(kSmem + kGenSmem <= 227 * 1024, "shared memory per CTA with generator warps");
+    static_assert(kSmem + kEpiBytes <= 227 * 1024, "shared memory per CTA with the epilogue staging tile");
 };
+// dynamic shared memory of tc_gemm_kernel<MODE, NMAX, GEN>
+template <int MODE, int NMAX, bool GEN>
+constexpr int gemm_smem() {
+    return Cfg<MODE, NMAX>::kSmem + (GEN ? kGenSmem : Cfg<MODE, NMAX>::kEpiBytes);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -117,30 +136,39 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// Polls between two looks at the grid's error flag in a bounded wait: the
+// flag is a global load (an L2 round trip), so reading it after every poll
+// would delay noticing the phase change by that round trip.
+constexpr uint32_t kPollsPerCheck = 64;
 // Bounded wait on an mbarrier phase; false (and an error code recorded) on
 // timeout or when another thread of the grid already failed.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+    if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (*reinterpret_cast<volatile int*>(err) != 0) return false;
-        if (clock64() - t0 > kSpinLimit) {
-            atomicCAS(err, 0, code);
-            return false;
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (it % kPollsPerCheck == 0) {
+            if (*reinterpret_cast<volatile int*>(err) != 0) return false;
+            if (clock64() - t0 > kSpinLimit) {
+                atomicCAS(err, 0, code);
+                return false;
+            }
         }
     }
-    return true;
 }
 // Bounded wait until *ctr >= e (acquire); false on timeout or a recorded error.
 __device__ __forceinline__ bool wait_counter(const int* ctr, int e, int* err) {
     const long long t0 = clock64();
-    for (;;) {
+    for (uint32_t it = 1;; ++it) {
         int v;
         asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
         if (v >= e) return true;
-        if (*reinterpret_cast<volatile int*>(err) != 0) return false;
-        if (clock64() - t0 > kSpinLimit) {
-            atomicCAS(err, 0, kErrDependency);
-            return false;
+        if (it % 16 == 0) {
+            if (*reinterpret_cast<volatile int*>(err) != 0) return false;
+            if (clock64() - t0 > kSpinLimit) {
+                atomicCAS(err, 0, kErrDependency);
+                return false;
+            }
         }
         __nanosleep(64);
     }
@@ -153,15 +181,15 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (tile rows at a 128-byte stride).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups
+// 512 bytes apart (tile rows at a 64-byte stride).
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= uint64_t((saddr & 0x3FFFFu) >> 4);  // start address
     d |= uint64_t(1) << 16;                   // leading byte offset (unused when swizzled)
-    d |= uint64_t(1024 >> 4) << 32;           // stride byte offset
+    d |= uint64_t(512 >> 4) << 32;            // stride byte offset
     d |= uint64_t(1) << 46;                   // descriptor version
-    d |= uint64_t(2) << 61;                   // 128-byte swizzle
+    d |= uint64_t(4) << 61;                   // 64-byte swizzle
     return d;
 }
 // Instruction descriptor (kind::tf32 / kind::f16): FP32 accumulator, both
@@ -208,15 +236,46 @@ __device__ __forceinline__ float round_tf32(float x) {
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
     return __uint_as_float(y);
 }
-// byte position of (row, byte-in-row) inside a 128-byte-swizzled tile
-__device__ __forceinline__ uint32_t swz(uint32_t row, uint32_t byte) {
-    return row * 128u + ((((byte >> 4) ^ (row & 7u)) << 4) | (byte & 15u));
+// Operand tile layout.  A chunk tile (rows x 128 bytes: kc columns of every
+// row) is stored as two K-halves, each rows x 64 bytes with the 64-byte
+// swizzle (16-byte group g of row n at group g ^ ((n >> 1) & 3)), so one
+// half is one contiguous copy and one shared-memory stage.
+// byte position of (row, byte-in-row < 64) inside one half
+__device__ __forceinline__ uint32_t swz64(uint32_t row, uint32_t byte) {
+    return row * 64u + ((((byte >> 4) ^ ((row >> 1) & 3u)) << 4) | (byte & 15u));
+}
+// byte position of (row, byte-in-row < 128) inside a chunk tile of `rows` rows
+__device__ __forceinline__ uint32_t swz(uint32_t row, uint32_t byte, uint32_t rows) {
+    return (byte >> 6) * rows * 64u + swz64(row, byte & 63u);
 }
 
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
+// Named barrier 2 over the four epilogue warps, and its reduction form
+// (true iff every epilogue thread passes true).
+__device__ __forceinline__ void epi_bar_sync() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
+__device__ __forceinline__ int epi_bar_and(bool pred) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 2, 128, p;\n\tselp.b32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(int(pred))
+        : "memory");
+    return r;
+}
+// Bulk store shared -> global (16-byte aligned, size a multiple of 16) and
+// its completion waits: .read = the source may be overwritten; plain = the
+// writes are performed.
+__device__ __forceinline__ void bulk_s2g(void* dst, uint32_t src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Tile t of a launch: from the merged list, or (segment tile lists) from the
 // list of the segment whose range holds t.
@@ -228,6 +287,13 @@ __device__ __forceinline__ TcTile fetch_tile(const TcParams& p, int t) {
     tt.seg = k;
     return tt;
 }
+// r-tiles a tile covers: rt alone, or rt and rt + 1 (two accumulators fed
+// from one block stage)
+__device__ __forceinline__ int tile_width(const TcTile& tt) { return tt.pad == 2 ? 2 : 1; }
+// TMEM accumulator buffers (NMAX columns each) a tile takes: one, or both
+// when it has two accumulators of more than NMAX / 2 columns (two narrower
+// ones share a buffer, at columns 0 and NMAX / 2)
+__device__ __forceinline__ int acc_buffers(int nw, int n_pad, int nmax) { return nw == 2 && 2 * n_pad > nmax ? 2 : 1; }
 
 // Epilogue of one tile: the accumulator rows of this thread (one column j
 // of r) for the task's n_pad block rows, read from TMEM at taddr and written
@@ -238,6 +304,7 @@ __device__ __forceinline__ void write_tile(const TcSeg& sg, const TcTask& tk, in
     using C = Cfg<MODE>;
     const int j = rt * 128 + row;
     const bool jv = j < sg.r;
+    const int lane = row & 31;
     const int ncols = tk.out_kind == OUT_U ? tk.n_pad : (tk.accumulate ? tk.n_pad : tk.out_cols);
     for (int n0 = 0; n0 < ncols; n0 += 32) {
         float v[32];
@@ -251,13 +318,24 @@ __device__ __forceinline__ void write_tile(const TcSeg& sg, const TcTask& tk, in
             for (int e = 0; e < 32; ++e) v[e] = 0.f;
         }
         if (tk.out_kind == OUT_U) {
-            if (!jv) continue;
+            // U rows perm[out_pos + n0 .. + 32): lane l loads the row index of
+            // n0 + l, the warp shares them by shuffles; all loads of the 32
+            // rows are issued before the first add (one latency, not 32)
+            const int nl = n0 + lane;
+            const int64_t prow = nl < tk.m ? sg.perm[tk.out_pos + nl] : 0;
 #pragma unroll
-            for (int e = 0; e < 32; ++e) {
-                const int n = n0 + e;
-                if (n < tk.m) {
-                    float* d = sg.U + sg.perm[tk.out_pos + n] * sg.ldu + j;
-                    *d = tk.accumulate ? *d + v[e] : v[e];
+            for (int e0 = 0; e0 < 32; e0 += 16) {  // 16 rows at a time (registers)
+                float old[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int64_t pr = __shfl_sync(0xffffffffu, prow, e0 + e);
+                    old[e] = (tk.accumulate && jv && n0 + e0 + e < tk.m) ? sg.U[pr * sg.ldu + j] : 0.f;
+                }
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int64_t pr = __shfl_sync(0xffffffffu, prow, e0 + e);
+                    if (jv && n0 + e0 + e < tk.m)
+                        sg.U[pr * sg.ldu + j] = tk.accumulate ? old[e] + v[e0 + e] : v[e0 + e];
                 }
             }
             continue;
@@ -269,48 +347,122 @@ __device__ __forceinline__ void write_tile(const TcSeg& sg, const TcTask& tk, in
         const uint32_t byte0 = uint32_t((n0 % C::kKc) * C::kEs);
         uint8_t* thi = sg.rt_hi[buf] + (int64_t(rt) * sg.rt_chunks[buf] + chunk) * kTileBytes;
         if constexpr (MODE == TC_TF32) {
+            // accumulating: every existing 16-byte group loaded first
+            float4 ex[8];
+#pragma unroll
+            for (int piece = 0; piece < 8; ++piece) {
+                ex[piece] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (tk.accumulate && n0 + 4 * piece < tk.n_pad)
+                    ex[piece] = *reinterpret_cast<const float4*>(thi + swz(row, byte0 + piece * 16, 128));
+            }
 #pragma unroll
             for (int piece = 0; piece < 8; ++piece) {
                 if (tk.accumulate && n0 + 4 * piece >= tk.n_pad) break;
-                float4* dst = reinterpret_cast<float4*>(thi + swz(row, byte0 + piece * 16));
+                float4* dst = reinterpret_cast<float4*>(thi + swz(row, byte0 + piece * 16, 128));
                 float4 o = make_float4(v[4 * piece], v[4 * piece + 1], v[4 * piece + 2], v[4 * piece + 3]);
                 if (tk.accumulate) {
-                    const float4 e = *dst;
-                    o.x += e.x; o.y += e.y; o.z += e.z; o.w += e.w;
+                    o.x += ex[piece].x; o.y += ex[piece].y; o.z += ex[piece].z; o.w += ex[piece].w;
                 }
                 *dst = make_float4(round_tf32(o.x), round_tf32(o.y), round_tf32(o.z), round_tf32(o.w));
             }
         } else {
             uint8_t* tlo = C::kSplit ? sg.rt_lo[buf] + (int64_t(rt) * sg.rt_chunks[buf] + chunk) * kTileBytes
                                      : nullptr;
+            // accumulating: every existing 16-byte group (hi and lo) loaded first
+            uint4 eh[4], el[4];
+#pragma unroll
+            for (int piece = 0; piece < 4; ++piece) {
+                eh[piece] = make_uint4(0, 0, 0, 0);
+                el[piece] = make_uint4(0, 0, 0, 0);
+                if (tk.accumulate && n0 + 8 * piece < tk.n_pad) {
+                    const uint32_t pos = swz(row, byte0 + piece * 16, 128);
+                    eh[piece] = *reinterpret_cast<const uint4*>(thi + pos);
+                    if constexpr (C::kSplit) el[piece] = *reinterpret_cast<const uint4*>(tlo + pos);
+                }
+            }
 #pragma unroll
             for (int piece = 0; piece < 4; ++piece) {
                 if (tk.accumulate && n0 + 8 * piece >= tk.n_pad) break;
-                const uint32_t pos = swz(row, byte0 + piece * 16);
-                float x[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) x[e] = v[8 * piece + e];
-                if (tk.accumulate) {
-                    const uint4 eh = *reinterpret_cast<const uint4*>(thi + pos);
-                    const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&eh);
-                    uint4 el = make_uint4(0, 0, 0, 0);
-                    if constexpr (C::kSplit) el = *reinterpret_cast<const uint4*>(tlo + pos);
-                    const __nv_bfloat16* l = reinterpret_cast<const __nv_bfloat16*>(&el);
-#pragma unroll
-                    for (int e = 0; e < 8; ++e)
-                        x[e] += __bfloat162float(h[e]) + (C::kSplit ? __bfloat162float(l[e]) : 0.f);
-                }
+                const uint32_t pos = swz(row, byte0 + piece * 16, 128);
+                const __nv_bfloat16* h = reinterpret_cast<const __nv_bfloat16*>(&eh[piece]);
+                const __nv_bfloat16* l = reinterpret_cast<const __nv_bfloat16*>(&el[piece]);
                 uint4 oh, ol;
                 __nv_bfloat16* hh = reinterpret_cast<__nv_bfloat16*>(&oh);
                 __nv_bfloat16* ll = reinterpret_cast<__nv_bfloat16*>(&ol);
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    hh[e] = __float2bfloat16_rn(x[e]);
-                    ll[e] = __float2bfloat16_rn(x[e] - __bfloat162float(hh[e]));
+                    float x = v[8 * piece + e];
+                    if (tk.accumulate) x += __bfloat162float(h[e]) + (C::kSplit ? __bfloat162float(l[e]) : 0.f);
+                    hh[e] = __float2bfloat16_rn(x);
+                    ll[e] = __float2bfloat16_rn(x - __bfloat162float(hh[e]));
                 }
                 *reinterpret_cast<uint4*>(thi + pos) = oh;
                 if constexpr (C::kSplit) *reinterpret_cast<uint4*>(tlo + pos) = ol;
             }
+        }
+    }
+}
+
+// Epilogue of one tile whose output is a fresh RT segment (no accumulation):
+// chunk by chunk, the four epilogue warps write their rows into the staging
+// tile in the operand layout (zeros in the padding columns and in rows
+// j >= r) and one thread stores each 16 KB chunk tile (and its lo copy) with
+// a bulk copy.  The store thread waits for the previous chunk's copies to
+// have read the staging tile before it is written again.
+template <int MODE>
+__device__ __forceinline__ void write_tile_staged(const TcSeg& sg, const TcTask& tk, int rt, int row, uint32_t taddr,
+                                                  uint8_t* stg, bool store_thread) {
+    using C = Cfg<MODE>;
+    const int j = rt * 128 + row;
+    const bool jv = j < sg.r;
+    const int buf = tk.out_kind == OUT_WTIL ? 1 : 2;
+    for (int ch = 0; ch * C::kKc < tk.out_cols; ++ch) {
+        if (store_thread) bulk_wait_read();
+        epi_bar_sync();
+#pragma unroll
+        for (int h = 0; h < C::kKc; h += 32) {  // 32 columns per TMEM load
+            const int n0 = ch * C::kKc + h;
+            float v[32];
+            if (tk.nchunks > 0 && n0 < tk.n_pad) {
+                tmem_ld32(taddr + uint32_t(n0), v);
+#pragma unroll
+                for (int e = 0; e < 32; ++e)
+                    if (n0 + e >= tk.n_pad || !jv) v[e] = 0.f;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 32; ++e) v[e] = 0.f;
+            }
+            const uint32_t byte0 = uint32_t(h * C::kEs);
+            if constexpr (MODE == TC_TF32) {
+#pragma unroll
+                for (int piece = 0; piece < 8; ++piece)
+                    *reinterpret_cast<float4*>(stg + swz(row, byte0 + piece * 16, 128)) =
+                        make_float4(round_tf32(v[4 * piece]), round_tf32(v[4 * piece + 1]),
+                                    round_tf32(v[4 * piece + 2]), round_tf32(v[4 * piece + 3]));
+            } else {
+#pragma unroll
+                for (int piece = 0; piece < 4; ++piece) {
+                    uint4 oh, ol;
+                    __nv_bfloat16* hh = reinterpret_cast<__nv_bfloat16*>(&oh);
+                    __nv_bfloat16* ll = reinterpret_cast<__nv_bfloat16*>(&ol);
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        hh[e] = __float2bfloat16_rn(v[8 * piece + e]);
+                        ll[e] = __float2bfloat16_rn(v[8 * piece + e] - __bfloat162float(hh[e]));
+                    }
+                    const uint32_t pos = swz(row, byte0 + piece * 16, 128);
+                    *reinterpret_cast<uint4*>(stg + pos) = oh;
+                    if constexpr (C::kSplit) *reinterpret_cast<uint4*>(stg + kTileBytes + pos) = ol;
+                }
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> the bulk copy
+        epi_bar_sync();
+        if (store_thread) {
+            const int64_t at = (int64_t(rt) * sg.rt_chunks[buf] + tk.out_pos + ch) * kTileBytes;
+            bulk_s2g(sg.rt_hi[buf] + at, smem_u32(stg), kTileBytes);
+            if constexpr (C::kSplit) bulk_s2g(sg.rt_lo[buf] + at, smem_u32(stg + kTileBytes), kTileBytes);
+            bulk_commit();
         }
     }
 }
@@ -348,9 +500,10 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
     auto idfull_bar = [&](int a) { return smem_u32(&bars[2 * C::kStages + 5 + a]); };
     auto idempty_bar = [&](int a) { return smem_u32(&bars[2 * C::kStages + 7 + a]); };
     const bool dyn = p.tile_next != nullptr;  // dynamic tile order (dependency mode)
-    // stage s: A_hi | B_hi | (A_lo | B_lo)
-    auto sA = [&](int s, int lo) { return s_base + s * C::kStageBytes + lo * (kTileBytes + NMAX * 128); };
-    auto sB = [&](int s, int lo) { return sA(s, lo) + kTileBytes; };
+    // stage s: A0_hi | A1_hi | B_hi | (A0_lo | A1_lo | B_lo): kSub K-halves of
+    // the right-hand-side tiles of r-tiles rt and rt + 1 and of the block tile
+    auto sA = [&](int s, int lo, int w) { return s_base + s * C::kStageBytes + lo * C::kPart + w * C::kAUnit; };
+    auto sB = [&](int s, int lo) { return s_base + s * C::kStageBytes + lo * C::kPart + 2 * C::kAUnit; };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntiles = p.ntiles;
@@ -391,7 +544,7 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---- producer: stream chunk tiles of every tile of this CTA
+            // ---- producer: stream the operand stages of every tile of this CTA
             int stage = 0, issued = 0, gseq = 0;
             uint32_t phase = 0;
             bool ok = true;
@@ -410,13 +563,15 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
                 const TcSeg& sg = p.segs[tt.seg];
                 const TcTask tk = sg.tasks[tt.task];
                 const int rt = tt.rt;
-                const uint32_t b_bytes = uint32_t(tk.n_pad) * 128u;
+                const int nw = tile_width(tt);
+                const uint32_t b_half = uint32_t(tk.n_pad) * 64u;  // one K-half of a block chunk tile
                 if (dyn) {
                     // results of other tiles of this launch the task needs
                     // before it starts (the operands are waited for slab by slab)
                     for (int d = sg.dep_off[tt.task]; d < sg.dep_off[tt.task + 1] && ok; ++d)
-                        ok = wait_counter(sg.counters + int64_t(sg.deps[2 * d]) * sg.dep_nrt + rt, sg.deps[2 * d + 1],
-                                          p.err);
+                        for (int w = 0; w < nw && ok; ++w)
+                            ok = wait_counter(sg.counters + int64_t(sg.deps[2 * d]) * sg.dep_nrt + rt + w,
+                                              sg.deps[2 * d + 1], p.err);
                     if (!ok) break;
                 }
                 for (int si = tk.slab0; si < tk.slab1 && ok; ++si) {
@@ -425,47 +580,16 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
                         // this slab's right-hand sides, written earlier in the
                         // launch by other tiles: wait (bounded), then make the
                         // generic writes visible to the bulk copies
-                        if (sl.dep_c0 >= 0)
-                            ok = wait_counter(sg.counters + int64_t(sl.dep_c0) * sg.dep_nrt + rt, sl.dep_n0, p.err);
-                        if (ok && sl.dep_c1 >= 0)
-                            ok = wait_counter(sg.counters + int64_t(sl.dep_c1) * sg.dep_nrt + rt, sl.dep_n1, p.err);
+                        for (int w = 0; w < nw && ok; ++w) {
+                            if (sl.dep_c0 >= 0)
+                                ok = wait_counter(sg.counters + int64_t(sl.dep_c0) * sg.dep_nrt + rt + w, sl.dep_n0,
+                                                  p.err);
+                            if (ok && sl.dep_c1 >= 0)
+                                ok = wait_counter(sg.counters + int64_t(sl.dep_c1) * sg.dep_nrt + rt + w, sl.dep_n1,
+                                                  p.err);
+                        }
                         if (!ok) break;
                         asm volatile("fence.proxy.async.global;" ::: "memory");
-                    }
-                    const int64_t a_off = (int64_t(rt) * sg.rt_chunks[sl.a_buf] + sl.a_chunk0) * kTileBytes;
-                    const uint8_t* a_hi = sg.rt_hi[sl.a_buf] + a_off;
-                    if constexpr (GEN) {
-                        if (sl.gen) {
-                            // block tiles generated by the generator warps; only
-                            // the right-hand-side tiles are copied
-                            for (int c = 0; c < sl.nchunks; ++c) {
-                                if (!mbar_wait(empty_bar(stage), phase ^ 1u, p.err, kErrProducer)) { ok = false; break; }
-                                const int j = gseq % C::kStages;
-                                if (!mbar_wait(genq_empty(j), uint32_t(((gseq / C::kStages) & 1) ^ 1), p.err,
-                                               kErrProducer)) { ok = false; break; }
-                                GenJob& jb = jobs[j];
-                                jb.rows = sl.b_off;
-                                jb.cols = sl.gen_cols + int64_t(c) * C::kKc;
-                                jb.cols_end = sl.gen_cols + sl.k;
-                                jb.seg = tt.seg;
-                                jb.stage = stage;
-                                jb.m = tk.m;
-                                jb.kvalid = min(C::kKc, sl.k - c * C::kKc);
-                                jb.n_pad = tk.n_pad;
-                                jb.stop = 0;
-                                mbar_arrive(genq_full(j));
-                                ++gseq;
-                                stage_isgen[stage] = 1;
-                                mbar_expect_tx(full_bar(stage), (C::kSplit ? 2u : 1u) * kTileBytes);
-                                bulk_g2s(sA(stage, 0), a_hi + int64_t(c) * kTileBytes, kTileBytes, full_bar(stage));
-                                if constexpr (C::kSplit)
-                                    bulk_g2s(sA(stage, 1), sg.rt_lo[sl.a_buf] + a_off + int64_t(c) * kTileBytes,
-                                             kTileBytes, full_bar(stage));
-                                ++issued;
-                                if (++stage == C::kStages) { stage = 0; phase ^= 1u; }
-                            }
-                            continue;
-                        }
                     }
                     if constexpr (!GEN) {
                         if (sl.gen) {  // the host launches the generator variant for these; never read as tiles
@@ -474,18 +598,48 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
                             break;
                         }
                     }
-                    const uint8_t* b_hi = sg.b_hi + sl.b_off;
-                    for (int c = 0; c < sl.nchunks; ++c) {
+                    // r-tile rt + w of the slab's right-hand sides: a_hi + w * a_rt
+                    const int64_t a_off = (int64_t(rt) * sg.rt_chunks[sl.a_buf] + sl.a_chunk0) * kTileBytes;
+                    const int64_t a_rt = int64_t(sg.rt_chunks[sl.a_buf]) * kTileBytes;
+                    const uint8_t* a_hi = sg.rt_hi[sl.a_buf] + a_off;
+                    const uint8_t* a_lo = C::kSplit ? sg.rt_lo[sl.a_buf] + a_off : nullptr;
+                    const bool gen = GEN && sl.gen;  // block tiles written by the generator warps
+                    const uint32_t b_stage = gen ? 0u : uint32_t(C::kSub) * b_half;
+                    for (int q = 0; q < 2 * sl.nchunks / C::kSub; ++q) {
                         if (!mbar_wait(empty_bar(stage), phase ^ 1u, p.err, kErrProducer)) { ok = false; break; }
-                        if constexpr (GEN) stage_isgen[stage] = 0;
-                        mbar_expect_tx(full_bar(stage), (C::kSplit ? 2u : 1u) * (kTileBytes + b_bytes));
-                        bulk_g2s(sA(stage, 0), a_hi + int64_t(c) * kTileBytes, kTileBytes, full_bar(stage));
-                        bulk_g2s(sB(stage, 0), b_hi + int64_t(c) * b_bytes, b_bytes, full_bar(stage));
-                        if constexpr (C::kSplit) {
-                            bulk_g2s(sA(stage, 1), sg.rt_lo[sl.a_buf] + a_off + int64_t(c) * kTileBytes, kTileBytes,
-                                     full_bar(stage));
-                            bulk_g2s(sB(stage, 1), sg.b_lo + sl.b_off + int64_t(c) * b_bytes, b_bytes,
-                                     full_bar(stage));
+                        if constexpr (GEN) {
+                            stage_isgen[stage] = gen ? 1 : 0;
+                            if (gen) {
+                                const int j = gseq % C::kStages;
+                                if (!mbar_wait(genq_empty(j), uint32_t(((gseq / C::kStages) & 1) ^ 1), p.err,
+                                               kErrProducer)) { ok = false; break; }
+                                GenJob& jb = jobs[j];
+                                jb.rows = sl.b_off;
+                                jb.cols = sl.gen_cols + int64_t(q) * C::kStageK;
+                                jb.cols_end = sl.gen_cols + sl.k;
+                                jb.seg = tt.seg;
+                                jb.stage = stage;
+                                jb.m = tk.m;
+                                jb.kvalid = max(0, min(C::kStageK, sl.k - q * C::kStageK));
+                                jb.n_pad = tk.n_pad;
+                                jb.stop = 0;
+                                mbar_arrive(genq_full(j));
+                                ++gseq;
+                            }
+                        }
+                        // stage q: K-halves [q kSub, (q + 1) kSub) of the slab's chunks
+                        const int64_t ah = int64_t(q) * C::kAUnit;
+                        const int64_t bh = int64_t(q) * b_stage;
+                        mbar_expect_tx(full_bar(stage), (C::kSplit ? 2u : 1u) * (uint32_t(nw) * C::kAUnit + b_stage));
+                        for (int w = 0; w < nw; ++w) {
+                            bulk_g2s(sA(stage, 0, w), a_hi + w * a_rt + ah, C::kAUnit, full_bar(stage));
+                            if constexpr (C::kSplit)
+                                bulk_g2s(sA(stage, 1, w), a_lo + w * a_rt + ah, C::kAUnit, full_bar(stage));
+                        }
+                        if (!gen) {
+                            bulk_g2s(sB(stage, 0), sg.b_hi + sl.b_off + bh, b_stage, full_bar(stage));
+                            if constexpr (C::kSplit)
+                                bulk_g2s(sB(stage, 1), sg.b_lo + sl.b_off + bh, b_stage, full_bar(stage));
                         }
                         ++issued;
                         if (++stage == C::kStages) { stage = 0; phase ^= 1u; }
@@ -514,8 +668,10 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // ---- MMA issuer (one thread)
-            int stage = 0, i = 0;
+            // ---- MMA issuer (one thread).  Accumulator buffers: a one-r-tile
+            // tile takes the next of the two in turn, a two-r-tile tile both.
+            int stage = 0, i = 0, bnext = 0;
+            uint32_t fills = 0;  // bit b: parity of the fills of accumulator buffer b
             uint32_t phase = 0, genpar = 0;
             bool ok = true;
             for (int t = blockIdx.x; ok; t += gridDim.x, ++i) {
@@ -528,12 +684,19 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
                 if (t >= ntiles) break;
                 const TcTile tt = fetch_tile(p, t);
                 const TcTask tk = p.segs[tt.seg].tasks[tt.task];
-                const int acc = i & 1;
-                if (!mbar_wait(tempty_bar(acc), uint32_t(((i >> 1) & 1) ^ 1), p.err, kErrMma)) break;
+                const int nw = tile_width(tt);
+                const int nb = acc_buffers(nw, tk.n_pad, NMAX);
+                const int b0 = nb == 2 ? 0 : bnext;
+                if (nb == 1) bnext ^= 1;
+                for (int b = 0; b < nb && ok; ++b)
+                    ok = mbar_wait(tempty_bar(b0 + b), ((fills >> (b0 + b)) & 1u) ^ 1u, p.err, kErrMma);
+                if (!ok) break;
                 tc_fence_after();
-                const uint32_t tacc = tmem + uint32_t(acc * NMAX);
+                const uint32_t tacc = tmem + uint32_t(b0 * NMAX);  // r-tile rt + w: tacc + w * acc_step
+                const uint32_t acc_step = uint32_t(nb == 2 ? NMAX : NMAX / 2);
                 const uint32_t idesc = make_idesc(MODE == TC_TF32 ? 2 : 1, tk.n_pad);
-                for (int q = 0; q < tk.nchunks; ++q) {
+                const uint32_t b_half = uint32_t(tk.n_pad) * 64u;
+                for (int q = 0; q < 2 * tk.nchunks / C::kSub; ++q) {
                     if (!mbar_wait(full_bar(stage), phase, p.err, kErrMma)) { ok = false; break; }
                     if constexpr (GEN) {
                         if (stage_isgen[stage]) {  // block tile written by the generator warps
@@ -545,21 +708,38 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
                         }
                     }
                     tc_fence_after();
-                    const uint64_t da = sw128_desc(sA(stage, 0)), db = sw128_desc(sB(stage, 0));
+                    // one descriptor per stage; the operands' descriptors differ
+                    // from it by their shared-memory offsets (in 16-byte units)
+                    const uint64_t d0 = sw64_desc(sA(stage, 0, 0));
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t off = uint64_t(kk * 2);  // 32 bytes per MMA K step, in 16-byte units
-                        mma<MODE>(tacc, da + off, db + off, idesc, (q > 0 || kk > 0) ? 1u : 0u);
-                        if constexpr (C::kSplit) {
-                            const uint64_t dal = sw128_desc(sA(stage, 1)), dbl = sw128_desc(sB(stage, 1));
-                            mma<MODE>(tacc, da + off, dbl + off, idesc, 1u);
-                            mma<MODE>(tacc, dal + off, db + off, idesc, 1u);
+                    for (int hs = 0; hs < C::kSub; ++hs) {
+                        const uint64_t db = d0 + (uint32_t(2 * C::kAUnit + hs * b_half) >> 4);
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+                            const uint64_t off = uint64_t(kk * 2);  // 32 bytes per MMA K step
+                            const uint32_t acc_in = (q > 0 || hs > 0 || kk > 0) ? 1u : 0u;
+#pragma unroll
+                            for (int w = 0; w < 2; ++w) {
+                                if (w < nw) {
+                                    const uint64_t da = d0 + uint64_t((w * C::kAUnit + hs * C::kHalfA) >> 4) + off;
+                                    const uint32_t tw = tacc + uint32_t(w) * acc_step;
+                                    mma<MODE>(tw, da, db + off, idesc, acc_in);
+                                    if constexpr (C::kSplit) {
+                                        constexpr uint64_t lo = uint64_t(C::kPart >> 4);
+                                        mma<MODE>(tw, da, db + lo + off, idesc, 1u);
+                                        mma<MODE>(tw, da + lo, db + off, idesc, 1u);
+                                    }
+                                }
+                            }
                         }
                     }
                     mma_commit(empty_bar(stage));
                     if (++stage == C::kStages) { stage = 0; phase ^= 1u; }
                 }
-                mma_commit(tfull_bar(acc));
+                for (int b = 0; b < nb; ++b) {
+                    mma_commit(tfull_bar(b0 + b));
+                    fills ^= 1u << (b0 + b);
+                }
             }
             // no MMA may still be running when TMEM is freed
             mma_commit(drain_bar);
@@ -571,11 +751,14 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
         // ---- epilogue: warps 2..5 own TMEM lane quarters (warp % 4)
         const int q4 = warp & 3;
         const int row = q4 * 32 + lane;  // row of the MMA tile = column of r
-        int i = 0;
+        const bool store_thread = warp == 2 && lane == 0;  // issues the staged tiles' bulk stores
+        uint8_t* stg = base + C::kStages * C::kStageBytes + 256;  // staging tile (kernels without generator warps)
+        int i = 0, bnext = 0;
+        uint32_t fills = 0;  // the MMA issuer's buffer sequence, replayed
         for (int t = blockIdx.x;; t += gridDim.x, ++i) {
             if (dyn) {
                 bool okid = mbar_wait(idfull_bar(i & 1), uint32_t((i >> 1) & 1), p.err, kErrEpilogue);
-                okid = __all_sync(0xffffffffu, okid);
+                okid = epi_bar_and(okid) != 0;  // the four warps leave together (they share barrier 2)
                 if (!okid) break;
                 t = tid_slot[i & 1];
                 __syncwarp();
@@ -587,41 +770,66 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
             const TcSeg& sg = p.segs[tt.seg];
             const TcTask tk = sg.tasks[tt.task];
             const int rt = tt.rt;
-            const int acc = i & 1;
-            bool ok = mbar_wait(tfull_bar(acc), uint32_t((i >> 1) & 1), p.err, kErrEpilogue);
-            ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
+            const int nw = tile_width(tt);
+            const int nb = acc_buffers(nw, tk.n_pad, NMAX);
+            const int b0 = nb == 2 ? 0 : bnext;
+            if (nb == 1) bnext ^= 1;
+            const int acc_step = nb == 2 ? NMAX : NMAX / 2;
+            bool ok = true;
+            for (int b = 0; b < nb && ok; ++b)
+                ok = mbar_wait(tfull_bar(b0 + b), (fills >> (b0 + b)) & 1u, p.err, kErrEpilogue);
+            // tcgen05.ld below is warp-collective, and the four warps share
+            // barrier 2 (staged stores): all of them go on or none
+            ok = epi_bar_and(ok) != 0;
             if (!ok) break;
             tc_fence_after();
-            const uint32_t taddr = tmem + uint32_t(acc * NMAX) + (uint32_t(q4 * 32) << 16);
             // RT outputs write the whole output segment of the task (zeros in the
             // padding columns and in rows j >= r), so every RT element a later
             // stage reads was written earlier in the same evaluation; only the
             // in-place S2N pushes touch valid elements alone.
-            write_tile<MODE>(sg, tk, rt, row, taddr);
-            // accumulator buffer free for the MMA of the tile after next
+            const bool staged = !GEN && tk.out_kind != OUT_U && !tk.accumulate;
+            for (int w = 0; w < nw; ++w) {
+                const uint32_t taddr = tmem + uint32_t(b0 * NMAX + w * acc_step) + (uint32_t(q4 * 32) << 16);
+                if (staged)
+                    write_tile_staged<MODE>(sg, tk, rt + w, row, taddr, stg, store_thread);
+                else
+                    write_tile<MODE>(sg, tk, rt + w, row, taddr);
+            }
+            // accumulator buffers free for the MMAs of a later tile
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(tempty_bar(acc));
+            for (int b = 0; b < nb; ++b) {
+                if (lane == 0) mbar_arrive(tempty_bar(b0 + b));
+                fills ^= 1u << (b0 + b);
+            }
             if (dyn) {
                 // publish this warp's 32 rows of the tile: consumers wait for
                 // four arrivals (one per epilogue warp) per task piece
                 const int s0 = sg.sig[2 * tt.task], s1 = sg.sig[2 * tt.task + 1];
                 if (s0 >= 0 || s1 >= 0) {
+                    if (staged) {
+                        // the bulk stores of the tile performed before any warp publishes
+                        if (store_thread) bulk_wait_all();
+                        epi_bar_sync();
+                    }
                     asm volatile("fence.proxy.async.global;" ::: "memory");
                     __syncwarp();
                     if (lane == 0) {
                         __threadfence();
-                        if (s0 >= 0) atomicAdd(sg.counters + int64_t(s0) * sg.dep_nrt + rt, 1);
-                        if (s1 >= 0) atomicAdd(sg.counters + int64_t(s1) * sg.dep_nrt + rt, 1);
+                        for (int w = 0; w < nw; ++w) {
+                            if (s0 >= 0) atomicAdd(sg.counters + int64_t(s0) * sg.dep_nrt + rt + w, 1);
+                            if (s1 >= 0) atomicAdd(sg.counters + int64_t(s1) * sg.dep_nrt + rt + w, 1);
+                        }
                     }
                 }
             }
         }
+        if (store_thread) bulk_wait_all();  // no bulk store may still read the staging tile
     } else {
         if constexpr (GEN) {
             // ---- generator warps 6..13: block tiles of generated slabs,
             // written into the stage's B region in the MMA layout (row n,
-            // 16-byte group g of 8 BF16 / 4 TF32 columns, 128-byte swizzle).
+            // 16-byte group g of 8 BF16 / 4 TF32 columns, 64-byte swizzle).
             // The eight warps work on one chunk at a time (named barrier 1):
             // the task piece's row points stay in shared memory across its
             // chunks, each chunk brings its column points.
@@ -665,19 +873,19 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
                         (jb.cols == pf_cols && jb.seg == pf_seg) ? pf : tab[jb.cols * (dp / 4) + gt];
                 pf_cols = -1;
                 {
-                    const int64_t nc = jb.cols + C::kKc;
+                    const int64_t nc = jb.cols + C::kStageK;
                     if (nc < jb.cols_end) {
-                        const int nk = int(jb.cols_end - nc < C::kKc ? jb.cols_end - nc : C::kKc);
+                        const int nk = int(jb.cols_end - nc < C::kStageK ? jb.cols_end - nc : C::kStageK);
                         if (gt < nk * dp / 4) pf = tab[nc * (dp / 4) + gt];
                         pf_cols = nc;
                         pf_seg = jb.seg;
                     }
                 }
                 gen_bar_sync();  // points in shared memory
-                uint8_t* bh = base + jb.stage * C::kStageBytes + kTileBytes;
-                uint8_t* bl = bh + kTileBytes + NMAX * 128;  // split BF16x3: the lo copy of the stage
+                uint8_t* bh = base + jb.stage * C::kStageBytes + 2 * C::kAUnit;
+                uint8_t* bl = bh + C::kPart;  // split BF16x3: the lo copy of the stage
                 constexpr int kPer = MODE == TC_TF32 ? 4 : 8;  // columns per 16-byte group
-                for (int it = gt; it < jb.n_pad * 8; it += kGenWarps * 32) {
+                for (int it = gt; it < jb.n_pad * 4 * C::kSub; it += kGenWarps * 32) {
                     // a warp: 32 consecutive rows of one column group (the
                     // column points are then the same word for the whole warp)
                     const int n = it % jb.n_pad, g = it / jb.n_pad;
@@ -712,7 +920,8 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
                             }
                         }
                     }
-                    const uint32_t pos = swz(uint32_t(n), uint32_t(g * 16));
+                    // group g of the stage: K-half g / 4, 16-byte group g % 4 of it
+                    const uint32_t pos = uint32_t(g >> 2) * uint32_t(jb.n_pad) * 64u + swz64(uint32_t(n), uint32_t((g & 3) * 16));
                     if constexpr (MODE == TC_TF32) {
                         *reinterpret_cast<float4*>(bh + pos) =
                             make_float4(round_tf32(v[0]), round_tf32(v[1]), round_tf32(v[2]), round_tf32(v[3]));
@@ -768,6 +977,7 @@ template <int MODE, int NMAX>
 struct Cfg2 {
     static constexpr bool kSplit = MODE == TC_BF16X3;
     static constexpr int kBHalf = NMAX / 2 * 128;  // bytes of one CTA's half block tile
+    static constexpr int kBQuarter = NMAX / 2 * 64;  // ... of one K-half of it
     static constexpr int kStageBytes = (kSplit ? 2 : 1) * (kTileBytes + kBHalf);
     static constexpr int kStages = (200 * 1024 / kStageBytes) < 8 ? (200 * 1024 / kStageBytes) : 8;
     static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;
@@ -802,15 +1012,18 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint32_t bar, uint32_t par
 }
 // Bounded wait with cluster-scope acquire (arrivals from the other CTA).
 __device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, int* err, int code) {
+    if (mbar_try_wait_cluster(bar, parity)) return true;
     const long long t0 = clock64();
-    while (!mbar_try_wait_cluster(bar, parity)) {
-        if (*reinterpret_cast<volatile int*>(err) != 0) return false;
-        if (clock64() - t0 > kSpinLimit) {
-            atomicCAS(err, 0, code);
-            return false;
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait_cluster(bar, parity)) return true;
+        if (it % kPollsPerCheck == 0) {
+            if (*reinterpret_cast<volatile int*>(err) != 0) return false;
+            if (clock64() - t0 > kSpinLimit) {
+                atomicCAS(err, 0, code);
+                return false;
+            }
         }
     }
-    return true;
 }
 __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
@@ -919,20 +1132,25 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
                         break;
                     }
                     const int64_t a_off = (int64_t(rt) * sg.rt_chunks[sl.a_buf] + sl.a_chunk0) * kTileBytes;
-                    const int64_t b_row = int64_t(tk.n_pad) * 128;
-                    const int64_t b_off = sl.b_off + int64_t(crank) * half;
+                    const int64_t b_row = int64_t(tk.n_pad) * 128;  // one chunk tile
+                    const uint32_t qrt = half / 2u;                 // this CTA's rows of one K-half
+                    const int64_t b_off = sl.b_off + int64_t(crank) * qrt;
                     for (int c = 0; c < sl.nchunks; ++c) {
                         if (!mbar_wait(empty_bar(stage), phase ^ 1u, p.err, kErrProducer)) { ok = false; break; }
                         mbar_expect_tx(full_bar(stage), (C::kSplit ? 2u : 1u) * (a_bytes + half));
                         if (live)
                             bulk_g2s(sA(stage, 0), sg.rt_hi[sl.a_buf] + a_off + int64_t(c) * kTileBytes, kTileBytes,
                                      full_bar(stage));
-                        bulk_g2s(sB(stage, 0), sg.b_hi + b_off + int64_t(c) * b_row, half, full_bar(stage));
+                        for (int h = 0; h < 2; ++h)
+                            bulk_g2s(sB(stage, 0) + h * C::kBQuarter, sg.b_hi + b_off + int64_t(c) * b_row + h * (b_row / 2),
+                                     qrt, full_bar(stage));
                         if constexpr (C::kSplit) {
                             if (live)
                                 bulk_g2s(sA(stage, 1), sg.rt_lo[sl.a_buf] + a_off + int64_t(c) * kTileBytes,
                                          kTileBytes, full_bar(stage));
-                            bulk_g2s(sB(stage, 1), sg.b_lo + b_off + int64_t(c) * b_row, half, full_bar(stage));
+                            for (int h = 0; h < 2; ++h)
+                                bulk_g2s(sB(stage, 1) + h * C::kBQuarter,
+                                         sg.b_lo + b_off + int64_t(c) * b_row + h * (b_row / 2), qrt, full_bar(stage));
                         }
                         ++issued;
                         if (++stage == C::kStages) { stage = 0; phase ^= 1u; }
@@ -969,15 +1187,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
                 for (int q = 0; q < tk.nchunks; ++q) {
                     if (!mbar_wait_cluster(full_bar(stage), phase, p.err, kErrMma)) { ok = false; break; }
                     tc_fence_after();
-                    const uint64_t da = sw128_desc(sA(stage, 0)), db = sw128_desc(sB(stage, 0));
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint64_t off = uint64_t(kk * 2);
-                        mma_pair<MODE>(tacc, da + off, db + off, idesc, (q > 0 || kk > 0) ? 1u : 0u);
-                        if constexpr (C::kSplit) {
-                            const uint64_t dal = sw128_desc(sA(stage, 1)), dbl = sw128_desc(sB(stage, 1));
-                            mma_pair<MODE>(tacc, da + off, dbl + off, idesc, 1u);
-                            mma_pair<MODE>(tacc, dal + off, db + off, idesc, 1u);
+                    for (int h = 0; h < 2; ++h) {  // the chunk's two K-halves
+                        const uint64_t da = sw64_desc(sA(stage, 0) + h * (kTileBytes / 2));
+                        const uint64_t db = sw64_desc(sB(stage, 0) + h * C::kBQuarter);
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+                            const uint64_t off = uint64_t(kk * 2);
+                            mma_pair<MODE>(tacc, da + off, db + off, idesc, (q > 0 || h > 0 || kk > 0) ? 1u : 0u);
+                            if constexpr (C::kSplit) {
+                                const uint64_t dal = sw64_desc(sA(stage, 1) + h * (kTileBytes / 2));
+                                const uint64_t dbl = sw64_desc(sB(stage, 1) + h * C::kBQuarter);
+                                mma_pair<MODE>(tacc, da + off, dbl + off, idesc, 1u);
+                                mma_pair<MODE>(tacc, dal + off, db + off, idesc, 1u);
+                            }
                         }
                     }
                     mma_commit_pair(empty_bar(stage));
@@ -1059,7 +1282,7 @@ __global__ void __launch_bounds__(256) tc_gather_kernel(const float* __restrict_
         const int k = e / 128, jj = e % 128, j = rt * 128 + jj;
         float x = 0.f;
         if (k < valid && j < r) x = W[perm[pos + k] * ldw + j];
-        const uint32_t at = swz(uint32_t(jj), uint32_t(k * C::kEs));
+        const uint32_t at = swz(uint32_t(jj), uint32_t(k * C::kEs), 128);
         if constexpr (MODE == TC_TF32) {
             *reinterpret_cast<float*>(hi + at) = round_tf32(x);
         } else {
@@ -1095,7 +1318,8 @@ __global__ void tc_tile_kernel(const TileJob* __restrict__ jobs, const float* __
         else if (col >= jb.k_split + jb.k_gap) sc = col - jb.k_gap;
         float x = 0.f;
         if (n < jb.m && sc >= 0 && sc < jb.k) x = src[int64_t(n) * jb.src_ld + sc];
-        const int64_t at = jb.dst_off + int64_t(ch) * jb.n_pad * 128 + swz(uint32_t(n), uint32_t(kk * C::kEs));
+        const int64_t at =
+            jb.dst_off + int64_t(ch) * jb.n_pad * 128 + swz(uint32_t(n), uint32_t(kk * C::kEs), uint32_t(jb.n_pad));
         if constexpr (MODE == TC_TF32) {
             *reinterpret_cast<float*>(b_hi + at) = round_tf32(x);
         } else {
@@ -1155,6 +1379,7 @@ static void build_fused(const Structure& st, TcPrec& T, TcFused& F, unsigned sta
     std::vector<int64_t> work;
     std::vector<std::pair<int, int>> group;  // (stage, tree level) of every task
     std::vector<int64_t> node_of;
+    F.piece = T.piece;
     F.tasks.clear();
     F.slabs.clear();
     for (const TcLaunch& l : T.launches) {
@@ -1335,7 +1560,7 @@ static std::pair<TcTile*, int> fused_tiles(TcFused& F, int n_rtiles, int order) 
     if (it != F.tiles.end()) return it->second;
     std::vector<TcTile> t;
     for (int32_t k : order == GOFMM_ORDER_LOCAL ? F.order_local : F.order)
-        for (int rt = 0; rt < n_rtiles; ++rt) t.push_back(TcTile{0, k, rt, 0});
+        task_tiles(t, 0, k, F.tasks[size_t(k)], n_rtiles, F.piece);
     auto v = std::make_pair(dupload(t), int(t.size()));
     F.tiles[key] = v;
     return v;
@@ -1463,6 +1688,7 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
                                                       : node_at_skel.at(t.out_row));
             }
         }
+        tl.piece = T.piece;
         T.launches.push_back(std::move(tl));
     }
     T.b_bytes = bbytes;
@@ -1517,13 +1743,13 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
 template <int MODE>
 static void set_smem_attr() {
     CUDA_OK(cudaFuncSetAttribute(tc_gemm_kernel<MODE, 256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 Cfg<MODE, 256>::kSmem));
+                                 gemm_smem<MODE, 256, false>()));
     CUDA_OK(cudaFuncSetAttribute(tc_gemm_kernel<MODE, 128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 Cfg<MODE, 128>::kSmem));
+                                 gemm_smem<MODE, 128, false>()));
     CUDA_OK(cudaFuncSetAttribute(tc_gemm_kernel<MODE, 256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 Cfg<MODE, 256>::kSmem + kGenSmem));
+                                 gemm_smem<MODE, 256, true>()));
     CUDA_OK(cudaFuncSetAttribute(tc_gemm_kernel<MODE, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 Cfg<MODE, 128>::kSmem + kGenSmem));
+                                 gemm_smem<MODE, 128, true>()));
     CUDA_OK(cudaFuncSetAttribute(tc_gemm_pair_kernel<MODE, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  Cfg2<MODE, 256>::kSmem));
     CUDA_OK(cudaFuncSetAttribute(tc_gemm_pair_kernel<MODE, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1548,8 +1774,12 @@ std::pair<TcTile*, int> launch_tiles(TcLaunch& l, int n_rtiles, int order, bool 
         std::stable_sort(tasks.begin(), tasks.end(),
                          [&](int32_t a, int32_t b) { return l.task_node[size_t(a)] < l.task_node[size_t(b)]; });
     std::vector<TcTile> t;
-    for (int32_t k : tasks)
-        for (int rt = 0; rt < n_rtiles; ++rt) t.push_back(TcTile{0, k, rt, 0});
+    for (int32_t k : tasks) {
+        if (pair)  // a tile is one r-tile pair of the SM-pair kernel
+            for (int rt = 0; rt < n_rtiles; ++rt) t.push_back(TcTile{0, k, rt, 0});
+        else
+            task_tiles(t, 0, k, l.tasks[size_t(k)], n_rtiles, l.piece);
+    }
     auto v = std::make_pair(dupload(t), int(t.size()));
     l.tiles[key] = v;
     return v;
@@ -1690,7 +1920,7 @@ template <int MODE, int NMAX, bool GEN>
 static void launch_gemm(const TcParams& p, int num_sms, cudaStream_t s) {
     const int grid = std::min(p.ntiles, num_sms);
     tc_gemm_kernel<MODE, NMAX, GEN>
-        <<<unsigned(grid), GEN ? 448 : 192, Cfg<MODE, NMAX>::kSmem + (GEN ? kGenSmem : 0), s>>>(p);
+        <<<unsigned(grid), GEN ? 448 : 192, gemm_smem<MODE, NMAX, GEN>(), s>>>(p);
     CUDA_OK(cudaGetLastError());
 }
 
@@ -1701,7 +1931,7 @@ static void launch_gemm_coop(const TcParams& p, int num_sms, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(std::min(p.ntiles, num_sms)));
     cfg.blockDim = dim3(GEN ? 448 : 192);
-    cfg.dynamicSmemBytes = Cfg<MODE, NMAX>::kSmem + (GEN ? kGenSmem : 0);
+    cfg.dynamicSmemBytes = gemm_smem<MODE, NMAX, GEN>();
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;

@@ -43,8 +43,31 @@ struct TcTask {
 };
 
 struct TcTile {
-    int32_t seg, task, rt, pad;
+    int32_t seg, task, rt, pad;  // pad = 2: r-tiles rt and rt + 1 (else rt alone)
 };
+
+// Tiles of one task over n_rtiles 128-column tiles of r.  Two r-tiles per
+// tile feed two accumulators from each staged block stage: fewer staged
+// bytes per flop (a third fewer for a 256-row block, a quarter for 128
+// rows).  Accumulators of at most piece / 2 columns share one of the two
+// TMEM buffers, so tiles still alternate buffers and the epilogue of one
+// overlaps the MMAs of the next: such tasks take two r-tiles from
+// kTwoRtMinChunksNarrow chunks on.  Wider accumulators take both buffers,
+// which exposes the epilogue: only tasks of kTwoRtMinChunksWide chunks or
+// more that write a right-hand-side buffer (the leaves' scattered U rows
+// are slower to write) take two r-tiles then.
+constexpr int kTwoRtMinChunksNarrow = 4;
+constexpr int kTwoRtMinChunksWide = 16;
+inline void task_tiles(std::vector<TcTile>& out, int32_t seg, int32_t task, const TcTask& tk, int n_rtiles,
+                       int piece) {
+    const bool two = 2 * tk.n_pad <= piece ? tk.nchunks >= kTwoRtMinChunksNarrow
+                                           : tk.nchunks >= kTwoRtMinChunksWide && tk.out_kind != OUT_U;
+    for (int rt = 0; rt < n_rtiles;) {
+        const int w = two && rt + 1 < n_rtiles ? 2 : 1;
+        out.push_back(TcTile{seg, task, int32_t(rt), int32_t(w)});
+        rt += w;
+    }
+}
 
 // One (evaluation, launch) pair inside a tensor-core launch: the tasks and
 // slabs of that launch of one compressed matrix, its B tiles, the RT buffers
@@ -111,6 +134,7 @@ struct TcLaunch {
     TcTask* d_tasks = nullptr;
     TcSlab* d_slabs = nullptr;
     int stage = 0;
+    int piece = 256;  // task piece height of the plan
     std::map<int, std::pair<TcTile*, int>> tiles;  // r-tiles -> tile list of this launch alone
 };
 
@@ -120,6 +144,7 @@ struct TcFused {
     std::vector<TcSlab> slabs;
     std::vector<int32_t> order;        // tasks in a topological, critical-path-first order
     std::vector<int32_t> order_local;  // topological; groups by critical path, heap order inside
+    int piece = 256;                   // task piece height of the plan
     TcTask* d_tasks = nullptr;
     TcSlab* d_slabs = nullptr;
     int32_t* d_dep_off = nullptr;
