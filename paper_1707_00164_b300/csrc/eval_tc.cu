@@ -794,13 +794,16 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
                     write_tile_staged<MODE>(sg, tk, rt + w, row, taddr, stg, store_thread);
                 else
                     write_tile<MODE>(sg, tk, rt + w, row, taddr);
-            }
-            // accumulator buffers free for the MMAs of a later tile
-            tc_fence_before();
-            __syncwarp();
-            for (int b = 0; b < nb; ++b) {
-                if (lane == 0) mbar_arrive(tempty_bar(b0 + b));
-                fills ^= 1u << (b0 + b);
+                // an accumulator buffer is free for the MMAs of a later tile as
+                // soon as this tile's accumulators in it are read (a tile with
+                // two buffers frees the first before draining the second)
+                if (nb == 2 || w == nw - 1) {
+                    const int b = nb == 2 ? w : 0;
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(tempty_bar(b0 + b));
+                    fills ^= 1u << (b0 + b);
+                }
             }
             if (dyn) {
                 // publish this warp's 32 rows of the tile: consumers wait for
