@@ -258,6 +258,7 @@ def whole_job_value(n, r, world, ms_per_rank, reduce_max):
 
 # -------------------------------------------------------- batching/serving --
 SCHED_NAMES = ["fused", "staged", "pair", "hybrid"]  # GOFMM_SCHED_*
+ORDER_NAMES = ["critical", "local", "schedule"]       # GOFMM_ORDER_*
 
 
 def compress_many(G, works, device):
@@ -520,7 +521,7 @@ def native_arm(args):
     tune = None
     if prec_name in ("tf32", "bf16", "bf16x3") and args.config:
         pc, sc, oc = args.config.split("/")
-        G.set_tc_config(h, prec, int(pc), SCHED_NAMES.index(sc), ["critical", "local"].index(oc))
+        G.set_tc_config(h, prec, int(pc), SCHED_NAMES.index(sc), ORDER_NAMES.index(oc))
         tune = dict(G.get_tc_config(h, prec), forced=True, candidates=[])
     elif prec_name in ("tf32", "bf16", "bf16x3") and not args.no_tune:
         tune = G.autotune(h, r, prec, None, stream)
@@ -665,7 +666,7 @@ def native_arm(args):
                    and hashlib.sha256(open(src, "rb").read()).hexdigest() == tr.get("sha256"))
         if current and tune is not None:
             cfg = (f"{tune['piece']}/{SCHED_NAMES[tune['schedule']]}/"
-                   f"{['critical', 'local'][tune['order']]}")
+                   f"{ORDER_NAMES[tune['order']]}")
             traffic = float(tr[cfg]) if cfg in tr else None
     if prec_name in ("fp32", "fp64"):
         kdesc = "gemm_simt_kernel, S2S launch (every far pair of every level)"

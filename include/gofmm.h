@@ -81,6 +81,10 @@ extern "C" {
 #define GOFMM_ORDER_LOCAL 1    /* fused: topological, (stage, level) groups by
                                   critical path, heap order inside; staged:
                                   heap order                                 */
+#define GOFMM_ORDER_SCHEDULE 2 /* fused: the order of a list schedule
+                                  simulated on the host (the earliest task to
+                                  be ready first, critical path among those
+                                  ready); staged: heap order                 */
 
 /*
  * Entry callback: fill out[i*nJ + j] = K(I[i], J[j]) for 0 <= i < nI,

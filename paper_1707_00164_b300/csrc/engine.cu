@@ -449,7 +449,7 @@ Batch* batch_create(Handle* const* hs, const int64_t* r, int count, int precisio
                 off += size_t(F.ncounters) * size_t(it.n_rtiles);
                 bf.piece = std::max(bf.piece, it.T->piece);
                 bf.gen = bf.gen || it.T->gen;
-                orders.push_back(it.H->tc_order[B->mode] == GOFMM_ORDER_LOCAL ? &F.order_local : &F.order);
+                orders.push_back(&fused_order(F, it.H->tc_order[B->mode]));
             }
             bf.counter_ints = off + 1;  // + the tile counter
             bf.d_counters = dalloc<int>(bf.counter_ints);

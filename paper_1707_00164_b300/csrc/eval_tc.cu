@@ -36,6 +36,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <queue>
 #include <set>
 #include <tuple>
 
@@ -1546,6 +1547,47 @@ static void build_fused(const Structure& st, TcPrec& T, TcFused& F, unsigned sta
                 if (--indeg[size_t(u)] == 0) ready.insert(key(u));
         }
         if (F.order_local.size() != nt) fail(GOFMM_ERR_ARG, "dependency cycle in the fused plan");
+
+        // Schedule order: a list schedule simulated on the host.  A task runs
+        // on one of W workers (the launch's CTAs over the two tiles a task
+        // has at r = 512) for its work plus a per-tile overhead, and is ready
+        // when every producer it waits for has finished.  The worker that
+        // frees first takes, among the tasks ready by then, the first in the
+        // locality order's priority (group with the longest critical path,
+        // then heap order); if none is ready, the one ready first.  Taken only
+        // after all its producers, so the order is topological; CTAs that
+        // claim tiles in it find their operands ready more often than in a
+        // priority order alone, and neighbouring tiles still share operands.
+        const int workers = std::max(1, T.num_sms / 2);
+        std::vector<int64_t> ready_at(nt, 0);
+        std::vector<int32_t> left(indeg);
+        using Ev = std::pair<int64_t, int32_t>;
+        std::priority_queue<Ev, std::vector<Ev>, std::greater<Ev>> pending;  // (ready time, task)
+        std::set<std::tuple<int64_t, int, int, int64_t, int32_t>> avail;      // locality priority
+        std::priority_queue<int64_t, std::vector<int64_t>, std::greater<int64_t>> freeat;
+        for (int w = 0; w < workers; ++w) freeat.push(0);
+        for (size_t t = 0; t < nt; ++t)
+            if (left[t] == 0) pending.push({0, int32_t(t)});
+        F.order_sched.clear();
+        while (F.order_sched.size() < nt) {
+            int64_t now = freeat.top();
+            freeat.pop();
+            if (avail.empty() && !pending.empty() && pending.top().first > now) now = pending.top().first;
+            while (!pending.empty() && pending.top().first <= now) {
+                avail.insert(key(pending.top().second));
+                pending.pop();
+            }
+            if (avail.empty()) fail(GOFMM_ERR_ARG, "dependency cycle in the fused plan");
+            const int32_t t = std::get<4>(*avail.begin());
+            avail.erase(avail.begin());
+            const int64_t done = now + work[size_t(t)] + 1024;
+            freeat.push(done);
+            F.order_sched.push_back(t);
+            for (int32_t u : succ[size_t(t)]) {
+                ready_at[size_t(u)] = std::max(ready_at[size_t(u)], done);
+                if (--left[size_t(u)] == 0) pending.push({ready_at[size_t(u)], u});
+            }
+        }
     }
     F.d_tasks = dupload(F.tasks);
     F.d_slabs = dupload(F.slabs);
@@ -1558,11 +1600,11 @@ static void build_fused(const Structure& st, TcPrec& T, TcFused& F, unsigned sta
 // Tile list of the fused launch: tasks in the given order (GOFMM_ORDER_*),
 // the r-tiles of a task adjacent.
 static std::pair<TcTile*, int> fused_tiles(TcFused& F, int n_rtiles, int order) {
-    const int key = n_rtiles * 2 + (order == GOFMM_ORDER_LOCAL ? 1 : 0);
+    const int key = n_rtiles * 4 + order;
     auto it = F.tiles.find(key);
     if (it != F.tiles.end()) return it->second;
     std::vector<TcTile> t;
-    for (int32_t k : order == GOFMM_ORDER_LOCAL ? F.order_local : F.order)
+    for (int32_t k : fused_order(F, order))
         task_tiles(t, 0, k, F.tasks[size_t(k)], n_rtiles, F.piece);
     auto v = std::make_pair(dupload(t), int(t.size()));
     F.tiles[key] = v;
@@ -1768,12 +1810,12 @@ static void set_smem_attr() {
 // SM-pair kernel.
 std::pair<TcTile*, int> launch_tiles(TcLaunch& l, int n_rtiles, int order, bool pair) {
     if (pair) n_rtiles = (n_rtiles + 1) / 2;
-    const int key = n_rtiles * 4 + (order == GOFMM_ORDER_LOCAL ? 1 : 0) + (pair ? 2 : 0);
+    const int key = n_rtiles * 4 + (order != GOFMM_ORDER_CRITICAL ? 1 : 0) + (pair ? 2 : 0);
     auto it = l.tiles.find(key);
     if (it != l.tiles.end()) return it->second;
     std::vector<int32_t> tasks(l.tasks.size());
     for (size_t k = 0; k < tasks.size(); ++k) tasks[k] = int32_t(k);
-    if (order == GOFMM_ORDER_LOCAL)
+    if (order != GOFMM_ORDER_CRITICAL)  // heap order
         std::stable_sort(tasks.begin(), tasks.end(),
                          [&](int32_t a, int32_t b) { return l.task_node[size_t(a)] < l.task_node[size_t(b)]; });
     std::vector<TcTile> t;
@@ -1801,6 +1843,9 @@ TcPrec& tc_plan(Handle& H, DeviceState& D, int precision) {
         t->es = mode == TC_TF32 ? 4 : 2;
         t->split = mode == TC_BF16X3;
         t->piece = H.tc_piece[mode];
+        int dev = 0;
+        CUDA_OK(cudaGetDevice(&dev));
+        CUDA_OK(cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, dev));  // the plan's orders use it
         std::vector<TileJob> jobs;
         build_tc_plan(H.st, D, *t, jobs);
         if (t->gen) {
@@ -1837,9 +1882,6 @@ TcPrec& tc_plan(Handle& H, DeviceState& D, int precision) {
         CUDA_OK(cudaMemset(t->d_err, 0, sizeof(int)));
         CUDA_OK(cudaMallocHost(&t->h_err, sizeof(int)));
         *t->h_err = 0;
-        int dev = 0;
-        CUDA_OK(cudaGetDevice(&dev));
-        CUDA_OK(cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, dev));
         set_smem_attr<TC_TF32>();
         set_smem_attr<TC_BF16>();
         set_smem_attr<TC_BF16X3>();

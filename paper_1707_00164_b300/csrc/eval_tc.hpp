@@ -144,6 +144,7 @@ struct TcFused {
     std::vector<TcSlab> slabs;
     std::vector<int32_t> order;        // tasks in a topological, critical-path-first order
     std::vector<int32_t> order_local;  // topological; groups by critical path, heap order inside
+    std::vector<int32_t> order_sched;  // a simulated list schedule's order (topological)
     int piece = 256;                   // task piece height of the plan
     TcTask* d_tasks = nullptr;
     TcSlab* d_slabs = nullptr;
@@ -198,6 +199,10 @@ TcSeg make_seg(const TcPrec& T, const TcLaunch& l, uint8_t* const* rt_hi, uint8_
 void launch_gemm_mode(int mode, int piece, const TcParams& p, int num_sms, cudaStream_t s, bool gen = false);
 // cooperative launch (every CTA resident): the dependency-driven mode
 void launch_gemm_coop_mode(int mode, int piece, const TcParams& p, int num_sms, cudaStream_t s, bool gen);
+// the fused plan's task order for a GOFMM_ORDER_* value
+inline const std::vector<int32_t>& fused_order(const TcFused& F, int order) {
+    return order == GOFMM_ORDER_LOCAL ? F.order_local : order == GOFMM_ORDER_SCHEDULE ? F.order_sched : F.order;
+}
 // device tile list of one launch alone for n_rtiles r-tiles (cached in the launch)
 std::pair<TcTile*, int> launch_tiles(TcLaunch& l, int n_rtiles, int order, bool pair = false);
 void tc_drop_plan(DeviceState& D, int precision);  // frees one mode's plan, stores and buffers
