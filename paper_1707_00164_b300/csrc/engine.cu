@@ -56,6 +56,7 @@ struct Engine {
     int64_t next_id = 1;
     int* d_err = nullptr;
     int* h_err = nullptr;
+    int* d_claims = nullptr;  // tile counters of one step's grouped launches (kClaimSlots)
     // statistics
     int64_t steps = 0, launches = 0, max_active = 0, completed = 0;
 };
@@ -148,6 +149,7 @@ Engine* engine_create(int device, int precision, int64_t pool_bytes) {
     E->pool = dalloc<uint8_t>(E->pool_bytes);
     E->free_blocks[0] = E->pool_bytes;
     E->d_err = dalloc<int>(1);
+    E->d_claims = dalloc<int>(kClaimSlots);
     CUDA_OK(cudaMemset(E->d_err, 0, sizeof(int)));
     CUDA_OK(cudaMallocHost(&E->h_err, sizeof(int)));
     *E->h_err = 0;
@@ -216,6 +218,8 @@ int64_t engine_step(Engine& E, cudaStream_t s) {
     std::vector<EngineRequest*> gemm;
     for (EngineRequest* q : E.active)
         if (q->next >= 1 && q->next <= int(q->T->launches.size())) gemm.push_back(q);
+    // the grouped launches claim their tiles from counters (whichever CTA is free)
+    if (!gemm.empty()) CUDA_OK(cudaMemsetAsync(E.d_claims, 0, kClaimSlots * sizeof(int), s));
     for (size_t b0 = 0; b0 < gemm.size(); b0 += kMaxSegs) {
         const size_t nb = std::min<size_t>(kMaxSegs, gemm.size() - b0);
         // every segment brings the device tile list its plan keeps for its
@@ -239,6 +243,8 @@ int64_t engine_step(Engine& E, cudaStream_t s) {
             gen = gen || q->T->gen;
         }
         p.ntiles = total;
+        const size_t slot = b0 / kMaxSegs;
+        p.tile_next = slot < size_t(kClaimSlots) ? E.d_claims + slot : nullptr;
         launch_gemm_mode(E.mode, piece, p, E.num_sms, s, gen);
         ++E.launches;
     }
@@ -328,6 +334,7 @@ void engine_destroy(Engine* E) {
     }
     dfree(E->pool);
     dfree(E->d_err);
+    dfree(E->d_claims);
     if (E->h_err) cudaFreeHost(E->h_err);
     delete E;
     if (old >= 0) cudaSetDevice(old);
@@ -383,6 +390,8 @@ struct Batch {
     std::vector<BatchStep> steps;
     bool fused = false;                 // every handle configured for the fused schedule
     std::vector<BatchFused> fused_launches;
+    int* d_claims = nullptr;            // tile counters of the per-step launches (one each)
+    int nclaims = 0;
     uint8_t* ws = nullptr;
     int* d_err = nullptr;
     int* h_err = nullptr;
@@ -516,6 +525,8 @@ Batch* batch_create(Handle* const* hs, const int64_t* r, int count, int precisio
         B->steps.push_back(std::move(st));
     }
     B->d_err = dalloc<int>(1);
+    for (const BatchStep& st : B->steps) B->nclaims += int(st.launches.size());
+    B->d_claims = dalloc<int>(size_t(std::max(1, B->nclaims)));
     CUDA_OK(cudaMemset(B->d_err, 0, sizeof(int)));
     CUDA_OK(cudaMallocHost(&B->h_err, sizeof(int)));
     *B->h_err = 0;
@@ -555,6 +566,9 @@ static void batch_launch(Batch& B, const float* const* W, const int64_t* ldw, fl
         CUDA_OK(cudaMemcpyAsync(B.h_err, B.d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
         return;
     }
+    // the per-step launches claim their tiles from counters
+    if (B.nclaims > 0) CUDA_OK(cudaMemsetAsync(B.d_claims, 0, size_t(B.nclaims) * sizeof(int), s));
+    int claim = 0;
     for (const BatchStep& st : B.steps) {
         for (int i : st.gathers) {
             const BatchItem& it = B.items[i];
@@ -572,6 +586,7 @@ static void batch_launch(Batch& B, const float* const* W, const int64_t* ldw, fl
                 p.segs[k] = make_seg(*it.T, it.T->launches[bl.segs[k].second], it.rt_hi, it.rt_lo, U[i], ldu[i],
                                      it.H->dev->d_idx, it.r);
             }
+            p.tile_next = B.d_claims + claim++;
             launch_gemm_mode(B.mode, bl.piece, p, B.num_sms, s, bl.gen);
         }
     }
@@ -635,6 +650,7 @@ void batch_destroy(Batch* B) {
     }
     dfree(B->ws);
     dfree(B->d_err);
+    dfree(B->d_claims);
     if (B->h_err) cudaFreeHost(B->h_err);
     if (B->capture_stream) cudaStreamDestroy(B->capture_stream);
     delete B;

@@ -20,15 +20,20 @@
 // reads it from shared memory, so a single linear cp.async.bulk stages it
 // (no tensor maps).
 //
-// Kernel: persistent, one CTA per SM looping over (task, 128-column tile of
-// r) tiles, 6 warps.  Warp 0 streams the K-halves of the A/B chunk tiles into
-// a ring of shared-memory stages (mbarrier complete_tx); warp 1 allocates
-// TMEM (two 256-column accumulators) and one thread issues the MMAs (2 per
-// stage, 6 for BF16x3) and commits each stage back to the producer; warps 2-5
-// read the other accumulator (tcgen05.ld) meanwhile and write the outputs:
-// the next stage's RT operand (rounded to TF32 / BF16 / BF16 hi+lo) or, for the
-// leaves, U scattered to the original order in FP32.  Every wait is bounded;
-// on timeout the kernel records an error code, drains what it issued and
+// Kernel: persistent, one CTA per SM looping over tiles (a task and one or
+// two 128-column tiles of r), 6 warps.  Warp 0 streams stages into a ring
+// in shared memory (mbarrier complete_tx): one K-half of a chunk (split
+// BF16x3) or a whole chunk (TF32, BF16) of the block and of the tile's one
+// or two right-hand-side tiles, 64 KB.  Warp 1 allocates TMEM (two
+// 256-column accumulator buffers) and one thread issues the MMAs, the block
+// against each right-hand-side tile into its own accumulator (a two-r-tile
+// tile stages the block once for both), and commits each stage back to the
+// producer.  Warps 2-5 read finished accumulators (tcgen05.ld) while the
+// MMAs of the next tile run and write the outputs: the next stage's RT
+// operand (rounded to TF32 / BF16 / BF16 hi+lo; a fresh segment through a
+// shared-memory staging tile and bulk stores) or, for the leaves, U
+// scattered to the original order in FP32.  Every wait is bounded; on
+// timeout the kernel records an error code, drains what it issued and
 // returns.
 #include <cuda_bf16.h>
 
@@ -500,7 +505,9 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
     const uint32_t drain_bar = smem_u32(&bars[2 * C::kStages + 4]);
     auto idfull_bar = [&](int a) { return smem_u32(&bars[2 * C::kStages + 5 + a]); };
     auto idempty_bar = [&](int a) { return smem_u32(&bars[2 * C::kStages + 7 + a]); };
-    const bool dyn = p.tile_next != nullptr;  // dynamic tile order (dependency mode)
+    // dynamic tile claiming from a counter (with dependency waits where the
+    // segments carry dependency arrays), else a static round-robin split
+    const bool dyn = p.tile_next != nullptr;
     // stage s: A0_hi | A1_hi | B_hi | (A0_lo | A1_lo | B_lo): kSub K-halves of
     // the right-hand-side tiles of r-tiles rt and rt + 1 and of the block tile
     auto sA = [&](int s, int lo, int w) { return s_base + s * C::kStageBytes + lo * C::kPart + w * C::kAUnit; };
@@ -566,7 +573,7 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
                 const int rt = tt.rt;
                 const int nw = tile_width(tt);
                 const uint32_t b_half = uint32_t(tk.n_pad) * 64u;  // one K-half of a block chunk tile
-                if (dyn) {
+                if (dyn && sg.dep_off) {
                     // results of other tiles of this launch the task needs
                     // before it starts (the operands are waited for slab by slab)
                     for (int d = sg.dep_off[tt.task]; d < sg.dep_off[tt.task + 1] && ok; ++d)
@@ -577,7 +584,7 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
                 }
                 for (int si = tk.slab0; si < tk.slab1 && ok; ++si) {
                     const TcSlab sl = sg.slabs[si];
-                    if (dyn) {
+                    if (dyn && sg.dep_off) {
                         // this slab's right-hand sides, written earlier in the
                         // launch by other tiles: wait (bounded), then make the
                         // generic writes visible to the bulk copies
@@ -806,7 +813,7 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
                     fills ^= 1u << (b0 + b);
                 }
             }
-            if (dyn) {
+            if (dyn && sg.sig) {
                 // publish this warp's 32 rows of the tile: consumers wait for
                 // four arrivals (one per epilogue warp) per task piece
                 const int s0 = sg.sig[2 * tt.task], s1 = sg.sig[2 * tt.task + 1];
@@ -1376,10 +1383,8 @@ static void build_fused(const Structure& st, TcPrec& T, TcFused& F, unsigned sta
             } else if (l.stage == 3) internal[size_t(cUF(h))] = 1;
         }
     }
-    std::vector<int> cdepth(size_t(3 * nn), 0);
     std::vector<int32_t> dep_off{0}, deps, sig;
     std::vector<int32_t> all_off{0}, all_deps;  // task and slab dependencies together (ordering only)
-    std::vector<int> depth;
     std::vector<int64_t> work;
     std::vector<std::pair<int, int>> group;  // (stage, tree level) of every task
     std::vector<int64_t> node_of;
@@ -1442,14 +1447,9 @@ static void build_fused(const Structure& st, TcPrec& T, TcFused& F, unsigned sta
                     d.end());
             std::sort(d.begin(), d.end());
             d.erase(std::unique(d.begin(), d.end()), d.end());
-            // every dependency of the task: the slabs' operand dependencies
-            // are waited for slab by slab in the kernel; the rest (an S2N push
-            // waiting for its node's S2S result) before the first copy
-            std::vector<std::pair<int32_t, int32_t>> all = d;
-            for (const auto& x : slab_deps)
-                if (!std::binary_search(d.begin(), d.end(), x)) all.push_back(x);
-            int dp = 0;
-            for (auto& x : all) dp = std::max(dp, cdepth[x.first]);
+            // the slabs' operand dependencies are waited for slab by slab in
+            // the kernel; the rest (an S2N push waiting for its node's S2S
+            // result) before the first copy
             for (auto& x : d) {
                 if (std::find(slab_deps.begin(), slab_deps.end(), x) != slab_deps.end()) continue;
                 deps.push_back(x.first);
@@ -1468,9 +1468,6 @@ static void build_fused(const Structure& st, TcPrec& T, TcFused& F, unsigned sta
             all_off.push_back(int32_t(all_deps.size() / 2));
             sig.push_back(s0);
             sig.push_back(s1);
-            depth.push_back(dp + 1);
-            if (s0 >= 0) cdepth[s0] = std::max(cdepth[s0], dp + 1);
-            if (s1 >= 0) cdepth[s1] = std::max(cdepth[s1], dp + 1);
             work.push_back(int64_t(t.nchunks) * t.n_pad);
             {
                 int lev = 0;
@@ -1502,7 +1499,6 @@ static void build_fused(const Structure& st, TcPrec& T, TcFused& F, unsigned sta
     F.order.resize(nt);
     for (size_t i = 0; i < nt; ++i) F.order[i] = int32_t(i);
     std::stable_sort(F.order.begin(), F.order.end(), [&](int32_t a, int32_t b) { return tail[a] > tail[b]; });
-    (void)depth;
 
     // Locality order: a topological order (Kahn) that takes, among the ready
     // tasks, those of the (stage, tree level) group with the longest critical
@@ -1880,6 +1876,7 @@ TcPrec& tc_plan(Handle& H, DeviceState& D, int precision) {
         }
         t->d_err = dalloc<int>(1);
         CUDA_OK(cudaMemset(t->d_err, 0, sizeof(int)));
+        t->d_claims = dalloc<int>(kClaimSlots);
         CUDA_OK(cudaMallocHost(&t->h_err, sizeof(int)));
         *t->h_err = 0;
         set_smem_attr<TC_TF32>();
@@ -2141,15 +2138,19 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
         D.last_fused = false;
         run_fused(T.fused_up);
         if (timing) CUDA_OK(cudaEventRecord(D.ev[2], s));
+        CUDA_OK(cudaMemsetAsync(T.d_claims, 0, kClaimSlots * sizeof(int), s));
+        int claim = 0;
         for (TcLaunch& l : T.launches) {
             if (l.stage != 2 || l.tasks.empty()) continue;
             const auto tl = launch_tiles(l, n_rtiles, H.tc_order[T.mode]);
             p.tiles = tl.first;
             p.ntiles = tl.second;
             p.segs[0] = make_seg(T, l, T.rt_hi, T.rt_lo, U, ldu, D.d_idx, r);
+            p.tile_next = claim < kClaimSlots ? T.d_claims + claim++ : nullptr;  // dynamic claiming
             launch_gemm_mode(T.mode, T.piece, p, T.num_sms, s, T.gen);
             ++launches;
         }
+        p.tile_next = nullptr;
         if (timing) CUDA_OK(cudaEventRecord(D.ev[3], s));
         run_fused(T.fused_down);
         if (timing)
@@ -2159,6 +2160,8 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
         D.last_fused = false;
         const bool pair = sched == GOFMM_SCHED_PAIR;
         int stage_done = 1;
+        if (!pair) CUDA_OK(cudaMemsetAsync(T.d_claims, 0, kClaimSlots * sizeof(int), s));
+        int claim = 0;
         for (TcLaunch& l : T.launches) {
             while (stage_done < l.stage) CUDA_OK(cudaEventRecord(D.ev[++stage_done], s));
             if (l.tasks.empty()) continue;
@@ -2166,10 +2169,14 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
             p.tiles = tl.first;
             p.ntiles = tl.second;
             p.segs[0] = make_seg(T, l, T.rt_hi, T.rt_lo, U, ldu, D.d_idx, r);
+            // the SM-pair kernel splits its tiles statically; the single-SM
+            // kernel claims them from a counter (no stragglers at the end)
+            p.tile_next = !pair && claim < kClaimSlots ? T.d_claims + claim++ : nullptr;
             if (pair) launch_gemm_pair_mode(T.mode, T.piece, p, T.num_sms, s);
             else launch_gemm_mode(T.mode, T.piece, p, T.num_sms, s, T.gen);
             ++launches;
         }
+        p.tile_next = nullptr;
         while (stage_done < 5) CUDA_OK(cudaEventRecord(D.ev[++stage_done], s));
     } else {
         // every grouped GEMM in one dependency-driven launch
@@ -2241,7 +2248,7 @@ static void free_prec(TcPrec*& T) {
             dfree(l.d_slabs);
             for (auto& kv : l.tiles) dfree(kv.second.first);
         }
-        dfree(T->d_chunk_pos); dfree(T->d_chunk_valid); dfree(T->b_hi); dfree(T->b_lo); dfree(T->d_err);
+        dfree(T->d_chunk_pos); dfree(T->d_chunk_valid); dfree(T->b_hi); dfree(T->b_lo); dfree(T->d_err); dfree(T->d_claims);
         dfree(T->gen_pts);
         for (TcFused* F : {&T->fused, &T->fused_up, &T->fused_down}) {
             dfree(F->d_tasks); dfree(F->d_slabs); dfree(F->d_dep_off); dfree(F->d_deps); dfree(F->d_sig);

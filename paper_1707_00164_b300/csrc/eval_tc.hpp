@@ -94,8 +94,9 @@ struct TcSeg {
     const float* pts;
     int32_t dim, dpad, gen_kind, pad2;
     float gen_inv, gen_shift;
-    // dependency-driven launch (TcParams::tile_next set): tile (task, rt)
-    // waits until counters[c * dep_nrt + rt] >= e for every (c, e) in
+    // dependency-driven launch (TcParams::tile_next set and dep_off not
+    // null; a launch without dependencies leaves all five null): tile
+    // (task, rt) waits until counters[c * dep_nrt + rt] >= e for every (c, e) in
     // deps[dep_off[task] .. dep_off[task+1]) and for its slabs' operand
     // counters, and adds one to counters[sig[2 task + i] * dep_nrt + rt]
     // (i = 0, 1; -1 = none) per epilogue warp when done
@@ -107,6 +108,7 @@ struct TcSeg {
 };
 constexpr int kGenMaxDpad = 16;  // generated blocks: at most 16 coordinates per point
 constexpr int kMaxSegs = 64;  // segments per launch (kernel parameters, by value)
+constexpr int kClaimSlots = 64;  // per-stage launches of one evaluation that claim tiles dynamically
 
 
 struct TcParams {
@@ -114,9 +116,10 @@ struct TcParams {
     int ntiles;
     int nsegs;
     int* err;
-    // dependency-driven mode (one launch for whole evaluations, each segment
-    // with its own dependency arrays and counters): tiles are taken in list
-    // order from this counter (dynamic); nullptr: static tiles, no waits
+    // tiles are taken in list order from this zeroed counter by whichever
+    // CTA is free (dynamic; with dependency waits in the segments that carry
+    // dependency arrays, which needs every CTA resident: a cooperative
+    // launch); nullptr: static round-robin split, no waits
     int* tile_next;
     TcSeg segs[kMaxSegs];
 };
@@ -182,6 +185,7 @@ struct TcPrec {
     int* d_err = nullptr;
     int* h_err = nullptr;  // pinned
     int num_sms = 148;     // persistent grid size
+    int* d_claims = nullptr;  // tile counters of the per-stage launches of one evaluation (kClaimSlots)
     TcFused fused;       // every stage in one launch
     TcFused fused_up;    // N2S levels in one launch (hybrid schedule)
     TcFused fused_down;  // S2N levels and leaves in one launch (hybrid schedule)
