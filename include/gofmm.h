@@ -322,10 +322,13 @@ int gofmm_engine_free(gofmm_engine* e);
 /*
  * ---- Static batch -----------------------------------------------------------
  * A fixed list of evaluations (handle i with r[i] right-hand sides, handles
- * may repeat) planned once: workspaces allocated, the merged step sequence
- * (one persistent grouped launch per step for all items, plus one gather per
- * item) built and uploaded.  gofmm_batch_evaluate runs it; calls with the
- * same W/U pointers replay a CUDA graph of the whole sequence.
+ * may repeat) planned once: workspaces allocated, the launch sequence built
+ * and uploaded.  If every handle is configured for the FUSED schedule the
+ * batch runs as one dependency-driven launch per 64 items (each item's
+ * tiles in its own order, the items interleaved task by task); otherwise as
+ * one persistent grouped launch per stage step for all items.  Either way
+ * one gather per item comes first.  gofmm_batch_evaluate runs it; calls
+ * with the same W/U pointers replay a CUDA graph of the whole sequence.
  */
 typedef struct gofmm_batch gofmm_batch;
 
@@ -408,10 +411,11 @@ int64_t gofmm_view(const gofmm_handle* h, int what, void* out);
  * configuration computes bitwise the same U: a task's summation order does
  * not depend on how tasks are cut or ordered.
  *   piece    : 128 or 256, the tallest task piece (the MMA N ceiling); taller
- *              blocks are cut into pieces.  128 halves the block tile held
- *              in shared memory, which deepens the copy pipeline (3 stages
- *              instead of 2 in BF16X3, 6 instead of 4 otherwise) at the cost
- *              of reading each right-hand-side tile once per piece.
+ *              blocks are cut into pieces.  128 halves the block part of a
+ *              shared-memory stage (4 stages of 48 KB instead of 3 of 64 KB)
+ *              at the cost of reading each right-hand-side tile once per
+ *              piece; blocks of at most piece / 2 rows feed two r-tiles from
+ *              one TMEM buffer.
  *   schedule : GOFMM_SCHED_*.
  *   order    : GOFMM_ORDER_* (tile order inside the launches).
  * A new `piece` rebuilds the precision's plan if one exists (synchronises
@@ -434,11 +438,12 @@ typedef struct {
 /*
  * Autotuner.  Times gofmm_evaluate of h with r right-hand sides in a
  * tensor-core precision under each candidate configuration (piece 256 and
- * 128, each with the FUSED, STAGED, PAIR and HYBRID schedules in CRITICAL and
- * in LOCAL order: 16 candidates, 12 without cached blocks (no PAIR); 3
- * warm-up and 7 timed calls each, CUDA events on
- * `stream`, on scratch W = 0 and U the library allocates), applies the
- * fastest with gofmm_set_tc_config and reports all of them in *out.
+ * 128, each with the FUSED and HYBRID schedules in CRITICAL, LOCAL and
+ * SCHEDULE order and the STAGED and PAIR schedules in LOCAL order: 16
+ * candidates, 14 without cached blocks (no PAIR); 3 warm-up and 7 timed
+ * calls each, CUDA events on `stream`, on a scratch W of pseudo-random
+ * values and a scratch U the library allocates), applies the fastest with
+ * gofmm_set_tc_config and reports all of them in *out.
  * cache_path (may be NULL): a JSON file of earlier choices.  If it holds
  * an entry for the same key (the structure's signature, ceil(r/128),
  * precision, GPU name and SM count), that choice is applied without
@@ -453,8 +458,10 @@ int gofmm_autotune(gofmm_handle* h, int64_t r, int precision, const char* cache_
 
 /*
  * The same for a static batch (gofmm_batch_create): the candidates are
- * piece 256 and 128 applied to every handle; each is timed as a whole
- * batch call.  Create the batch after tuning.
+ * piece 256 and 128, each with the FUSED schedule (the batch runs as one
+ * dependency-driven launch per 64 items) and the STAGED one (one grouped
+ * launch per stage step), in LOCAL order, applied to every handle; each is
+ * timed as a whole batch call.  Create the batch after tuning.
  */
 int gofmm_autotune_batch(gofmm_handle* const* hs, const int64_t* r, int count, int precision,
                          const char* cache_path, void* stream, gofmm_tune_t* out);
