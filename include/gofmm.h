@@ -215,6 +215,24 @@ int gofmm_evaluate_host(gofmm_handle* h, const void* W, int64_t ldw, void* U, in
                         int64_t r, int dtype, int precision, void* stream);
 
 /*
+ * As gofmm_evaluate_host, but returns once the copies and the evaluation are
+ * enqueued: U is final, and W may be changed, only after
+ * gofmm_synchronize(h, stream) returns.  W must hold its values when the
+ * call is made (its copy to the device does not wait for earlier work on
+ * `stream`; the evaluation does).  Consecutive asynchronous calls on a
+ * handle alternate two device staging slots (each call waits on the device
+ * until the slot's previous call has copied its U out), so the copies of one
+ * call overlap the evaluation of the next; with pinned host buffers a stream
+ * of calls runs at about the larger of the copy time and the evaluation
+ * time per call.  Calls whose U regions overlap must not be in flight
+ * together.  The result is bitwise that of gofmm_evaluate.  Errors: as
+ * gofmm_evaluate_host; a bounded wait given up is reported by
+ * gofmm_synchronize.
+ */
+int gofmm_evaluate_host_async(gofmm_handle* h, const void* W, int64_t ldw, void* U, int64_t ldu,
+                              int64_t r, int dtype, int precision, void* stream);
+
+/*
  * As gofmm_evaluate (FP64 or FP32 precision only), but allocating nothing:
  * the evaluation's scratch lives in a fixed 32 MiB device array that the
  * library holds on every device it is loaded on until the process exits.

@@ -276,7 +276,7 @@ int gofmm_evaluate(gofmm_handle* h, const void* W, int64_t ldw, void* U, int64_t
                    int dtype, int precision, void* stream) {
     return guarded([&] {
         if (!h) gofmm::fail(GOFMM_ERR_ARG, "handle is NULL");
-        gofmm::device_evaluate(h->h, W, ldw, U, ldu, r, dtype, precision, stream, false);
+        gofmm::device_evaluate(h->h, W, ldw, U, ldu, r, dtype, precision, stream, 0);
     });
 }
 
@@ -284,7 +284,15 @@ int gofmm_evaluate_host(gofmm_handle* h, const void* W, int64_t ldw, void* U, in
                         int dtype, int precision, void* stream) {
     return guarded([&] {
         if (!h) gofmm::fail(GOFMM_ERR_ARG, "handle is NULL");
-        gofmm::device_evaluate(h->h, W, ldw, U, ldu, r, dtype, precision, stream, true);
+        gofmm::device_evaluate(h->h, W, ldw, U, ldu, r, dtype, precision, stream, 1);
+    });
+}
+
+int gofmm_evaluate_host_async(gofmm_handle* h, const void* W, int64_t ldw, void* U, int64_t ldu, int64_t r,
+                              int dtype, int precision, void* stream) {
+    return guarded([&] {
+        if (!h) gofmm::fail(GOFMM_ERR_ARG, "handle is NULL");
+        gofmm::device_evaluate(h->h, W, ldw, U, ldu, r, dtype, precision, stream, 2);
     });
 }
 

@@ -476,8 +476,8 @@ static void ensure_workspace(Handle& H, int fi, int64_t r) {
     DeviceState& D = *H.dev;
     Family& F = D.fam[fi];
     if (F.ws_r >= r) return;
-    dfree(F.WT); dfree(F.WTIL); dfree(F.UTIL); dfree(F.dW); dfree(F.dU);
-    F.WT = F.WTIL = F.UTIL = F.dW = F.dU = nullptr;
+    dfree(F.WT); dfree(F.WTIL); dfree(F.UTIL); dfree(F.dW); dfree(F.dU); dfree(F.dW2); dfree(F.dU2);
+    F.WT = F.WTIL = F.UTIL = F.dW = F.dU = F.dW2 = F.dU2 = nullptr;
     F.ws_r = 0;
     F.WT = dalloc<T>(size_t(D.n * r));
     F.WTIL = dalloc<T>(size_t(std::max<int64_t>(D.S_tot, 1) * r));
@@ -486,16 +486,27 @@ static void ensure_workspace(Handle& H, int fi, int64_t r) {
 }
 
 template <typename T>
-static void ensure_staging(Handle& H, int fi, int64_t r) {
+static void ensure_staging(Handle& H, int fi, int64_t r, bool two) {
     Family& F = H.dev->fam[fi];
-    if (F.dW && F.stage_r >= r) return;
+    if (F.dW && F.stage_r >= r && (!two || F.dW2)) return;
+    // buffers still read or written by earlier asynchronous calls
+    CUDA_OK(cudaDeviceSynchronize());
+    const int64_t rr = std::max(r, F.stage_r);
     dfree(F.dW);
     dfree(F.dU);
-    F.dW = F.dU = nullptr;
+    dfree(F.dW2);
+    dfree(F.dU2);
+    F.dW = F.dU = F.dW2 = F.dU2 = nullptr;
     F.stage_r = 0;
-    F.dW = dalloc<T>(size_t(H.dev->n * r));
-    F.dU = dalloc<T>(size_t(H.dev->n * r));
-    F.stage_r = r;
+    F.dW = dalloc<T>(size_t(H.dev->n * rr));
+    F.dU = dalloc<T>(size_t(H.dev->n * rr));
+    if (two) {
+        F.dW2 = dalloc<T>(size_t(H.dev->n * rr));
+        F.dU2 = dalloc<T>(size_t(H.dev->n * rr));
+    }
+    F.stage_r = rr;
+    for (cudaEvent_t& e : F.slot_free)
+        if (!e) CUDA_OK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 }
 
 static int family_of(int precision) { return precision == GOFMM_PREC_FP64 ? 0 : 1; }
@@ -653,7 +664,7 @@ int simt_evaluate_on(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu
 }
 
 void device_evaluate(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu, int64_t r, int dtype,
-                     int precision, void* stream, bool host_buffers) {
+                     int precision, void* stream, int host_buffers) {
     if (!W || !U) fail(GOFMM_ERR_ARG, "W and U must not be NULL");
     if (r < 1 || r > (int64_t(1) << 30)) fail(GOFMM_ERR_ARG, "r must be >= 1");
     if (ldw < r || ldu < r) fail(GOFMM_ERR_ARG, "leading dimensions must be >= r");
@@ -682,15 +693,21 @@ void device_evaluate(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu
     void* Ud = U;
     int64_t ldw_d = ldw, ldu_d = ldu;
     const bool pipelined = host_buffers && H.timing == 0 && r >= 2 * kHostChunk;
+    const bool async = host_buffers == 2;
     const int64_t chunk = host_chunk(r);
+    int slot = 0;  // staging slot of this call
     if (host_buffers) {
-        if (fi == 0) ensure_staging<double>(H, 0, r);
-        else ensure_staging<float>(H, 1, r);
+        if (fi == 0) ensure_staging<double>(H, 0, r, async);
+        else ensure_staging<float>(H, 1, r, async);
+        F = &D.fam[fi];
+        if (async) slot = F->stage_slot = F->stage_slot ^ 1;  // asynchronous calls alternate the two slots
+        // the slot's previous call must have copied its U out first
+        CUDA_OK(cudaStreamWaitEvent(s, F->slot_free[slot], 0));
         if (!pipelined)
-            CUDA_OK(cudaMemcpy2DAsync(F->dW, size_t(r) * es, W, size_t(ldw) * es, size_t(r) * es, size_t(D.n),
-                                      cudaMemcpyHostToDevice, s));
-        Wd = F->dW;
-        Ud = F->dU;
+            CUDA_OK(cudaMemcpy2DAsync(slot ? F->dW2 : F->dW, size_t(r) * es, W, size_t(ldw) * es, size_t(r) * es,
+                                      size_t(D.n), cudaMemcpyHostToDevice, s));
+        Wd = slot ? F->dW2 : F->dW;
+        Ud = slot ? F->dU2 : F->dU;
         ldw_d = ldu_d = r;
     }
     auto launch_all = [&](cudaStream_t st) -> int {
@@ -718,11 +735,18 @@ void device_evaluate(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu
             CUDA_OK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
             D.pipe_events.push_back(e);
         }
-        cudaEvent_t start = D.pipe_events[2 * size_t(nch)];
-        CUDA_OK(cudaEventRecord(start, s));  // the copies follow the caller's earlier work
-        CUDA_OK(cudaStreamWaitEvent(D.h2d_stream, start, 0));
-        char* dW = static_cast<char*>(F->dW);
-        char* dU = static_cast<char*>(F->dU);
+        if (async) {
+            // the copies in wait only for the slot to be free, so that they
+            // overlap the evaluation of the call before (W is read as it is
+            // when the call is made)
+            CUDA_OK(cudaStreamWaitEvent(D.h2d_stream, F->slot_free[slot], 0));
+        } else {
+            cudaEvent_t start = D.pipe_events[2 * size_t(nch)];
+            CUDA_OK(cudaEventRecord(start, s));  // the copies follow the caller's earlier work
+            CUDA_OK(cudaStreamWaitEvent(D.h2d_stream, start, 0));
+        }
+        char* dW = static_cast<char*>(slot ? F->dW2 : F->dW);
+        char* dU = static_cast<char*>(slot ? F->dU2 : F->dU);
         for (int64_t k = 0; k < nch; ++k) {
             const int64_t c0 = k * chunk, ck = std::min<int64_t>(chunk, r - c0);
             CUDA_OK(cudaMemcpy2DAsync(dW + size_t(c0) * es, size_t(r) * es, static_cast<const char*>(W) + size_t(c0) * es,
@@ -752,8 +776,11 @@ void device_evaluate(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu
                                       D.d2h_stream));
         }
         D.last_launches = launches;
-        CUDA_OK(cudaStreamSynchronize(D.d2h_stream));
-        CUDA_OK(cudaStreamSynchronize(s));
+        CUDA_OK(cudaEventRecord(F->slot_free[slot], D.d2h_stream));
+        if (!async) {
+            CUDA_OK(cudaStreamSynchronize(D.d2h_stream));
+            CUDA_OK(cudaStreamSynchronize(s));
+        }
         return;
     }
     if (H.timing != 0 || host_buffers) {
@@ -790,9 +817,10 @@ void device_evaluate(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu
         }
     }
     if (host_buffers) {
-        CUDA_OK(cudaMemcpy2DAsync(U, size_t(ldu) * es, F->dU, size_t(r) * es, size_t(r) * es, size_t(D.n),
+        CUDA_OK(cudaMemcpy2DAsync(U, size_t(ldu) * es, Ud, size_t(r) * es, size_t(r) * es, size_t(D.n),
                                   cudaMemcpyDeviceToHost, s));
-        CUDA_OK(cudaStreamSynchronize(s));
+        CUDA_OK(cudaEventRecord(F->slot_free[slot], s));
+        if (!async) CUDA_OK(cudaStreamSynchronize(s));
     }
 }
 
@@ -809,6 +837,10 @@ void device_trim(Handle& H) {
         dfree(F.UTIL);
         dfree(F.dW);
         dfree(F.dU);
+        dfree(F.dW2);
+        dfree(F.dU2);
+        for (cudaEvent_t e : F.slot_free)
+            if (e) cudaEventDestroy(e);
         F = Family{};
     }
 }
@@ -817,6 +849,7 @@ void device_synchronize(Handle& H, void* stream) {
     if (!H.dev) return;
     DeviceGuard g(H.st.prm.device);
     CUDA_OK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    if (H.dev->d2h_stream) CUDA_OK(cudaStreamSynchronize(H.dev->d2h_stream));  // asynchronous host-buffer calls
     CUDA_OK(cudaGetLastError());
     if (const int e = tc_error(*H.dev)) {
         tc_clear_error(*H.dev);  // reported once; the handle stays usable
@@ -904,6 +937,9 @@ void device_destroy(Handle& H) {
     dfree(D->d_idx); dfree(D->d_pts64); dfree(D->d_pts32); dfree(D->d_kblocks);
     for (Family& F : D->fam) {
         dfree(F.kstore); dfree(F.pstore); dfree(F.WT); dfree(F.WTIL); dfree(F.UTIL); dfree(F.dW); dfree(F.dU);
+        dfree(F.dW2); dfree(F.dU2);
+        for (cudaEvent_t e : F.slot_free)
+            if (e) cudaEventDestroy(e);
     }
     if (D->ev_ok)
         for (auto& e : D->ev) cudaEventDestroy(e);

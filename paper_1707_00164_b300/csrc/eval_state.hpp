@@ -76,9 +76,16 @@ struct Family {  // stores and workspace of one element type
     void* WT = nullptr;
     void* WTIL = nullptr;
     void* UTIL = nullptr;
-    void* dW = nullptr;  // device staging for gofmm_evaluate_host
+    // device staging of the host-buffer entry points: slot 0 (and, for
+    // asynchronous calls, which alternate, slot 1); slot_free[k] is recorded
+    // when the copies out of slot k's last call are done
+    void* dW = nullptr;
     void* dU = nullptr;
+    void* dW2 = nullptr;
+    void* dU2 = nullptr;
     int64_t stage_r = 0;
+    int stage_slot = 0;
+    cudaEvent_t slot_free[2] = {nullptr, nullptr};
 };
 
 struct DeviceState {

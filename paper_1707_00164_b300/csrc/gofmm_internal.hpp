@@ -183,8 +183,10 @@ struct Handle {
 
 // Device side (eval.cu); all throw Error.
 void device_prepare(Handle& H, int64_t r_max, int precision);
+// host_buffers: 0 device pointers, 1 host pointers (returns when U is
+// written), 2 host pointers, asynchronous (U is final after device_synchronize)
 void device_evaluate(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu, int64_t r,
-                     int dtype, int precision, void* stream, bool host_buffers);
+                     int dtype, int precision, void* stream, int host_buffers);
 void device_evaluate_static(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu, int64_t r, int dtype,
                             int precision, void* stream);
 void device_destroy(Handle& H);

@@ -459,7 +459,7 @@ TuneResult autotune(Handle& H, int64_t r, int precision, const char* cache_path,
                 device_set_tc_config(H, precision, piece, c[0], c[1]);
                 device_prepare(H, r, precision);
                 const float ms = time_median(
-                    [&] { device_evaluate(H, W.p, r, U.p, r, r, GOFMM_DTYPE_F32, precision, s, false); }, s, kWarm,
+                    [&] { device_evaluate(H, W.p, r, U.p, r, r, GOFMM_DTYPE_F32, precision, s, 0); }, s, kWarm,
                     kReps);
                 device_synchronize(H, s);  // a kernel that gave up a wait fails the tuning
                 res.cand_piece[res.n] = piece;

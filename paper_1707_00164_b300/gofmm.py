@@ -80,6 +80,8 @@ def _load():
                                      C.c_int, C.c_int, C.c_void_p]),
         "gofmm_evaluate_host": (C.c_int, [H, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                           C.c_int64, C.c_int, C.c_int, C.c_void_p]),
+        "gofmm_evaluate_host_async": (C.c_int, [H, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
+                                                C.c_int64, C.c_int, C.c_int, C.c_void_p]),
         "gofmm_evaluate_static": (C.c_int, [H, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64,
                                             C.c_int64, C.c_int, C.c_int, C.c_void_p]),
         "gofmm_synchronize": (C.c_int, [H, C.c_void_p]),
@@ -260,17 +262,28 @@ def evaluate_static(h: Handle, W, U, precision: int, stream=None):
                                      _dtype_code(W), int(precision), C.c_void_p(s.cuda_stream)))
 
 
-def evaluate_host(h: Handle, W: np.ndarray, U: np.ndarray, precision: int, stream=None):
-    """As evaluate, with host numpy arrays (C-contiguous rows); blocks until
-    U holds the result."""
+def _host_args(W: np.ndarray, U: np.ndarray):
     if W.ndim != 2 or W.shape != U.shape or W.dtype != U.dtype:
         raise ValueError("W and U must be 2-D arrays of one shape and dtype")
     if W.strides[1] != W.itemsize or U.strides[1] != U.itemsize:
         raise ValueError("W and U need unit column stride")
+    return (C.c_void_p(W.ctypes.data), W.strides[0] // W.itemsize, C.c_void_p(U.ctypes.data),
+            U.strides[0] // U.itemsize, W.shape[1], _dtype_code(W))
+
+
+def evaluate_host(h: Handle, W: np.ndarray, U: np.ndarray, precision: int, stream=None):
+    """As evaluate, with host numpy arrays (C-contiguous rows); blocks until
+    U holds the result."""
     sp = None if stream is None else C.c_void_p(stream.cuda_stream)
-    _check(LIB.gofmm_evaluate_host(h.ptr, C.c_void_p(W.ctypes.data), W.strides[0] // W.itemsize,
-                                   C.c_void_p(U.ctypes.data), U.strides[0] // U.itemsize,
-                                   W.shape[1], _dtype_code(W), int(precision), sp))
+    _check(LIB.gofmm_evaluate_host(h.ptr, *_host_args(W, U), int(precision), sp))
+
+
+def evaluate_host_async(h: Handle, W: np.ndarray, U: np.ndarray, precision: int, stream=None):
+    """As evaluate_host, but returns once the work is enqueued: U is final
+    (and W may change) after synchronize(h, stream).  W and U must stay
+    alive until then; pinned memory lets the copies overlap other calls."""
+    sp = None if stream is None else C.c_void_p(stream.cuda_stream)
+    _check(LIB.gofmm_evaluate_host_async(h.ptr, *_host_args(W, U), int(precision), sp))
 
 
 def debug_stall_next(h: Handle, precision: int):

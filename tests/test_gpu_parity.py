@@ -176,3 +176,31 @@ def test_host_buffer_pipeline_is_bitwise_the_device_evaluation(prec, dt):
     assert np.all(np.isnan(Upad[:, r:]))  # nothing written past r
     if prec == G.PREC_FP64:
         assert np.linalg.norm(Upad[:, :r] - O.evaluate(st, K, W)) <= 1e-12 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("prec,dt,r", [(G.PREC_FP64, np.float64, 300), (G.PREC_BF16X3, np.float32, 300),
+                                       (G.PREC_BF16X3, np.float32, 37)], ids=["fp64", "bf16x3", "bf16x3_r37"])
+def test_host_async_calls_in_flight_are_bitwise_the_device_evaluation(prec, dt, r):
+    """Several asynchronous host-buffer calls in flight at once (the two
+    device staging slots alternate; r = 300 runs the two-chunk pipeline,
+    r = 37 one chunk), then a synchronous call: each U bitwise the
+    device-buffer evaluation of its W, final after synchronize."""
+    w = wl.scaled(wl.C1, 3000)
+    h, st, K = both(w, leaf_size=64, callback=False)
+    Ws = [torch.from_numpy(wl.scaled(wl.C1, 3000, w_seed=10 + i).rhs(r).astype(dt)).pin_memory() for i in range(3)]
+    refs = []
+    for W in Ws:
+        Wd = W.cuda()
+        Ud = torch.empty_like(Wd)
+        G.evaluate(h, Wd, Ud, prec)
+        G.synchronize(h)
+        refs.append(Ud.cpu().numpy())
+    Us = [torch.full_like(W, float("nan")).pin_memory() for W in Ws]
+    for W, U in zip(Ws, Us):
+        G.evaluate_host_async(h, W.numpy(), U.numpy(), prec)
+    G.synchronize(h)
+    for U, ref in zip(Us, refs):
+        assert np.array_equal(U.numpy(), ref)
+    Ux = np.full((w.n, r), np.nan, dtype=dt)
+    G.evaluate_host(h, Ws[1].numpy(), Ux, prec)  # a synchronous call after asynchronous ones
+    assert np.array_equal(Ux, refs[1])
