@@ -220,11 +220,11 @@ int gofmm_evaluate_host(gofmm_handle* h, const void* W, int64_t ldw, void* U, in
  * gofmm_synchronize(h, stream) returns.  W must hold its values when the
  * call is made (its copy to the device does not wait for earlier work on
  * `stream`; the evaluation does).  Consecutive asynchronous calls on a
- * handle alternate two device staging slots (each call waits on the device
- * until the slot's previous call has copied its U out), so the copies of one
- * call overlap the evaluation of the next; with pinned host buffers a stream
- * of calls runs at about the larger of the copy time and the evaluation
- * time per call.  Calls whose U regions overlap must not be in flight
+ * handle take three device staging slots in turn (each call waits on the
+ * device until the slot's previous call has copied its U out), so the copy
+ * in of one call, the evaluation of the one before and the copy out of the
+ * one before that can run at once; with pinned host buffers the copies and
+ * the evaluation of a stream of calls overlap.  Calls whose U regions overlap must not be in flight
  * together.  The result is bitwise that of gofmm_evaluate.  Errors: as
  * gofmm_evaluate_host; a bounded wait given up is reported by
  * gofmm_synchronize.

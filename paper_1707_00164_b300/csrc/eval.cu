@@ -476,8 +476,13 @@ static void ensure_workspace(Handle& H, int fi, int64_t r) {
     DeviceState& D = *H.dev;
     Family& F = D.fam[fi];
     if (F.ws_r >= r) return;
-    dfree(F.WT); dfree(F.WTIL); dfree(F.UTIL); dfree(F.dW); dfree(F.dU); dfree(F.dW2); dfree(F.dU2);
-    F.WT = F.WTIL = F.UTIL = F.dW = F.dU = F.dW2 = F.dU2 = nullptr;
+    dfree(F.WT); dfree(F.WTIL); dfree(F.UTIL);
+    F.WT = F.WTIL = F.UTIL = nullptr;
+    for (int k = 0; k < Family::kStageSlots; ++k) {  // staging too, so it is sized again
+        dfree(F.sW[k]);
+        dfree(F.sU[k]);
+        F.sW[k] = F.sU[k] = nullptr;
+    }
     F.ws_r = 0;
     F.WT = dalloc<T>(size_t(D.n * r));
     F.WTIL = dalloc<T>(size_t(std::max<int64_t>(D.S_tot, 1) * r));
@@ -486,23 +491,24 @@ static void ensure_workspace(Handle& H, int fi, int64_t r) {
 }
 
 template <typename T>
-static void ensure_staging(Handle& H, int fi, int64_t r, bool two) {
+static void ensure_staging(Handle& H, int fi, int64_t r, bool all) {
     Family& F = H.dev->fam[fi];
-    if (F.dW && F.stage_r >= r && (!two || F.dW2)) return;
+    const int want = all ? Family::kStageSlots : 1;
+    bool have = F.stage_r >= r;
+    for (int k = 0; k < want; ++k) have = have && F.sW[k];
+    if (have) return;
     // buffers still read or written by earlier asynchronous calls
     CUDA_OK(cudaDeviceSynchronize());
     const int64_t rr = std::max(r, F.stage_r);
-    dfree(F.dW);
-    dfree(F.dU);
-    dfree(F.dW2);
-    dfree(F.dU2);
-    F.dW = F.dU = F.dW2 = F.dU2 = nullptr;
+    for (int k = 0; k < Family::kStageSlots; ++k) {
+        dfree(F.sW[k]);
+        dfree(F.sU[k]);
+        F.sW[k] = F.sU[k] = nullptr;
+    }
     F.stage_r = 0;
-    F.dW = dalloc<T>(size_t(H.dev->n * rr));
-    F.dU = dalloc<T>(size_t(H.dev->n * rr));
-    if (two) {
-        F.dW2 = dalloc<T>(size_t(H.dev->n * rr));
-        F.dU2 = dalloc<T>(size_t(H.dev->n * rr));
+    for (int k = 0; k < want; ++k) {
+        F.sW[k] = dalloc<T>(size_t(H.dev->n * rr));
+        F.sU[k] = dalloc<T>(size_t(H.dev->n * rr));
     }
     F.stage_r = rr;
     for (cudaEvent_t& e : F.slot_free)
@@ -692,22 +698,28 @@ void device_evaluate(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu
     const void* Wd = W;
     void* Ud = U;
     int64_t ldw_d = ldw, ldu_d = ldu;
-    const bool pipelined = host_buffers && H.timing == 0 && r >= 2 * kHostChunk;
     const bool async = host_buffers == 2;
-    const int64_t chunk = host_chunk(r);
+    // synchronous calls overlap their own column halves with the copies;
+    // asynchronous calls overlap whole calls (the copies of one with the
+    // evaluation of the next), so they run as one chunk on the copy streams
+    const bool pipelined = host_buffers && H.timing == 0 && (async || r >= 2 * kHostChunk);
+    const int64_t chunk = async ? r : host_chunk(r);
     int slot = 0;  // staging slot of this call
     if (host_buffers) {
         if (fi == 0) ensure_staging<double>(H, 0, r, async);
         else ensure_staging<float>(H, 1, r, async);
         F = &D.fam[fi];
-        if (async) slot = F->stage_slot = F->stage_slot ^ 1;  // asynchronous calls alternate the two slots
+        if (async) {  // asynchronous calls take the slots in turn
+            slot = F->stage_next;
+            F->stage_next = (F->stage_next + 1) % Family::kStageSlots;
+        }
         // the slot's previous call must have copied its U out first
         CUDA_OK(cudaStreamWaitEvent(s, F->slot_free[slot], 0));
         if (!pipelined)
-            CUDA_OK(cudaMemcpy2DAsync(slot ? F->dW2 : F->dW, size_t(r) * es, W, size_t(ldw) * es, size_t(r) * es,
+            CUDA_OK(cudaMemcpy2DAsync(F->sW[slot], size_t(r) * es, W, size_t(ldw) * es, size_t(r) * es,
                                       size_t(D.n), cudaMemcpyHostToDevice, s));
-        Wd = slot ? F->dW2 : F->dW;
-        Ud = slot ? F->dU2 : F->dU;
+        Wd = F->sW[slot];
+        Ud = F->sU[slot];
         ldw_d = ldu_d = r;
     }
     auto launch_all = [&](cudaStream_t st) -> int {
@@ -745,8 +757,8 @@ void device_evaluate(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu
             CUDA_OK(cudaEventRecord(start, s));  // the copies follow the caller's earlier work
             CUDA_OK(cudaStreamWaitEvent(D.h2d_stream, start, 0));
         }
-        char* dW = static_cast<char*>(slot ? F->dW2 : F->dW);
-        char* dU = static_cast<char*>(slot ? F->dU2 : F->dU);
+        char* dW = static_cast<char*>(F->sW[slot]);
+        char* dU = static_cast<char*>(F->sU[slot]);
         for (int64_t k = 0; k < nch; ++k) {
             const int64_t c0 = k * chunk, ck = std::min<int64_t>(chunk, r - c0);
             CUDA_OK(cudaMemcpy2DAsync(dW + size_t(c0) * es, size_t(r) * es, static_cast<const char*>(W) + size_t(c0) * es,
@@ -835,10 +847,10 @@ void device_trim(Handle& H) {
         dfree(F.WT);
         dfree(F.WTIL);
         dfree(F.UTIL);
-        dfree(F.dW);
-        dfree(F.dU);
-        dfree(F.dW2);
-        dfree(F.dU2);
+        for (int k = 0; k < Family::kStageSlots; ++k) {
+            dfree(F.sW[k]);
+            dfree(F.sU[k]);
+        }
         for (cudaEvent_t e : F.slot_free)
             if (e) cudaEventDestroy(e);
         F = Family{};
@@ -936,8 +948,11 @@ void device_destroy(Handle& H) {
     }
     dfree(D->d_idx); dfree(D->d_pts64); dfree(D->d_pts32); dfree(D->d_kblocks);
     for (Family& F : D->fam) {
-        dfree(F.kstore); dfree(F.pstore); dfree(F.WT); dfree(F.WTIL); dfree(F.UTIL); dfree(F.dW); dfree(F.dU);
-        dfree(F.dW2); dfree(F.dU2);
+        dfree(F.kstore); dfree(F.pstore); dfree(F.WT); dfree(F.WTIL); dfree(F.UTIL);
+        for (int k = 0; k < Family::kStageSlots; ++k) {
+            dfree(F.sW[k]);
+            dfree(F.sU[k]);
+        }
         for (cudaEvent_t e : F.slot_free)
             if (e) cudaEventDestroy(e);
     }

@@ -76,16 +76,17 @@ struct Family {  // stores and workspace of one element type
     void* WT = nullptr;
     void* WTIL = nullptr;
     void* UTIL = nullptr;
-    // device staging of the host-buffer entry points: slot 0 (and, for
-    // asynchronous calls, which alternate, slot 1); slot_free[k] is recorded
-    // when the copies out of slot k's last call are done
-    void* dW = nullptr;
-    void* dU = nullptr;
-    void* dW2 = nullptr;
-    void* dU2 = nullptr;
+    // device staging of the host-buffer entry points: slot 0 (synchronous
+    // calls) and, for asynchronous calls, which take the slots in turn, all
+    // kStageSlots: the copy in of one call, the evaluation of the one before
+    // and the copy out of the one before that run at once.  slot_free[k] is
+    // recorded when the copy out of slot k's last call is done.
+    static constexpr int kStageSlots = 3;
+    void* sW[kStageSlots] = {nullptr, nullptr, nullptr};
+    void* sU[kStageSlots] = {nullptr, nullptr, nullptr};
     int64_t stage_r = 0;
-    int stage_slot = 0;
-    cudaEvent_t slot_free[2] = {nullptr, nullptr};
+    int stage_next = 0;
+    cudaEvent_t slot_free[kStageSlots] = {nullptr, nullptr, nullptr};
 };
 
 struct DeviceState {
