@@ -101,10 +101,26 @@ def test_evaluate_without_a_gpu_fails_loudly():
     h = G.compress(G.Entries.gaussian(K.points, 0.3, 1e-3), G.default_params(leaf_size=32))
     W = np.ones((w.n, 2))
     U = np.zeros_like(W)
-    with pytest.raises(G.GofmmError) as e:
-        G.evaluate_host(h, W, U, G.PREC_FP64)
-    assert e.value.code == G.ERR_CUDA
-    assert not U.any()
+    for fn in (G.evaluate_host, G.evaluate_host_async):
+        with pytest.raises(G.GofmmError) as e:
+            fn(h, W, U, G.PREC_FP64)
+        assert e.value.code == G.ERR_CUDA
+        assert not U.any()
+
+
+def test_host_evaluation_argument_errors():
+    """Checked before any device work (no GPU needed): overlapping W and U,
+    mismatched dtype and precision, both host entry points alike."""
+    w, K = _small()
+    h = G.compress(G.Entries.gaussian(K.points, 0.3, 1e-3), G.default_params(leaf_size=32))
+    W = np.ones((w.n, 2))
+    for fn in (G.evaluate_host, G.evaluate_host_async):
+        with pytest.raises(G.GofmmError) as e:
+            fn(h, W, W, G.PREC_FP64)  # U aliases W
+        assert e.value.code == G.ERR_ARG
+        with pytest.raises(G.GofmmError) as e:
+            fn(h, W, np.zeros_like(W), G.PREC_FP32)  # F64 data, FP32 precision
+        assert e.value.code == G.ERR_UNSUPPORTED
 
 
 def test_device_sampling_needs_a_generator_and_a_gpu():
