@@ -83,10 +83,21 @@ def test_batch_cache_hit_sets_every_handle(tmp_path):
     rs = [16, 200, 64]
     key = G.autotune_key(hs, rs, G.PREC_BF16)
     path = tmp_path / "tune.json"
-    _cache(path, [{"key": key, "piece": 128, "schedule": 0, "order": 0}])
+    _cache(path, [{"key": key, "piece": 128, "schedule": 1, "order": 1}])
     t = G.autotune_batch(hs, rs, G.PREC_BF16, str(path))
     assert t["from_cache"] and t["piece"] == 128
-    assert all(G.get_tc_config(h, G.PREC_BF16)["piece"] == 128 for h in hs)
+    # the batch form (staged) and order come with the piece
+    assert all(G.get_tc_config(h, G.PREC_BF16) == dict(piece=128, schedule=1, order=1) for h in hs)
+
+
+def test_cache_hit_with_the_schedule_order(tmp_path):
+    h = _handle()
+    key = G.autotune_key([h], [512], G.PREC_TF32)
+    path = tmp_path / "tune.json"
+    _cache(path, [{"key": key, "piece": 256, "schedule": G.SCHED_HYBRID, "order": G.ORDER_SCHEDULE}])
+    t = G.autotune(h, 512, G.PREC_TF32, str(path))
+    assert t["from_cache"] and (t["schedule"], t["order"]) == (G.SCHED_HYBRID, G.ORDER_SCHEDULE)
+    assert G.get_tc_config(h, G.PREC_TF32) == dict(piece=256, schedule=G.SCHED_HYBRID, order=G.ORDER_SCHEDULE)
 
 
 def test_cache_miss_needs_a_gpu_and_leaves_the_file_alone(tmp_path):
