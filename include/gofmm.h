@@ -224,8 +224,10 @@ int gofmm_evaluate_host(gofmm_handle* h, const void* W, int64_t ldw, void* U, in
  * device until the slot's previous call has copied its U out), so the copy
  * in of one call, the evaluation of the one before and the copy out of the
  * one before that can run at once; with pinned host buffers the copies and
- * the evaluation of a stream of calls overlap.  Calls whose U regions overlap must not be in flight
- * together.  The result is bitwise that of gofmm_evaluate.  Errors: as
+ * the evaluation of a stream of calls overlap.  The copies out of one
+ * handle's calls run in call order, so calls writing the same U leave the
+ * last call's result.  The result is bitwise that of gofmm_evaluate.
+ * Errors: as
  * gofmm_evaluate_host; a bounded wait given up is reported by
  * gofmm_synchronize.
  */
