@@ -227,8 +227,7 @@ int gofmm_evaluate_host(gofmm_handle* h, const void* W, int64_t ldw, void* U, in
  * the evaluation of a stream of calls overlap.  The copies out of one
  * handle's calls run in call order, so calls writing the same U leave the
  * last call's result.  The result is bitwise that of gofmm_evaluate.
- * Errors: as
- * gofmm_evaluate_host; a bounded wait given up is reported by
+ * Errors: as gofmm_evaluate_host; a bounded wait given up is reported by
  * gofmm_synchronize.
  */
 int gofmm_evaluate_host_async(gofmm_handle* h, const void* W, int64_t ldw, void* U, int64_t ldu,
