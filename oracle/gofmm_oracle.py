@@ -12,11 +12,17 @@ notes of the repository.
 Input: an entry routine ``K(I, J) -> ndarray`` (plus ``K.diag(I)``) -- the
 only input the method needs (§1, problem statement).  Points are never seen.
 
-Pinning (tests/test_oracle_*.py): dense brute force K.W, exactness at full
-rank and with no far field, the explicitly assembled H-matrix of the
+Pinning (tests/test_oracle_pins*.py): dense brute force K.W, exactness at
+full rank and with no far field, the explicitly assembled H-matrix of the
 telescoping formula, symmetry, the Fig. 2 worked example of FindFar/MergeFar,
 kNN against a k-d tree, pivoted QR against LAPACK GEQP3, the tree split on
-1-D points, and the eps2-versus-tau trend.  No function here is unpinned.
+1-D points, the eps2-versus-tau trend, a hand-tallied near-list ballot
+(votes, ties, budget, symmetrisation), hand-counted importance-sampled rows
+I' and the uniformity of their tail, the centroid scores and Alg. 1 split
+recomputed on explicit Gram vectors (Gram-l2 and angle), and a hand-counted
+flop tally.  Each of these pins fails when the corresponding step is
+mutated (ballot or sampling order reversed, ties flipped, the self vote or
+the node's own indices kept, a centroid-score term changed).
 """
 from __future__ import annotations
 
@@ -206,17 +212,15 @@ def _median_split(idx: np.ndarray, v: np.ndarray):
     return np.sort(idx[order[:half]]), np.sort(idx[order[half:]])
 
 
-def metric_split(K, diagK, idx, kind, seed, h, n_centroid):
-    """Alg. 1 (metricSplit) with the sampled centroid of §2.1.
-
-    c = mean of the Gram vectors of n_c sampled indices of the node, so
-    d(i, c)^2 = K_ii - (2/n_c) sum_{j in C} K_ij + const (Gram-l2) and
-    d(i, c) = 1 - (sum_j K_ij / n_c)^2 / (K_ii |c|^2) (angle).
-    p = argmax_i d(i, c), q = argmax_i d(i, p), split on d_ip - d_iq.
-    Ties of an argmax go to the smallest original index.
-    """
-    nc = min(n_centroid, idx.size)
-    C = partial_shuffle(idx, nc, stream_key(seed, _P_CENTROID, h))
+def centroid_scores(K, diagK, idx, C, kind):
+    """Distance of every index of the node to the sampled centroid
+    c = (1/n_c) sum_{j in C} phi_j (§2.1, "Tree partitioning"), from entries
+    only: d(i, c)^2 - |c|^2 = K_ii - (2/n_c) sum_{j in C} K_ij for the
+    Gram-l2 distance (the constant |c|^2 is dropped: it does not move the
+    argmax), and d(i, c) = 1 - (phi_i, c)^2 / (|phi_i|^2 |c|^2) with
+    (phi_i, c) = (1/n_c) sum_j K_ij and |c|^2 = (1/n_c^2) sum_{j,k} K_jk for
+    the angle distance."""
+    nc = C.size
     Kc = K(idx, C)
     S = np.zeros(idx.size)
     for t in range(nc):
@@ -233,6 +237,20 @@ def metric_split(K, diagK, idx, kind, seed, h, n_centroid):
         cc = acc / (nc * nc)
         a = S / nc
         score = 1.0 - (a * a) / (kii * cc)
+    return score
+
+
+def metric_split(K, diagK, idx, kind, seed, h, n_centroid):
+    """Alg. 1 (metricSplit) with the sampled centroid of §2.1.
+
+    The centroid is taken over n_c indices drawn from the node;
+    p = argmax_i d(i, c) (`centroid_scores`), q = argmax_i d(i, p), split on
+    d_ip - d_iq.  Ties of an argmax go to the smallest original index.
+    """
+    nc = min(n_centroid, idx.size)
+    C = partial_shuffle(idx, nc, stream_key(seed, _P_CENTROID, h))
+    kii = diagK[idx]
+    score = centroid_scores(K, diagK, idx, C, kind)
     p = int(idx[int(np.argmax(score))])
     dp = distance_values(kind, kii, diagK[p], K(idx, [p])[:, 0])
     q = int(idx[int(np.argmax(dp))])
@@ -706,6 +724,32 @@ def evaluate_leaves(st: Structure, K, W: np.ndarray, leaves) -> Dict[int, np.nda
     return out
 
 
+class _AbsEntries:
+    """|K(I, J)| entry by entry (diagonal too)."""
+
+    def __init__(self, K):
+        self.K = K
+
+    def __call__(self, I, J):
+        return np.abs(self.K(I, J))
+
+    def diag(self, I):
+        return np.abs(self.K.diag(I))
+
+
+def evaluate_abs(st: Structure, K, W: np.ndarray) -> np.ndarray:
+    """Rounding-error scale of the evaluation: Alg. 7 run on |P|, |K| and
+    |W| (every interpolation matrix, every sampled block and the right-hand
+    sides replaced by their entrywise absolute values).  Each task of
+    Table 2 is a product of nonnegative factors, so the result bounds
+    |P^T K P| |W| and |K_{ba}| |W| term by term; a product computed with unit
+    roundoff u is then off by at most a small multiple of u times this value,
+    element by element.  Test infrastructure for the tensor-precision bounds
+    (no passage of the paper defines it)."""
+    ast = dataclasses.replace(st, P={h: np.abs(P) for h, P in st.P.items()})
+    return evaluate(ast, _AbsEntries(K), np.abs(np.asarray(W, dtype=np.float64)))
+
+
 def dense_rows(K, rows: np.ndarray, W: np.ndarray, block=256) -> np.ndarray:
     """Exact rows of K W by brute force."""
     n = W.shape[0]
@@ -763,10 +807,12 @@ def assemble(st: Structure, K) -> np.ndarray:
 
 def flop_count(st: Structure, r: int) -> dict:
     """Algorithmic flops per evaluation (Table 2 with the real block shapes):
-    N2S/S2N count 2 s (ncols) r each, S2S 2 s_b s_a r per far pair, L2L
+    N2S/S2N count 2 s (ncols - s) r each -- P = [I | T] Pi^T, and its
+    identity part is a copy, not arithmetic (§2.2, low-rank approximation
+    and the cost paragraph after Alg. 7) -- S2S 2 s_b s_a r per far pair, L2L
     2 |b| |a| r per near pair."""
     tree = st.tree
-    n2s = sum(2 * P.shape[0] * P.shape[1] * r for P in st.P.values())
+    n2s = sum(2 * P.shape[0] * (P.shape[1] - P.shape[0]) * r for P in st.P.values())
     s2s = sum(2 * st.skel[b].size * st.skel[int(a)].size * r
               for b, lst in st.far.items() for a in lst)
     l2l = 0
