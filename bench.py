@@ -688,19 +688,21 @@ def native_arm(args):
     else:
         kname = "tc_gemm_pair_kernel" if tune["schedule"] == G.SCHED_PAIR else "tc_gemm_kernel"
         kdesc = f"{kname}<{prec_name}>: every launch of the staged schedule (N2S, S2S, S2N, L2L)"
-    # algorithmic bytes of those launches: every cached block and
-    # interpolation tile once, W read once, skeleton weights and potentials
-    # written and read once each, U written once (FP32)
+    # algorithmic bytes of those launches: every cached block and the T part
+    # of every interpolation matrix once (the identity part of P is a copy of
+    # skeleton rows, counted with the right-hand sides), W read once,
+    # skeleton weights and potentials written and read once each, U written
+    # once (FP32)
     be = {"tf32": 4, "bf16": 2, "bf16x3": 4, "fp32": 4, "fp64": 8}[prec_name]
-    alg_bytes = ((st["near_entries"] + st["far_entries"] + st["interp_entries"]) * be + w.n * r * be
+    alg_bytes = ((st["near_entries"] + st["far_entries"] + st["interp_t_entries"]) * be + w.n * r * be
                  + 4 * st["skel_total"] * r * be + w.n * r * 4)
     # per stage (one launch per stage, timing level 1): algorithmic flops and
     # bytes of the stage against the tensor (or ALU) and HBM peaks
     hbm = peaks.get("hbm_gbs", 6400.0)
     stage_work = {
-        "upward": (r * st["flops_n2s"], st["interp_entries"] * be + w.n * r * be + st["skel_total"] * r * be),
+        "upward": (r * st["flops_n2s"], st["interp_t_entries"] * be + w.n * r * be + st["skel_total"] * r * be),
         "s2s": (r * st["flops_s2s"], st["far_entries"] * be + 2 * st["skel_total"] * r * be),
-        "s2n": (r * st["flops_s2n"], st["interp_entries"] * be + 2 * st["skel_total"] * r * be),
+        "s2n": (r * st["flops_s2n"], st["interp_t_entries"] * be + 2 * st["skel_total"] * r * be),
         "leaf": (r * st["flops_l2l"], st["near_entries"] * be + w.n * r * be + w.n * r * 4),
     }
     per_stage = {}

@@ -141,7 +141,10 @@ typedef struct gofmm_stats_t {
     double mean_rank;
     int64_t near_pairs, far_pairs;  /* ordered pairs                             */
     int64_t max_near;               /* largest |Near(beta)|                      */
-    /* algorithmic flops per right-hand side column (Table 2, real shapes) */
+    /* algorithmic flops per right-hand side column (Table 2, real shapes):
+       N2S and S2N count 2 s (ncols - s) per node, the T part of
+       P = [I | T] Pi^T (the identity part is a copy, not arithmetic); S2S
+       2 s_b s_a per far pair; L2L 2 |b| |a| per near pair */
     double flops_n2s, flops_s2s, flops_s2n, flops_l2l;
     /* entries held by the cached K blocks (near, far) */
     int64_t near_entries, far_entries;
@@ -150,6 +153,7 @@ typedef struct gofmm_stats_t {
     int ann_iterations;
     double ann_recall;
     double compress_seconds;
+    int64_t interp_t_entries;       /* sum over nodes of s * (ncols - s): the T parts */
 } gofmm_stats_t;
 
 typedef struct gofmm_handle gofmm_handle;

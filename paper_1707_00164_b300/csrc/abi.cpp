@@ -551,8 +551,12 @@ int gofmm_stats(const gofmm_handle* hd, gofmm_stats_t* s) {
             s->max_rank = std::max(s->max_rank, r);
             s->skel_total += r;
             s->interp_entries += int64_t(st.P[h].size());
+            // P = [I | T] Pi^T: only the T part (s x (ncols - s)) is
+            // arithmetic; the identity part is a copy (Table 2, real shapes)
+            const int64_t t_entries = int64_t(st.P[h].size()) - r * r;
+            s->interp_t_entries += t_entries;
             ++cnt;
-            s->flops_n2s += 2.0 * double(st.P[h].size());
+            s->flops_n2s += 2.0 * double(t_entries);
             for (int64_t a : st.far[h]) {
                 s->flops_s2s += 2.0 * double(r) * double(st.skel[a].size());
                 s->far_entries += r * int64_t(st.skel[a].size());

@@ -63,7 +63,7 @@ class StatsC(C.Structure):
                 ("flops_l2l", C.c_double), ("near_entries", C.c_int64), ("far_entries", C.c_int64),
                 ("interp_entries", C.c_int64), ("skel_total", C.c_int64),
                 ("ann_iterations", C.c_int), ("ann_recall", C.c_double),
-                ("compress_seconds", C.c_double)]
+                ("compress_seconds", C.c_double), ("interp_t_entries", C.c_int64)]
 
 
 def _load():

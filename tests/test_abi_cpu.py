@@ -92,6 +92,11 @@ def test_stats_flop_count_matches_oracle():
     s = G.stats(h)
     f = O.flop_count(st, 1)
     assert s["flops_n2s"] == f["n2s"] and s["flops_s2s"] == f["s2s"] and s["flops_l2l"] == f["l2l"]
+    assert s["flops_s2n"] == f["s2n"]
+    # only the T part of P counts: s (ncols - s) entries per node
+    t_entries = sum(P.shape[0] * (P.shape[1] - P.shape[0]) for P in st.P.values())
+    assert s["interp_t_entries"] == t_entries and s["flops_n2s"] == 2 * t_entries
+    assert s["interp_entries"] == sum(P.size for P in st.P.values())
     assert s["skel_total"] == sum(v.size for v in st.skel.values())
 
 
