@@ -724,7 +724,7 @@ def evaluate_leaves(st: Structure, K, W: np.ndarray, leaves) -> Dict[int, np.nda
     return out
 
 
-class _AbsEntries:
+class AbsEntries:
     """|K(I, J)| entry by entry (diagonal too)."""
 
     def __init__(self, K):
@@ -747,7 +747,7 @@ def evaluate_abs(st: Structure, K, W: np.ndarray) -> np.ndarray:
     element by element.  Test infrastructure for the tensor-precision bounds
     (no passage of the paper defines it)."""
     ast = dataclasses.replace(st, P={h: np.abs(P) for h, P in st.P.items()})
-    return evaluate(ast, _AbsEntries(K), np.abs(np.asarray(W, dtype=np.float64)))
+    return evaluate(ast, AbsEntries(K), np.abs(np.asarray(W, dtype=np.float64)))
 
 
 def dense_rows(K, rows: np.ndarray, W: np.ndarray, block=256) -> np.ndarray:

@@ -12,7 +12,7 @@ import pytest
 import oracle as O
 import paper_1707_00164_b300 as G
 import workloads as wl
-from common import assert_same_structure, both
+from common import assert_same_structure, assert_tensor_close, both
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -141,6 +141,7 @@ def test_full_size_fp32_against_oracle_rows():
     rows = torch.from_numpy(g["rows"]).cuda()
     got = U[rows][:, : g["u_oracle"].shape[1]].double().cpu().numpy()
     assert rel(got, g["u_oracle"]) <= FP32_TOL
+    assert_tensor_close(got, g["u_oracle"], g["u_abs"], g["u_kabs"], G.PREC_FP32)  # row by row, all 512 columns
     # same rows as the oracle => same error against the exact product
     assert abs(rel(got, g["u_exact"]) - rel(g["u_oracle"], g["u_exact"])) <= 1e-4
     # K~ symmetric: V^T (K~ W) == (K~ V)^T W

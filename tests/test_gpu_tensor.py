@@ -17,7 +17,7 @@ import pytest
 import oracle as O
 import paper_1707_00164_b300 as G
 import workloads as wl
-from common import assert_same_structure, both
+from common import abs_product, assert_same_structure, assert_tensor_close, both
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -76,6 +76,7 @@ def test_tensor_core_evaluate_matches_oracle(name, w, r, over, prec):
     U = run(h, W, prec)
     assert np.all(np.isfinite(U))
     assert rel(U, ref) <= tol(prec, K, W), (rel(U, ref), sum_condition(K, W))
+    assert_tensor_close(U, ref, O.evaluate_abs(st, K, W), abs_product(K, W), prec)
 
 
 def test_tensor_core_is_deterministic_and_r_independent():
@@ -104,8 +105,10 @@ def test_full_size_tensor_core_against_oracle_rows(prec):
     U = torch.empty_like(W)
     G.evaluate(h, W, U, prec)
     G.synchronize(h)
-    got = U[torch.from_numpy(g["rows"]).cuda()][:, : g["u_oracle"].shape[1]].double().cpu().numpy()
+    assert g["u_oracle"].shape[1] == 512   # every r-tile of the launch is compared
+    got = U[torch.from_numpy(g["rows"]).cuda()].double().cpu().numpy()
     assert rel(got, g["u_oracle"]) <= TOL[prec]
+    assert_tensor_close(got, g["u_oracle"], g["u_abs"], g["u_kabs"], prec)
     # the configuration the benchmark times (autotuned) and every other one
     # the tuner measured give bitwise this result at full size
     ref = U.clone()
@@ -158,8 +161,8 @@ GOLDEN_C3 = os.path.join(os.path.dirname(__file__), "golden", "imq4d_n131072_r20
 def test_precision_workload_every_mode_against_oracle_rows():
     """IMQ kernel, 4-D uniform points, N = 131072, m = 256, s = 512 (ranks up
     to 512: tasks split across two MMA N tiles), tau 1e-6, r = 2048: every
-    mode against the oracle's FP64 rows (first 64 columns written by
-    tests/golden/make_rows.py)."""
+    mode against the oracle's FP64 rows (all 2048 columns, written by
+    tests/golden/make_rows.py), element by element in the tensor modes."""
     g = np.load(GOLDEN_C3)
     w = wl.C3
     K = w.matrix()
@@ -175,3 +178,4 @@ def test_precision_workload_every_mode_against_oracle_rows():
         G.synchronize(h)
         got = U[rows][:, :cols].double().cpu().numpy()
         assert rel(got, g["u_oracle"]) <= tol, (prec, rel(got, g["u_oracle"]))
+        assert_tensor_close(got, g["u_oracle"], g["u_abs"], g["u_kabs"], prec)
