@@ -248,6 +248,7 @@ int gofmm_evaluate_host_async(gofmm_handle* h, const void* W, int64_t ldw, void*
  * of this library.
  *   - The handle must already be prepared for `precision` (gofmm_prepare or
  *     an earlier gofmm_evaluate); otherwise ERR_ARG.
+ *   - r in [1, 2^30] and ldw, ldu >= r, else ERR_ARG.
  *   - Needs (N + 2 * S) * r elements of scratch (S = sum of skeleton sizes,
  *     gofmm_stats skel_total), each rounded up to 256 bytes; larger calls
  *     fail with ERR_ARG and a message naming the sizes.

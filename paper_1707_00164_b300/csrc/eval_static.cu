@@ -51,7 +51,10 @@ size_t round_up(size_t x) { return (x + 255) / 256 * 256; }
 void device_evaluate_static(Handle& H, const void* W, int64_t ldw, void* U, int64_t ldu, int64_t r, int dtype,
                             int precision, void* stream) {
     if (!W || !U) fail(GOFMM_ERR_ARG, "W and U must not be NULL");
-    if (r < 1 || ldw < r || ldu < r) fail(GOFMM_ERR_ARG, "need r >= 1 and leading dimensions >= r");
+    // the same bound on r as gofmm_evaluate: the scratch sizes below are
+    // products with r and must not wrap, and the kernels take r as an int
+    if (r < 1 || r > (int64_t(1) << 30)) fail(GOFMM_ERR_ARG, "r must be in [1, 2^30]");
+    if (ldw < r || ldu < r) fail(GOFMM_ERR_ARG, "leading dimensions must be >= r");
     if (precision != GOFMM_PREC_FP64 && precision != GOFMM_PREC_FP32)
         fail(GOFMM_ERR_UNSUPPORTED, "the static-scratch evaluation supports FP64 and FP32 only");
     if ((precision == GOFMM_PREC_FP64) != (dtype == GOFMM_DTYPE_F64))

@@ -44,6 +44,34 @@ def test_static_scratch_matches_evaluate_twice(prec, dtype, tol):
         assert np.isfinite(err) and err <= tol, err
 
 
+def test_static_scratch_allocates_nothing():
+    """After a first call (which looks up the array's device address), calls
+    at several r leave the device's free memory unchanged: nothing is
+    allocated per call.  Every buffer is made before the first reading and
+    the results are compared only after the last one."""
+    w, h = _handle()
+    rs = (8, 24, 40)
+    G.prepare(h, max(rs), G.PREC_FP32)
+    Ws = {r: torch.from_numpy(w.rhs(r)).to("cuda", torch.float32) for r in rs}
+    Us = {r: [torch.full_like(Ws[r], float("nan")) for _ in range(2)] for r in rs}
+    refs = {r: torch.empty_like(Ws[r]) for r in rs}
+    for r in rs:
+        G.evaluate(h, Ws[r], refs[r], G.PREC_FP32)
+    G.evaluate_static(h, Ws[rs[0]], Us[rs[0]][0], G.PREC_FP32)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for k in range(2):
+        for r in rs:
+            G.evaluate_static(h, Ws[r], Us[r][k], G.PREC_FP32)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    for r in rs:
+        for k in range(2):
+            err = float(torch.linalg.norm((Us[r][k] - refs[r]).double()) / torch.linalg.norm(refs[r].double()))
+            assert np.isfinite(err) and err <= FP32_TOL, (r, k, err)
+
+
 def test_static_scratch_rejects_oversize_and_unprepared():
     w, h = _handle(1500)
     W = torch.zeros((w.n, 8), dtype=torch.float64, device="cuda")
