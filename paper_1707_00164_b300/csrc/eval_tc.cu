@@ -59,32 +59,15 @@ constexpr long long kSpinLimit = 2000000000LL;  // clock cycles (about a second)
 constexpr int kErrProducer = 1, kErrMma = 2, kErrEpilogue = 3, kErrDependency = 4, kErrTmemPair = 5,
               kErrGenerator = 6;
 constexpr int kGenWarps = 8;      // generator warps of the in-kernel entry generation
-// their shared-memory area: job ring, barriers and flags (1 KB), the row
-// points of the current task piece (256 x 16 floats), one chunk's column
-// points (64 x 16 floats)
-constexpr int kGenSmem = 1024 + (kMaxN + 64) * kGenMaxDpad * 4;
+constexpr int kGenThreads = 192 + 32 * kGenWarps;  // threads of the kernel variant with generator warps
 
-// Named barrier 1 over the eight generator warps.
-__device__ __forceinline__ void gen_bar_sync() {
-    asm volatile("bar.sync 1, %0;" ::"n"(kGenWarps * 32) : "memory");
-}
-// ... and its reduction form: true iff every generator thread passes true.
-__device__ __forceinline__ int gen_bar_and(bool pred) {
-    int r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %1, 0;\n\t"
-        "bar.red.and.pred q, 1, %2, p;\n\tselp.b32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"(int(pred)), "n"(kGenWarps * 32)
-        : "memory");
-    return r;
-}
-
-// One chunk of a generated block tile: rows perm[rows .. rows + m) (the
+// One stage of a generated block tile: rows perm[rows .. rows + m) (the
 // rest of the n_pad rows zero), columns perm[cols .. cols + kvalid) (the rest
-// of the chunk zero), written into stage `stage`.
+// of the stage zero), written into stage `stage`.  The columns' points reach
+// the job's slot of the column-point ring by a bulk copy that completes on
+// the job's barrier.
 struct GenJob {
-    int64_t rows, cols, cols_end;  // cols_end: end of the slab's column list
+    int64_t rows, cols;
     int32_t seg, stage, m, kvalid, n_pad, stop;
 };
 
@@ -113,13 +96,17 @@ struct Cfg {
     // epilogue staging tile (hi and lo) of the kernels without generator warps
     static constexpr int kEpiBytes = (kSplit ? 2 : 1) * kTileBytes;
     static_assert(kSmem <= 227 * 1024, "shared memory per CTA");
-    static_assert(kSmem + kGenSmem <= 227 * 1024, "shared memory per CTA with generator warps");
+    // generator warps' area: barriers, flags and the job ring (1 KB), then
+    // one slot of column points per job (kStageK points of up to 16 floats)
+    static constexpr int kColSlot = kStageK * kGenMaxDpad * 4;
+    static constexpr int kGenBytes = 1024 + kStages * kColSlot;
+    static_assert(kSmem + kGenBytes <= 227 * 1024, "shared memory per CTA with generator warps");
     static_assert(kSmem + kEpiBytes <= 227 * 1024, "shared memory per CTA with the epilogue staging tile");
 };
 // dynamic shared memory of tc_gemm_kernel<MODE, NMAX, GEN>
 template <int MODE, int NMAX, bool GEN>
 constexpr int gemm_smem() {
-    return Cfg<MODE, NMAX>::kSmem + (GEN ? kGenSmem : Cfg<MODE, NMAX>::kEpiBytes);
+    return Cfg<MODE, NMAX>::kSmem + (GEN ? Cfg<MODE, NMAX>::kGenBytes : Cfg<MODE, NMAX>::kEpiBytes);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -473,13 +460,159 @@ __device__ __forceinline__ void write_tile_staged(const TcSeg& sg, const TcTask&
     }
 }
 
+// A generator lane's row: its point pre-scaled by -2, with 1 in the norm's
+// slot, so that |y|^2 - 2 x.y is one FMA chain over the column point's DP
+// floats (coordinates, then |y|^2, then zeros); n = |x|^2.  Cached across
+// the stages of a task piece (rows, segment, row block).
+template <int DP>
+struct GenRow {
+    float x[DP];
+    float n;
+    int64_t rows;
+    int seg, rb;
+};
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+// The items of one generated stage that warp gw owns: item i = (block rb of
+// 32 rows, 16-byte column group g), i = gw, gw + kGenWarps, ...; lane = row
+// rb * 32 + lane.  DP: floats per point (compile time).  Entries:
+// d2 = max(|x|^2 + |y|^2 - 2 x.y, 0) (exactly 0 for the same index);
+// Gaussian exp(-d2 inv) = 2^(d2 * (-inv log2 e)); IMQ 1 / sqrt(1 + d2 inv);
+// plus the shift on the same index (K_ii).  Written in the MMA layout.
+template <int MODE, int DP>
+__device__ __forceinline__ void gen_stage(GenRow<DP>& R, const GenJob& jb, const TcSeg& sg, const float* cpts,
+                                          uint8_t* bh, uint8_t* bl, int gw, int lane) {
+    constexpr bool kSplit = MODE == TC_BF16X3;
+    constexpr int kPer = MODE == TC_TF32 ? 4 : 8;         // columns per 16-byte group
+    constexpr int kGroups = 4 * (kSplit ? 1 : 2);         // 16-byte column groups per stage
+    const int nrb = (jb.n_pad + 31) / 32;
+    const bool gauss = sg.gen_kind == GOFMM_GEN_GAUSSIAN;
+    const float scale = gauss ? -sg.gen_inv * 1.4426950408889634f : sg.gen_inv;  // log2(e)
+    const float4* tab = reinterpret_cast<const float4*>(sg.pts);
+    for (int item = gw; item < nrb * kGroups; item += kGenWarps) {
+        const int rb = item % nrb, g = item / nrb;
+        const int n = rb * 32 + lane;
+        if (R.rows != jb.rows || R.seg != jb.seg || R.rb != rb) {
+            float x[DP];
+#pragma unroll
+            for (int q4 = 0; q4 < DP / 4; ++q4) {
+                float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (n < jb.m) t = tab[(jb.rows + n) * (DP / 4) + q4];
+                x[4 * q4] = t.x;
+                x[4 * q4 + 1] = t.y;
+                x[4 * q4 + 2] = t.z;
+                x[4 * q4 + 3] = t.w;
+            }
+            R.n = 0.f;
+#pragma unroll
+            for (int d = 0; d < DP; ++d) {
+                if (d == sg.dim) R.n = x[d];
+                R.x[d] = d == sg.dim ? 1.f : -2.f * x[d];
+            }
+            R.rows = jb.rows;
+            R.seg = jb.seg;
+            R.rb = rb;
+        }
+        if (n >= jb.n_pad) continue;
+        const int k0 = g * kPer;
+        // entry e is on the diagonal (the same index-list position) iff e == de
+        const int64_t dd = jb.rows + n - (jb.cols + k0);
+        const int de = dd >= 0 && dd < kPer ? int(dd) : -1;
+        const int kv = n < jb.m ? jb.kvalid - k0 : 0;  // valid columns of this group (<= 0: none)
+        float v[kPer];
+#pragma unroll
+        for (int e = 0; e < kPer; ++e) {
+            const float4* cp = reinterpret_cast<const float4*>(cpts + (k0 + e) * DP);
+            float d2 = R.n;
+#pragma unroll
+            for (int q4 = 0; q4 < DP / 4; ++q4) {
+                const float4 c = cp[q4];  // the same address for the whole warp
+                d2 = fmaf(R.x[4 * q4], c.x, d2);
+                d2 = fmaf(R.x[4 * q4 + 1], c.y, d2);
+                d2 = fmaf(R.x[4 * q4 + 2], c.z, d2);
+                d2 = fmaf(R.x[4 * q4 + 3], c.w, d2);
+            }
+            d2 = e == de ? 0.f : fmaxf(d2, 0.f);
+            float y = gauss ? ex2_approx(d2 * scale) : rsqrtf(fmaf(d2, scale, 1.f));
+            if (e == de) y += sg.gen_shift;
+            v[e] = e < kv ? y : 0.f;
+        }
+        // group g of the stage: K-half g / 4, 16-byte group g % 4 of it
+        const uint32_t pos = uint32_t(g >> 2) * uint32_t(jb.n_pad) * 64u + swz64(uint32_t(n), uint32_t((g & 3) * 16));
+        if constexpr (MODE == TC_TF32) {
+            *reinterpret_cast<float4*>(bh + pos) =
+                make_float4(round_tf32(v[0]), round_tf32(v[1]), round_tf32(v[2]), round_tf32(v[3]));
+        } else {
+            uint4 oh, ol;
+            __nv_bfloat162* hh = reinterpret_cast<__nv_bfloat162*>(&oh);
+            __nv_bfloat162* ll = reinterpret_cast<__nv_bfloat162*>(&ol);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                hh[e] = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+                const float2 hf = __bfloat1622float2(hh[e]);
+                ll[e] = __floats2bfloat162_rn(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
+            }
+            *reinterpret_cast<uint4*>(bh + pos) = oh;
+            if constexpr (kSplit) *reinterpret_cast<uint4*>(bl + pos) = ol;
+        }
+    }
+}
+
+// The job loop of a generator warp for segments of point width DP: waits
+// for each job (bounded), generates its share of the stage, publishes it.
+// Returns the width of a job of another width (not consumed), or -1 at the
+// stop job or on an error.  gbars: the job-full, job-empty and stage-done
+// barriers, kStages each.
+template <int MODE, int NMAX, int DP>
+__device__ __noinline__ int gen_loop(const TcParams& p, const GenJob* jobs, const float* colring, uint8_t* base,
+                                     uint64_t* gbars, int& seq, int gw, int lane) {
+    using C = Cfg<MODE, NMAX>;
+    GenRow<DP> R;
+    R.rows = -1;
+    R.seg = R.rb = -1;
+    R.n = 0.f;
+#pragma unroll
+    for (int d = 0; d < DP; ++d) R.x[d] = 0.f;
+    for (;; ++seq) {
+        const int j = seq % C::kStages;
+        const uint32_t full = smem_u32(&gbars[j]), empty = smem_u32(&gbars[C::kStages + j]);
+        const uint32_t par = uint32_t((seq / C::kStages) & 1);
+        bool ok = true;
+        if (lane == 0) ok = mbar_wait(full, par, p.err, kErrGenerator);
+        ok = __shfl_sync(0xffffffffu, ok, 0) != 0;  // lane 0 waited for the whole warp
+        if (!ok) return -1;
+        // every lane observes the completed phase itself (the job's fields
+        // and the bulk-copied column points become visible)
+        (void)mbar_try_wait(full, par);
+        __syncwarp();
+        const GenJob jb = jobs[j];
+        if (jb.stop) return -1;
+        const TcSeg& sg = p.segs[jb.seg];
+        if (sg.dpad != DP) return sg.dpad;
+        uint8_t* bh = base + jb.stage * C::kStageBytes + 2 * C::kAUnit;
+        uint8_t* bl = bh + C::kPart;  // split BF16x3: the lo copy of the stage
+        gen_stage<MODE, DP>(R, jb, sg, colring + j * (C::kColSlot / 4), bh, bl, gw, lane);
+        // generic writes -> visible to the MMAs (async proxy); this warp is
+        // done with the job's column points
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+            mbar_arrive(smem_u32(&gbars[2 * C::kStages + jb.stage]));  // stage written
+            mbar_arrive(empty);
+        }
+    }
+}
+
 // Persistent grouped GEMM: CTA b processes tiles b, b + gridDim.x, ... (tile
 // = task * n_rtiles + r-tile; tasks are sorted heaviest first).  The stage
 // ring runs on across tiles and the accumulator is double-buffered in TMEM
 // (2 x 256 columns), so the epilogue of one tile overlaps the MMAs of the
 // next.
 template <int MODE, int NMAX, bool GEN>
-__global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
+__global__ void __launch_bounds__(GEN ? kGenThreads : 192, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
     using C = Cfg<MODE, NMAX>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -490,8 +623,7 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
     uint64_t* gbars = reinterpret_cast<uint64_t*>(gen_area);
     uint8_t* stage_isgen = gen_area + 3 * 8 * C::kStages;
     GenJob* jobs = reinterpret_cast<GenJob*>(gen_area + 256);
-    float* rowpts = reinterpret_cast<float*>(gen_area + 1024);
-    float* colpts = rowpts + kMaxN * kGenMaxDpad;
+    float* colring = reinterpret_cast<float*>(gen_area + 1024);  // kStages slots of C::kColSlot bytes
     auto genq_full = [&](int j) { return smem_u32(&gbars[j]); };
     auto genq_empty = [&](int j) { return smem_u32(&gbars[C::kStages + j]); };
     auto gen_done = [&](int s) { return smem_u32(&gbars[2 * C::kStages + s]); };
@@ -624,14 +756,23 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
                                 GenJob& jb = jobs[j];
                                 jb.rows = sl.b_off;
                                 jb.cols = sl.gen_cols + int64_t(q) * C::kStageK;
-                                jb.cols_end = sl.gen_cols + sl.k;
                                 jb.seg = tt.seg;
                                 jb.stage = stage;
                                 jb.m = tk.m;
                                 jb.kvalid = max(0, min(C::kStageK, sl.k - q * C::kStageK));
                                 jb.n_pad = tk.n_pad;
                                 jb.stop = 0;
-                                mbar_arrive(genq_full(j));
+                                // the stage's column points (consecutive rows of the
+                                // point table, dpad floats each: a multiple of 16
+                                // bytes) into the job's slot
+                                const uint32_t cbytes = uint32_t(jb.kvalid) * uint32_t(sg.dpad) * 4u;
+                                if (cbytes) {
+                                    mbar_expect_tx(genq_full(j), cbytes);
+                                    bulk_g2s(smem_u32(colring) + uint32_t(j * C::kColSlot),
+                                             sg.pts + jb.cols * sg.dpad, cbytes, genq_full(j));
+                                } else {
+                                    mbar_arrive(genq_full(j));
+                                }
                                 ++gseq;
                             }
                         }
@@ -838,125 +979,32 @@ __global__ void __launch_bounds__(GEN ? 448 : 192, 1) tc_gemm_kernel(const __gri
         if (store_thread) bulk_wait_all();  // no bulk store may still read the staging tile
     } else {
         if constexpr (GEN) {
-            // ---- generator warps 6..13: block tiles of generated slabs,
-            // written into the stage's B region in the MMA layout (row n,
-            // 16-byte group g of 8 BF16 / 4 TF32 columns, 64-byte swizzle).
-            // The eight warps work on one chunk at a time (named barrier 1):
-            // the task piece's row points stay in shared memory across its
-            // chunks, each chunk brings its column points.
-            const int gt = threadIdx.x - 192;
-            int64_t cur_rows = -1;
-            int cur_seg = -1;
-            // column points of the slab's next chunk, loaded while this chunk
-            // is computed (one float4 per thread: 64 columns x 16 floats at most)
-            float4 pf = make_float4(0.f, 0.f, 0.f, 0.f);
-            int64_t pf_cols = -1;
-            int pf_seg = -1;
-            for (int seq = 0;; ++seq) {
-                const int j = seq % C::kStages;
-                bool ok = true;
-                if (lane == 0) ok = mbar_wait(genq_full(j), uint32_t((seq / C::kStages) & 1), p.err, kErrGenerator);
-                ok = __shfl_sync(0xffffffffu, ok, 0) != 0;  // lane 0 waited for the whole warp
-                __syncwarp();
-                const int all_ok = gen_bar_and(ok);
-                if (!all_ok) break;
-                const GenJob jb = jobs[j];
-                if (jb.stop) break;
-                const TcSeg& sg = p.segs[jb.seg];
-                const int dp = sg.dpad;
-                const float4* tab = reinterpret_cast<const float4*>(sg.pts);
-                if (jb.rows != cur_rows || jb.seg != cur_seg) {
-                    // row points transposed (coordinate-major), so the 32
-                    // rows a warp handles read 32 consecutive words
-                    for (int e = gt; e < jb.m * dp / 4; e += kGenWarps * 32) {
-                        const float4 x = tab[jb.rows * (dp / 4) + e];
-                        const int n = e / (dp / 4), d0 = (e % (dp / 4)) * 4;
-                        rowpts[(d0 + 0) * kMaxN + n] = x.x;
-                        rowpts[(d0 + 1) * kMaxN + n] = x.y;
-                        rowpts[(d0 + 2) * kMaxN + n] = x.z;
-                        rowpts[(d0 + 3) * kMaxN + n] = x.w;
-                    }
-                    cur_rows = jb.rows;
-                    cur_seg = jb.seg;
+            // ---- generator warps 6..: block tiles of generated slabs,
+            // written into the stage's B region in the MMA layout.  The job
+            // loop runs in the instantiation for the point width of the
+            // current segment and returns here when a job of another width
+            // arrives (a batch can mix matrices) or at the end.
+            int seq = 0, dpad = 0;
+            for (;;) {
+                if (dpad == 0) {  // width of the next job, once it is posted
+                    const int j = seq % C::kStages;
+                    const uint32_t par = uint32_t((seq / C::kStages) & 1);
+                    bool ok = true;
+                    if (lane == 0) ok = mbar_wait(genq_full(j), par, p.err, kErrGenerator);
+                    ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
+                    if (!ok) break;
+                    (void)mbar_try_wait(genq_full(j), par);
+                    __syncwarp();
+                    if (jobs[j].stop) break;
+                    dpad = p.segs[jobs[j].seg].dpad;
                 }
-                if (gt < jb.kvalid * dp / 4)
-                    reinterpret_cast<float4*>(colpts)[gt] =
-                        (jb.cols == pf_cols && jb.seg == pf_seg) ? pf : tab[jb.cols * (dp / 4) + gt];
-                pf_cols = -1;
-                {
-                    const int64_t nc = jb.cols + C::kStageK;
-                    if (nc < jb.cols_end) {
-                        const int nk = int(jb.cols_end - nc < C::kStageK ? jb.cols_end - nc : C::kStageK);
-                        if (gt < nk * dp / 4) pf = tab[nc * (dp / 4) + gt];
-                        pf_cols = nc;
-                        pf_seg = jb.seg;
-                    }
+                switch (dpad) {  // the host allows 4, 8, 12 or 16 floats per point
+                    case 4: dpad = gen_loop<MODE, NMAX, 4>(p, jobs, colring, base, gbars, seq, warp - 6, lane); break;
+                    case 8: dpad = gen_loop<MODE, NMAX, 8>(p, jobs, colring, base, gbars, seq, warp - 6, lane); break;
+                    case 12: dpad = gen_loop<MODE, NMAX, 12>(p, jobs, colring, base, gbars, seq, warp - 6, lane); break;
+                    default: dpad = gen_loop<MODE, NMAX, 16>(p, jobs, colring, base, gbars, seq, warp - 6, lane); break;
                 }
-                gen_bar_sync();  // points in shared memory
-                uint8_t* bh = base + jb.stage * C::kStageBytes + 2 * C::kAUnit;
-                uint8_t* bl = bh + C::kPart;  // split BF16x3: the lo copy of the stage
-                constexpr int kPer = MODE == TC_TF32 ? 4 : 8;  // columns per 16-byte group
-                for (int it = gt; it < jb.n_pad * 4 * C::kSub; it += kGenWarps * 32) {
-                    // a warp: 32 consecutive rows of one column group (the
-                    // column points are then the same word for the whole warp)
-                    const int n = it % jb.n_pad, g = it / jb.n_pad;
-                    float v[kPer];
-#pragma unroll
-                    for (int e = 0; e < kPer; ++e) v[e] = 0.f;
-                    if (n < jb.m) {
-                        // the row point in registers; coordinates past dim are
-                        // zero in both points, so all dp of them can be summed
-                        float xr[kGenMaxDpad];
-#pragma unroll
-                        for (int d = 0; d < kGenMaxDpad; ++d) xr[d] = d < dp ? rowpts[d * kMaxN + n] : 0.f;
-#pragma unroll
-                        for (int e = 0; e < kPer; ++e) {
-                            const int k = g * kPer + e;
-                            const float4* cp = reinterpret_cast<const float4*>(colpts + k * dp);
-                            float acc = 0.f;
-#pragma unroll
-                            for (int q4 = 0; q4 < kGenMaxDpad / 4; ++q4) {
-                                if (q4 * 4 < dp) {
-                                    const float4 c = cp[q4];  // the same address for the whole warp
-                                    const float t0 = xr[4 * q4] - c.x, t1 = xr[4 * q4 + 1] - c.y;
-                                    const float t2 = xr[4 * q4 + 2] - c.z, t3 = xr[4 * q4 + 3] - c.w;
-                                    acc += t0 * t0 + t1 * t1 + t2 * t2 + t3 * t3;
-                                }
-                            }
-                            if (k < jb.kvalid) {
-                                float x = sg.gen_kind == GOFMM_GEN_GAUSSIAN ? __expf(-acc * sg.gen_inv)
-                                                                           : rsqrtf(1.f + acc * sg.gen_inv);
-                                if (jb.rows + n == jb.cols + k) x += sg.gen_shift;  // the same index: K_ii
-                                v[e] = x;
-                            }
-                        }
-                    }
-                    // group g of the stage: K-half g / 4, 16-byte group g % 4 of it
-                    const uint32_t pos = uint32_t(g >> 2) * uint32_t(jb.n_pad) * 64u + swz64(uint32_t(n), uint32_t((g & 3) * 16));
-                    if constexpr (MODE == TC_TF32) {
-                        *reinterpret_cast<float4*>(bh + pos) =
-                            make_float4(round_tf32(v[0]), round_tf32(v[1]), round_tf32(v[2]), round_tf32(v[3]));
-                    } else {
-                        uint4 oh, ol;
-                        __nv_bfloat16* hh = reinterpret_cast<__nv_bfloat16*>(&oh);
-                        __nv_bfloat16* ll = reinterpret_cast<__nv_bfloat16*>(&ol);
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            hh[e] = __float2bfloat16_rn(v[e]);
-                            ll[e] = __float2bfloat16_rn(v[e] - __bfloat162float(hh[e]));
-                        }
-                        *reinterpret_cast<uint4*>(bh + pos) = oh;
-                        if constexpr (C::kSplit) *reinterpret_cast<uint4*>(bl + pos) = ol;
-                    }
-                }
-                gen_bar_sync();  // every warp done with this chunk's points before the next overwrites them
-                // generic writes -> visible to the MMAs (async proxy)
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) {
-                    mbar_arrive(gen_done(jb.stage));
-                    mbar_arrive(genq_empty(j));
-                }
+                if (dpad < 0) break;
             }
         }
     }
@@ -1845,14 +1893,23 @@ TcPrec& tc_plan(Handle& H, DeviceState& D, int precision) {
         std::vector<TileJob> jobs;
         build_tc_plan(H.st, D, *t, jobs);
         if (t->gen) {
-            // point table in index-list order for the generator warps
-            if (H.K.dim > kGenMaxDpad)
-                fail(GOFMM_ERR_UNSUPPORTED, "in-kernel generation on the tensor cores supports at most 16 coordinates");
-            const int dp = (H.K.dim + 3) / 4 * 4;
+            // point table in index-list order for the generator warps: the
+            // coordinates in FP32, then the squared norm of those FP32
+            // coordinates (summed in FP64, rounded once), zero padding to a
+            // multiple of four floats
+            if (H.K.dim + 1 > kGenMaxDpad)
+                fail(GOFMM_ERR_UNSUPPORTED, "in-kernel generation on the tensor cores supports at most 15 coordinates");
+            const int dp = (H.K.dim + 1 + 3) / 4 * 4;
             std::vector<float> tab(D.idx.size() * size_t(dp), 0.f);
-            for (size_t q = 0; q < D.idx.size(); ++q)
-                for (int d = 0; d < H.K.dim; ++d)
-                    tab[q * size_t(dp) + size_t(d)] = float(H.K.pts[size_t(D.idx[q]) * size_t(H.K.dim) + size_t(d)]);
+            for (size_t q = 0; q < D.idx.size(); ++q) {
+                double nrm = 0.0;
+                for (int d = 0; d < H.K.dim; ++d) {
+                    const float x = float(H.K.pts[size_t(D.idx[q]) * size_t(H.K.dim) + size_t(d)]);
+                    tab[q * size_t(dp) + size_t(d)] = x;
+                    nrm += double(x) * double(x);
+                }
+                tab[q * size_t(dp) + size_t(H.K.dim)] = float(nrm);
+            }
             t->gen_pts = dupload(tab);
             t->gen_dim = H.K.dim;
             t->gen_dpad = dp;
@@ -1962,7 +2019,7 @@ template <int MODE, int NMAX, bool GEN>
 static void launch_gemm(const TcParams& p, int num_sms, cudaStream_t s) {
     const int grid = std::min(p.ntiles, num_sms);
     tc_gemm_kernel<MODE, NMAX, GEN>
-        <<<unsigned(grid), GEN ? 448 : 192, gemm_smem<MODE, NMAX, GEN>(), s>>>(p);
+        <<<unsigned(grid), GEN ? kGenThreads : 192, gemm_smem<MODE, NMAX, GEN>(), s>>>(p);
     CUDA_OK(cudaGetLastError());
 }
 
@@ -1972,7 +2029,7 @@ template <int MODE, int NMAX, bool GEN>
 static void launch_gemm_coop(const TcParams& p, int num_sms, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(std::min(p.ntiles, num_sms)));
-    cfg.blockDim = dim3(GEN ? 448 : 192);
+    cfg.blockDim = dim3(GEN ? kGenThreads : 192);
     cfg.dynamicSmemBytes = gemm_smem<MODE, NMAX, GEN>();
     cfg.stream = s;
     cudaLaunchAttribute attr[1];

@@ -88,7 +88,8 @@ struct TcSeg {
     const TcTile* tiles;  // segment tile lists (TcParams::tiles == nullptr): this segment's tiles
     // in-kernel entry generation (generated slabs): point table in index-list
     // order (row t = the point of perm[t], tree order then skeleton lists),
-    // dpad floats per point (dim padded to a multiple of 4);
+    // dpad floats per point (the coordinates, then the point's squared norm,
+    // then zeros to a multiple of 4);
     // GOFMM_GEN_GAUSSIAN exp(-d2 inv) or GOFMM_GEN_IMQ 1/sqrt(1 + d2 inv),
     // plus shift where the row and column are the same index-list position
     const float* pts;
@@ -106,7 +107,7 @@ struct TcSeg {
     int* counters;
     int32_t dep_nrt, pad3;
 };
-constexpr int kGenMaxDpad = 16;  // generated blocks: at most 16 coordinates per point
+constexpr int kGenMaxDpad = 16;  // generated blocks: at most 16 floats per point (15 coordinates and the norm)
 constexpr int kMaxSegs = 64;  // segments per launch (kernel parameters, by value)
 constexpr int kClaimSlots = 64;  // per-stage launches of one evaluation that claim tiles dynamically
 
