@@ -72,6 +72,7 @@ def parse():
     ap.add_argument("--config", default="",
                     help="force the tensor-core configuration of the main workload, piece/schedule/order "
                          "(e.g. 128/staged/local); no autotuning")
+    ap.add_argument("--no-study", action="store_true", help="skip the HSS-vs-FMM accuracy/time study")
     ap.add_argument("--n", type=int, default=0,
                     help="profiling only: the same recipe at another N (not a bench line)")
     return ap.parse_args()
@@ -463,6 +464,110 @@ def serving_bench(G, torch, dev, works, handles, loads=(0.5, 0.8, 1.0), prec_nam
     return out
 
 
+def hss_fmm_study(G, torch, dev, steps=5):
+    """Accuracy against time for fixed-rank HSS (budget 0, the paper's way to
+    enforce HSS in §3) and FMM (budget 3 % and 10 %), as in §4 "Comparison
+    between FMM and HSS" (Fig. 6): compression time on the host, evaluation
+    time on the GPU in split BF16x3 (tensor cores, default launch
+    configuration) and FP64 (CUDA cores), and eps2 of each against the exact
+    K W on 100 seeded rows (FP64, from the workload's own entry routine)."""
+    stream = torch.cuda.current_stream(dev)
+    exact = {}
+    cases = []
+    for label, w in wl.hss_fmm_cases():
+        K = w.matrix()
+        rows = wl.sample_rows(w.n)
+        Wn = w.rhs(w.r)
+        if w.name not in exact:
+            exact[w.name] = K(rows, np.arange(w.n)) @ Wn
+        ref = exact[w.name]
+        t0 = time.perf_counter()
+        h = G.compress(G.Entries.gaussian(K.points, w.bandwidth, w.shift),
+                       G.default_params(**w.params(), device=dev.index or 0))
+        st = G.stats(h)
+        ent = {"case": label, "scheme": "HSS" if w.budget == 0 else "FMM", "N": w.n, "m": w.leaf_size,
+               "s": w.max_rank, "budget": w.budget, "compress_s": round(time.perf_counter() - t0, 3),
+               "mean_rank": round(st["mean_rank"], 1), "max_rank": st["max_rank"],
+               "near_pairs": st["near_pairs"], "far_pairs": st["far_pairs"],
+               "gflop_per_eval": w.r * (st["flops_n2s"] + st["flops_s2s"] + st["flops_s2n"] + st["flops_l2l"]) / 1e9}
+        for name, dt in (("bf16x3", np.float32), ("fp64", np.float64)):
+            pr = G.PRECISIONS[name]
+            W = torch.from_numpy(Wn.astype(dt)).to(dev)
+            U = torch.empty_like(W)
+            G.prepare(h, w.r, pr)
+            for _ in range(2):
+                G.evaluate(h, W, U, pr, stream)
+            G.synchronize(h, stream)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(steps):
+                G.evaluate(h, W, U, pr, stream)
+            b.record(stream)
+            G.synchronize(h, stream)
+            got = U[torch.from_numpy(rows).to(dev)].double().cpu().numpy()
+            ent[name] = {"eval_ms": round(a.elapsed_time(b) / steps, 4),
+                         "eps2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+            del W, U
+        G.free(h)
+        cases.append(ent)
+    return {"what": "fixed-rank HSS (budget 0) vs FMM (budget 3 %, 10 %), tau 0, r 512; eps2 against the exact "
+                    "K W on 100 seeded rows; compression on the host, evaluation on the GPU",
+            "cases": cases}
+
+
+def accurate_bench(G, torch, dev, steps=10, tuning=True):
+    """The evaluation at a configuration whose compression error is small:
+    workloads.ACCURATE (3-D Gaussian, N = 65536, r = 512, ranks below the
+    cap, tau 1e-7).  Split BF16x3 (autotuned) and FP64 timed; eps2 of each
+    against the exact K W on 100 seeded rows (FP64, from the workload's own
+    entry routine) and of BF16x3 against the FP64 evaluation (the precision
+    error; the FP64 path matches the oracle to 1e-12 in the tests)."""
+    w = wl.ACCURATE
+    K = w.matrix()
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    h = G.compress(G.Entries.gaussian(K.points, w.bandwidth, w.shift),
+                   G.default_params(**w.params(), device=dev.index or 0))
+    comp = time.perf_counter() - t0
+    st = G.stats(h)
+    rows = wl.sample_rows(w.n)
+    Wn = w.rhs(w.r)
+    exact = K(rows, np.arange(w.n)) @ Wn
+    flops = w.r * (st["flops_n2s"] + st["flops_s2s"] + st["flops_s2n"] + st["flops_l2l"])
+    out = {"workload": f"{w.name}: Gaussian h {w.bandwidth} on {w.dim}-D uniform points, N {w.n}, m {w.leaf_size}, "
+                       f"s {w.max_rank}, tau {w.tau}, budget {w.budget:.0%}, r {w.r}",
+           "compress_s": round(comp, 2), "mean_rank": round(st["mean_rank"], 1), "max_rank": st["max_rank"],
+           "flops_per_eval": flops, "modes": {}}
+    got = {}
+    for name, dt in (("fp64", np.float64), ("bf16x3", np.float32)):
+        pr = G.PRECISIONS[name]
+        W = torch.from_numpy(Wn.astype(dt)).to(dev)
+        U = torch.empty_like(W)
+        G.prepare(h, w.r, pr)
+        tune = G.autotune(h, w.r, pr, None, stream) if name == "bf16x3" and tuning else None
+        for _ in range(2):
+            G.evaluate(h, W, U, pr, stream)
+        G.synchronize(h, stream)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            G.evaluate(h, W, U, pr, stream)
+        b.record(stream)
+        G.synchronize(h, stream)
+        ms = a.elapsed_time(b) / steps
+        got[name] = U[torch.from_numpy(rows).to(dev)].double().cpu().numpy()
+        ent = {"ms": ms, "value": w.n * w.r / (ms / 1e3), "unit": UNIT, "tflops": flops / (ms / 1e3) / 1e12,
+               "eps2_vs_exact_KW": float(np.linalg.norm(got[name] - exact) / np.linalg.norm(exact))}
+        if tune is not None:
+            ent["config"] = {k: tune[k] for k in ("piece", "schedule", "order")}
+        out["modes"][name] = ent
+        del W, U
+    out["modes"]["bf16x3"]["eps2_vs_fp64_evaluation"] = float(
+        np.linalg.norm(got["bf16x3"] - got["fp64"]) / np.linalg.norm(got["fp64"]))
+    G.free(h)
+    return out
+
+
 # ------------------------------------------------------------------ native --
 def native_arm(args):
     import torch
@@ -753,6 +858,27 @@ def native_arm(args):
                 ent = {"ms": gms, "value": w.n * r / (gms / 1e3), "accuracy": accuracy_of(hg, pr)}
                 if tg is not None:
                     ent["config"] = {k: tg[k] for k in ("piece", "schedule", "order")}
+                # ALU / SFU roofline of the entry generation: every entry the
+                # evaluation needs (near and far blocks, once) costs 3 d + 4
+                # ALU operations (differences, squares and their sum, the
+                # scale) and one SFU operation (exp or rsqrt); peaks from the
+                # SM count, 128 FP32 lanes and 16 SFU lanes per SM, and the
+                # SM clock sampled during the main run
+                sgen = G.stats(hg)
+                entries = sgen["near_entries"] + sgen["far_entries"]
+                mhz = clk.summary().get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
+                alu_ops = entries * (3 * w.dim + 4)
+                alu_peak = SMS * FP32_LANES * mhz * 1e6
+                sfu_peak = SMS * 16 * mhz * 1e6
+                ent["generator_roofline"] = {
+                    "bound": "alu", "entries_per_eval": entries, "ops_per_entry": 3 * w.dim + 4,
+                    "achieved_gops": alu_ops / (gms / 1e3) / 1e9, "peak_gops": alu_peak / 1e9,
+                    "frac": alu_ops / (gms / 1e3) / alu_peak,
+                    "sfu_frac": entries / (gms / 1e3) / sfu_peak,
+                    "alu_bound_ms": 1e3 * alu_ops / alu_peak,
+                    "note": (f"derived peak: {SMS} SMs x {FP32_LANES} FP32 lanes x {mhz:.0f} MHz (one op per lane "
+                             f"per clock); SFU {SMS} x 16 lanes; entries counted once (the kernel generates each "
+                             f"block once per tile of r-tiles)")}
                 generated[name] = ent
             G.free(hg)
         except Exception as e:
@@ -796,6 +922,19 @@ def native_arm(args):
     if "error" in extra:
         batching = batching or {"error": extra["error"]}
 
+    accurate = None
+    if rank == 0 and world == 1 and not args.n and not args.no_study:
+        try:
+            accurate = accurate_bench(G, torch, dev, tuning=not args.no_tune)
+        except Exception as e:
+            accurate = {"error": repr(e)[:300]}
+    study = None
+    if rank == 0 and world == 1 and not args.n and not args.no_study:
+        try:
+            study = hss_fmm_study(G, torch, dev)
+        except Exception as e:
+            study = {"error": repr(e)[:300]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
@@ -809,7 +948,7 @@ def native_arm(args):
             "config": config_dict(w, prec_name, args.cache), "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clk.summary(), "e2e": e2e, "e2e_sync": e2e_sync, "gpu_launches": launches * args.steps,
             "autotune": tune, "accuracy": acc, "modes": modes, "dense_cublas": dense, "precision_workload": precision, "batching": batching,
-            "serving": serving,
+            "serving": serving, "hss_vs_fmm": study, "accurate_workload": accurate,
             "compress_seconds": round(compress_s, 2), "compression": compression, "generated_blocks": generated,
             "structure": {k: st[k] for k in ("depth", "mean_rank", "max_rank", "near_pairs", "far_pairs",
                                               "near_entries", "far_entries")},

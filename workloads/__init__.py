@@ -163,7 +163,15 @@ C3 = Workload("imq4d_n131072_r2048", 131072, 4, "uniform", IMQ, 0.5, 1e-2,
               leaf_size=256, max_rank=512, tau=1e-6, kappa=32, budget=0.03, r=2048,
               point_seed=5, w_seed=6)
 
-WORKLOADS = {w.name: w for w in (C1, C2, C3)}
+# A workload whose compression reaches an eps2 against the exact K W well
+# below 1e-4 at the throughput workload's N and r: the FP64 workload's 3-D
+# Gaussian (h 0.3 on the unit cube) at N = 65536, m 128, s 256 (ranks stay
+# below the cap), tau 1e-7, r = 512.
+ACCURATE = Workload("gaussian3d_n65536_r512", 65536, 3, "uniform", GAUSSIAN, 0.3, 1e-3,
+                    leaf_size=128, max_rank=256, tau=1e-7, kappa=32, budget=0.03, r=512,
+                    point_seed=1, w_seed=2)
+
+WORKLOADS = {w.name: w for w in (C1, C2, C3, ACCURATE)}
 
 
 def scaled(w: Workload, n: int, r: Optional[int] = None, **over) -> Workload:
@@ -224,3 +232,23 @@ def serving_requests(count: int = 2000, n_matrices: int = 8, seed: int = 9):
     rs = rng.integers(1, 513, size=count)
     gaps = rng.exponential(1.0, size=count)
     return mats, rs, gaps
+
+
+def hss_fmm_cases():
+    """Fixed-rank HSS (budget 0) against FMM (budget 3 % and 10 %) on two
+    synthetic kernels, r = 512 right-hand sides, tau = 0 (every node keeps
+    min(s, its columns) skeletons): the 6-D Gaussian recipe of the throughput
+    workload at N = 16384 (m 128) and the 3-D Gaussian of the FP64 workload
+    at N = 4096 (m 64).  Returns [(label, workload)]."""
+    out = []
+    base = [(scaled(C2, 16384, r=512, leaf_size=128, tau=0.0, name="gaussian6d_n16384"),
+             [(64, 0.0), (128, 0.0), (256, 0.0), (512, 0.0), (64, 0.03), (64, 0.10), (128, 0.03),
+              (128, 0.10), (256, 0.03)]),
+            (scaled(C1, 4096, r=512, leaf_size=64, tau=0.0, name="gaussian3d_n4096",
+                    entries_via_callback=False),
+             [(32, 0.0), (64, 0.0), (128, 0.0), (256, 0.0), (32, 0.03), (32, 0.10), (64, 0.03), (64, 0.10)])]
+    for w, cfgs in base:
+        for s, b in cfgs:
+            label = f"{w.name} {'HSS' if b == 0 else 'FMM'} s{s} budget {b:.0%}"
+            out.append((label, dataclasses.replace(w, max_rank=s, budget=b)))
+    return out
