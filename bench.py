@@ -865,16 +865,16 @@ def native_arm(args):
                 # SM count, 128 FP32 lanes and 16 SFU lanes per SM, and the
                 # SM clock sampled during the main run
                 sgen = G.stats(hg)
-                entries = sgen["near_entries"] + sgen["far_entries"]
+                n_entries = sgen["near_entries"] + sgen["far_entries"]
                 mhz = clk.summary().get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
-                alu_ops = entries * (3 * w.dim + 4)
+                alu_ops = n_entries * (3 * w.dim + 4)
                 alu_peak = SMS * FP32_LANES * mhz * 1e6
                 sfu_peak = SMS * 16 * mhz * 1e6
                 ent["generator_roofline"] = {
-                    "bound": "alu", "entries_per_eval": entries, "ops_per_entry": 3 * w.dim + 4,
+                    "bound": "alu", "entries_per_eval": n_entries, "ops_per_entry": 3 * w.dim + 4,
                     "achieved_gops": alu_ops / (gms / 1e3) / 1e9, "peak_gops": alu_peak / 1e9,
                     "frac": alu_ops / (gms / 1e3) / alu_peak,
-                    "sfu_frac": entries / (gms / 1e3) / sfu_peak,
+                    "sfu_frac": n_entries / (gms / 1e3) / sfu_peak,
                     "alu_bound_ms": 1e3 * alu_ops / alu_peak,
                     "note": (f"derived peak: {SMS} SMs x {FP32_LANES} FP32 lanes x {mhz:.0f} MHz (one op per lane "
                              f"per clock); SFU {SMS} x 16 lanes; entries counted once (the kernel generates each "

@@ -476,22 +476,29 @@ __device__ __forceinline__ float ex2_approx(float x) {
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+// The segment's generator constants, read once per job.
+struct GenConst {
+    const float4* tab;  // point table
+    float scale;        // Gaussian: -inv log2(e); IMQ: inv
+    float shift;
+    int dim;
+};
 // The items of one generated stage that warp gw owns: item i = (block rb of
 // 32 rows, 16-byte column group g), i = gw, gw + kGenWarps, ...; lane = row
-// rb * 32 + lane.  DP: floats per point (compile time).  Entries:
-// d2 = max(|x|^2 + |y|^2 - 2 x.y, 0) (exactly 0 for the same index);
-// Gaussian exp(-d2 inv) = 2^(d2 * (-inv log2 e)); IMQ 1 / sqrt(1 + d2 inv);
-// plus the shift on the same index (K_ii).  Written in the MMA layout.
-template <int MODE, int DP>
-__device__ __forceinline__ void gen_stage(GenRow<DP>& R, const GenJob& jb, const TcSeg& sg, const float* cpts,
+// rb * 32 + lane.  DP: floats per point, GAUSS: the kernel (compile time).
+// Entries: d2 = max(|x|^2 + |y|^2 - 2 x.y, 0) (exactly 0 for the same
+// index); Gaussian exp(-d2 inv) = 2^(d2 * (-inv log2 e)); IMQ
+// 1 / sqrt(1 + d2 inv); plus the shift on the same index (K_ii).  Written
+// in the MMA layout.
+template <int MODE, int DP, bool GAUSS>
+__device__ __forceinline__ void gen_stage(GenRow<DP>& R, const GenJob& jb, const GenConst& gc, const float* cpts,
                                           uint8_t* bh, uint8_t* bl, int gw, int lane) {
     constexpr bool kSplit = MODE == TC_BF16X3;
     constexpr int kPer = MODE == TC_TF32 ? 4 : 8;         // columns per 16-byte group
     constexpr int kGroups = 4 * (kSplit ? 1 : 2);         // 16-byte column groups per stage
     const int nrb = (jb.n_pad + 31) / 32;
-    const bool gauss = sg.gen_kind == GOFMM_GEN_GAUSSIAN;
-    const float scale = gauss ? -sg.gen_inv * 1.4426950408889634f : sg.gen_inv;  // log2(e)
-    const float4* tab = reinterpret_cast<const float4*>(sg.pts);
+    const float scale = gc.scale;
+    const float4* tab = gc.tab;
     for (int item = gw; item < nrb * kGroups; item += kGenWarps) {
         const int rb = item % nrb, g = item / nrb;
         const int n = rb * 32 + lane;
@@ -509,8 +516,8 @@ __device__ __forceinline__ void gen_stage(GenRow<DP>& R, const GenJob& jb, const
             R.n = 0.f;
 #pragma unroll
             for (int d = 0; d < DP; ++d) {
-                if (d == sg.dim) R.n = x[d];
-                R.x[d] = d == sg.dim ? 1.f : -2.f * x[d];
+                if (d == gc.dim) R.n = x[d];
+                R.x[d] = d == gc.dim ? 1.f : -2.f * x[d];
             }
             R.rows = jb.rows;
             R.seg = jb.seg;
@@ -522,22 +529,30 @@ __device__ __forceinline__ void gen_stage(GenRow<DP>& R, const GenJob& jb, const
         const int64_t dd = jb.rows + n - (jb.cols + k0);
         const int de = dd >= 0 && dd < kPer ? int(dd) : -1;
         const int kv = n < jb.m ? jb.kvalid - k0 : 0;  // valid columns of this group (<= 0: none)
+        // the kPer dot products advance together (independent FMA chains);
+        // column points are read by the whole warp at one address
+        const float4* cp = reinterpret_cast<const float4*>(cpts + k0 * DP);
         float v[kPer];
 #pragma unroll
-        for (int e = 0; e < kPer; ++e) {
-            const float4* cp = reinterpret_cast<const float4*>(cpts + (k0 + e) * DP);
-            float d2 = R.n;
+        for (int e = 0; e < kPer; ++e) v[e] = R.n;
 #pragma unroll
-            for (int q4 = 0; q4 < DP / 4; ++q4) {
-                const float4 c = cp[q4];  // the same address for the whole warp
-                d2 = fmaf(R.x[4 * q4], c.x, d2);
-                d2 = fmaf(R.x[4 * q4 + 1], c.y, d2);
-                d2 = fmaf(R.x[4 * q4 + 2], c.z, d2);
-                d2 = fmaf(R.x[4 * q4 + 3], c.w, d2);
+        for (int q4 = 0; q4 < DP / 4; ++q4) {
+#pragma unroll
+            for (int e = 0; e < kPer; ++e) {
+                const float4 c = cp[e * (DP / 4) + q4];
+                v[e] = fmaf(R.x[4 * q4], c.x, v[e]);
+                v[e] = fmaf(R.x[4 * q4 + 1], c.y, v[e]);
+                v[e] = fmaf(R.x[4 * q4 + 2], c.z, v[e]);
+                v[e] = fmaf(R.x[4 * q4 + 3], c.w, v[e]);
             }
-            d2 = e == de ? 0.f : fmaxf(d2, 0.f);
-            float y = gauss ? ex2_approx(d2 * scale) : rsqrtf(fmaf(d2, scale, 1.f));
-            if (e == de) y += sg.gen_shift;
+        }
+#pragma unroll
+        for (int e = 0; e < kPer; ++e) {
+            const float d2 = e == de ? 0.f : fmaxf(v[e], 0.f);
+            float y;
+            if constexpr (GAUSS) y = ex2_approx(d2 * scale);
+            else y = rsqrtf(fmaf(d2, scale, 1.f));
+            if (e == de) y += gc.shift;
             v[e] = e < kv ? y : 0.f;
         }
         // group g of the stage: K-half g / 4, 16-byte group g % 4 of it
@@ -594,7 +609,15 @@ __device__ __noinline__ int gen_loop(const TcParams& p, const GenJob* jobs, cons
         if (sg.dpad != DP) return sg.dpad;
         uint8_t* bh = base + jb.stage * C::kStageBytes + 2 * C::kAUnit;
         uint8_t* bl = bh + C::kPart;  // split BF16x3: the lo copy of the stage
-        gen_stage<MODE, DP>(R, jb, sg, colring + j * (C::kColSlot / 4), bh, bl, gw, lane);
+        const bool gauss = sg.gen_kind == GOFMM_GEN_GAUSSIAN;
+        GenConst gc;
+        gc.tab = reinterpret_cast<const float4*>(sg.pts);
+        gc.scale = gauss ? -sg.gen_inv * 1.4426950408889634f : sg.gen_inv;  // log2(e)
+        gc.shift = sg.gen_shift;
+        gc.dim = sg.dim;
+        const float* cpts = colring + j * (C::kColSlot / 4);
+        if (gauss) gen_stage<MODE, DP, true>(R, jb, gc, cpts, bh, bl, gw, lane);
+        else gen_stage<MODE, DP, false>(R, jb, gc, cpts, bh, bl, gw, lane);
         // generic writes -> visible to the MMAs (async proxy); this warp is
         // done with the job's column points
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
