@@ -518,7 +518,7 @@ def hss_fmm_study(G, torch, dev, steps=5):
 def accurate_bench(G, torch, dev, steps=10, tuning=True):
     """The evaluation at a configuration whose compression error is small:
     workloads.ACCURATE (3-D Gaussian, N = 65536, r = 512, ranks below the
-    cap, tau 1e-7).  Split BF16x3 (autotuned) and FP64 timed; eps2 of each
+    cap, tau 1e-9).  Split BF16x3 (autotuned) and FP64 timed; eps2 of each
     against the exact K W on 100 seeded rows (FP64, from the workload's own
     entry routine) and of BF16x3 against the FP64 evaluation (the precision
     error; the FP64 path matches the oracle to 1e-12 in the tests)."""
