@@ -259,7 +259,7 @@ def whole_job_value(n, r, world, ms_per_rank, reduce_max):
 
 # -------------------------------------------------------- batching/serving --
 SCHED_NAMES = ["fused", "staged", "pair", "hybrid"]  # GOFMM_SCHED_*
-ORDER_NAMES = ["critical", "local", "schedule"]       # GOFMM_ORDER_*
+ORDER_NAMES = ["critical", "local", "schedule", "ready"]  # GOFMM_ORDER_*
 
 
 def compress_many(G, works, device):

@@ -85,6 +85,11 @@ extern "C" {
                                   simulated on the host (the earliest task to
                                   be ready first, critical path among those
                                   ready); staged: heap order                 */
+#define GOFMM_ORDER_READY 3    /* fused: the upward pass and S2S in the
+                                  locality order, the downward pushes and the
+                                  leaves taken from a queue of tiles whose
+                                  inputs are complete (a batch: the locality
+                                  order); staged: heap order                 */
 
 /*
  * Entry callback: fill out[i*nJ + j] = K(I[i], J[j]) for 0 <= i < nI,

@@ -166,6 +166,70 @@ __device__ __forceinline__ bool wait_counter(const int* ctr, int e, int* err) {
         __nanosleep(64);
     }
 }
+__device__ __forceinline__ int ld_acquire_i32(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_i32(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Ready queue (TcReady): the tile written into a claimed slot, after a
+// bounded wait for its writer; -1 on timeout or a recorded error.
+__device__ __noinline__ int ready_entry(const TcParams& p, int slot) {
+    const int* e = p.ready.queue + 2 + slot;
+    const long long t0 = clock64();
+    for (uint32_t it = 1;; ++it) {
+        const int v = ld_acquire_i32(e);
+        if (v >= 0) return v;
+        if (it % 16 == 0) {
+            if (*reinterpret_cast<volatile int*>(p.err) != 0) return -1;
+            if (clock64() - t0 > kSpinLimit) {
+                atomicCAS(p.err, 0, kErrDependency);
+                return -1;
+            }
+        }
+        __nanosleep(64);
+    }
+}
+// Next tile of a ready-queue launch: a queued tile whose inputs are
+// complete, else the next tile of the list, else (the list exhausted) the
+// next queue slot, waited for.  -1: no tile left, or an error.  No CTA takes
+// a queued slot it has to wait for while the list still has tiles, and
+// every queued tile is written into exactly one slot, so a waiting CTA is
+// always served.
+__device__ __noinline__ int ready_claim(const TcParams& p, bool& list_left) {
+    int* q = p.ready.queue;  // q[0]: slots reserved by writers, q[1]: slots claimed
+    for (;;) {
+        const int head = *reinterpret_cast<volatile int*>(q + 1);
+        const int tail = ld_acquire_i32(q);
+        if (head < tail) {
+            if (atomicCAS(q + 1, head, head + 1) == head) return ready_entry(p, head);
+            continue;
+        }
+        if (list_left) {
+            const int s = atomicAdd(p.tile_next, 1);
+            if (s < p.ready.n_static) return s;
+            list_left = false;
+            continue;
+        }
+        const int h = atomicAdd(q + 1, 1);
+        return h < p.ready.n ? ready_entry(p, h) : -1;
+    }
+}
+// The arrival that completed counter pair `pair` (counter * r-tiles + r-tile):
+// every queued tile waiting on it loses one pending count; those that reach
+// zero are appended to the queue.
+__device__ __noinline__ void ready_release(const TcParams& p, int pair) {
+    __threadfence();  // the earlier arrivals on this counter happen before the entries written below
+    for (int i = p.ready.cons_off[pair]; i < p.ready.cons_off[pair + 1]; ++i) {
+        const int u = p.ready.cons[i];
+        if (atomicSub(p.ready.pending + u, 1) == 1) {
+            const int slot = atomicAdd(p.ready.queue, 1);
+            st_release_i32(p.ready.queue + 2 + slot, p.ready.n_static + u);
+        }
+    }
+}
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                  "l"(src), "r"(bytes), "r"(bar)
@@ -711,11 +775,18 @@ __global__ void __launch_bounds__(GEN ? kGenThreads : 192, 1) tc_gemm_kernel(con
             int stage = 0, issued = 0, gseq = 0;
             uint32_t phase = 0;
             bool ok = true;
+            bool list_left = true;  // ready queue: the list still has tiles
             for (int i = 0, t = blockIdx.x; ok; ++i) {
                 if (dyn) {
-                    // take the next tile in priority order and hand its id on
+                    // take the next tile in priority order (or from the ready
+                    // queue) and hand its id on
                     if (!mbar_wait(idempty_bar(i & 1), uint32_t(((i >> 1) & 1) ^ 1), p.err, kErrProducer)) break;
-                    t = atomicAdd(p.tile_next, 1);
+                    if (p.ready.queue) {
+                        const int c = ready_claim(p, list_left);
+                        t = c < 0 ? ntiles : c;
+                    } else {
+                        t = atomicAdd(p.tile_next, 1);
+                    }
                     tid_slot[i & 1] = t < ntiles ? t : -1;
                     mbar_arrive(idfull_bar(i & 1));
                 } else if (i > 0) {
@@ -991,10 +1062,13 @@ __global__ void __launch_bounds__(GEN ? kGenThreads : 192, 1) tc_gemm_kernel(con
                     __syncwarp();
                     if (lane == 0) {
                         __threadfence();
-                        for (int w = 0; w < nw; ++w) {
-                            if (s0 >= 0) atomicAdd(sg.counters + int64_t(s0) * sg.dep_nrt + rt + w, 1);
-                            if (s1 >= 0) atomicAdd(sg.counters + int64_t(s1) * sg.dep_nrt + rt + w, 1);
-                        }
+                        for (int w = 0; w < nw; ++w)
+                            for (int c : {s0, s1}) {
+                                if (c < 0) continue;
+                                const int old = atomicAdd(sg.counters + int64_t(c) * sg.dep_nrt + rt + w, 1);
+                                // the final arrival releases the queued tiles waiting on it
+                                if (p.ready.queue && old + 1 == p.ready.req[c]) ready_release(p, c * sg.dep_nrt + rt + w);
+                            }
                     }
                 }
             }
@@ -1462,6 +1536,7 @@ static void build_fused(const Structure& st, TcPrec& T, TcFused& F, unsigned sta
     F.piece = T.piece;
     F.tasks.clear();
     F.slabs.clear();
+    F.task_stage.clear();
     for (const TcLaunch& l : T.launches) {
         if (!((stage_mask >> l.stage) & 1u)) continue;
         for (size_t k = 0; k < l.tasks.size(); ++k) {
@@ -1545,6 +1620,7 @@ static void build_fused(const Structure& st, TcPrec& T, TcFused& F, unsigned sta
                 for (int64_t x = h + 1; x > 1; x >>= 1) ++lev;
                 group.emplace_back(l.stage, lev);
                 node_of.push_back(h);
+                F.task_stage.push_back(int8_t(l.stage));
             }
             F.tasks.push_back(t);
         }
@@ -1659,9 +1735,83 @@ static void build_fused(const Structure& st, TcPrec& T, TcFused& F, unsigned sta
     F.d_tasks = dupload(F.tasks);
     F.d_slabs = dupload(F.slabs);
     F.d_dep_off = dupload(dep_off);
+    F.dep_off_host = dep_off;
     F.deps_host = deps;
     F.d_deps = dupload(deps.empty() ? std::vector<int32_t>{0, 0} : deps);
     F.d_sig = dupload(sig);
+}
+
+// Ready-queue form of the fused launch for n_rtiles r-tiles: the upward
+// pass and S2S tiles in the locality order (claimed in list order), then the
+// push and leaf tiles, which enter the launch's queue once complete: for
+// each of them the (counter, r-tile) pairs it waits for (its task's
+// dependencies and its slabs' operand counters over its r-tiles), inverted
+// into per-pair consumer lists; those with none start in the queue.
+static TcFused::Ready& ready_tiles(TcFused& F, int n_rtiles) {
+    auto it = F.ready.find(n_rtiles);
+    if (it != F.ready.end()) return it->second;
+    std::vector<TcTile> tiles, queued;
+    std::vector<int32_t> qtask;
+    for (int32_t k : F.order_local) {
+        const bool q = F.task_stage[size_t(k)] >= 3;
+        const size_t before = q ? queued.size() : tiles.size();
+        task_tiles(q ? queued : tiles, 0, k, F.tasks[size_t(k)], n_rtiles, F.piece);
+        if (q)
+            for (size_t i = before; i < queued.size(); ++i) qtask.push_back(k);
+    }
+    TcFused::Ready R;
+    R.n_static = int(tiles.size());
+    R.n = int(queued.size());
+    const size_t npairs = size_t(F.ncounters) * size_t(n_rtiles);
+    std::vector<int32_t> req(size_t(F.ncounters), 0), pending(size_t(R.n), 0);
+    std::vector<std::vector<int32_t>> cons(npairs);
+    auto need = [&](int32_t c, int32_t e) {
+        if (req[size_t(c)] != 0 && req[size_t(c)] != e) fail(GOFMM_ERR_ARG, "inconsistent counter target in the fused plan");
+        req[size_t(c)] = e;
+    };
+    for (int i = 0; i < R.n; ++i) {
+        const TcTile& t = queued[size_t(i)];
+        const int32_t k = qtask[size_t(i)];
+        std::vector<std::pair<int32_t, int32_t>> d;  // (counter, arrivals)
+        for (int32_t x = F.dep_off_host[size_t(k)]; x < F.dep_off_host[size_t(k) + 1]; ++x)
+            d.emplace_back(F.deps_host[size_t(2 * x)], F.deps_host[size_t(2 * x + 1)]);
+        const TcTask& tk = F.tasks[size_t(k)];
+        for (int si = tk.slab0; si < tk.slab1; ++si) {
+            const TcSlab& sl = F.slabs[size_t(si)];
+            if (sl.dep_c0 >= 0) d.emplace_back(sl.dep_c0, sl.dep_n0);
+            if (sl.dep_c1 >= 0) d.emplace_back(sl.dep_c1, sl.dep_n1);
+        }
+        std::sort(d.begin(), d.end());
+        d.erase(std::unique(d.begin(), d.end()), d.end());
+        for (const auto& x : d) {
+            need(x.first, x.second);
+            for (int w = 0; w < (t.pad == 2 ? 2 : 1); ++w) {
+                cons[size_t(x.first) * size_t(n_rtiles) + size_t(t.rt + w)].push_back(i);
+                ++pending[size_t(i)];
+            }
+        }
+    }
+    std::vector<int32_t> off(npairs + 1, 0), flat;
+    for (size_t pidx = 0; pidx < npairs; ++pidx) {
+        off[pidx + 1] = off[pidx] + int32_t(cons[pidx].size());
+        flat.insert(flat.end(), cons[pidx].begin(), cons[pidx].end());
+    }
+    std::vector<int> q0(size_t(2 + R.n), -1);
+    int ready0 = 0;
+    for (int i = 0; i < R.n; ++i)
+        if (pending[size_t(i)] == 0) q0[size_t(2 + ready0++)] = R.n_static + i;
+    q0[0] = ready0;  // tail
+    q0[1] = 0;       // head
+    tiles.insert(tiles.end(), queued.begin(), queued.end());
+    R.tiles = dupload(tiles);
+    R.queue0 = dupload(q0);
+    R.queue = dalloc<int>(q0.size());
+    R.pending0 = dupload(pending.empty() ? std::vector<int32_t>{0} : pending);
+    R.pending = dalloc<int>(std::max<size_t>(pending.size(), 1));
+    R.cons_off = dupload(off);
+    R.cons = dupload(flat.empty() ? std::vector<int32_t>{0} : flat);
+    R.req = dupload(req);
+    return F.ready.emplace(n_rtiles, R).first->second;
 }
 
 // Tile list of the fused launch: tasks in the given order (GOFMM_ORDER_*),
@@ -1981,7 +2131,10 @@ void tc_prepare(Handle& H, DeviceState& D, int64_t r_max, int precision) {
             F->d_counters = dalloc<int>(size_t(F->ncounters) * size_t(r_pad / 128) + 1);  // + tile counter
             F->counters_nrt = int(r_pad / 128);
         }
-        for (int nrt = 1; nrt <= int(r_pad / 128); ++nrt) fused_tiles(*F, nrt, H.tc_order[T->mode]);
+        for (int nrt = 1; nrt <= int(r_pad / 128); ++nrt) {
+            fused_tiles(*F, nrt, H.tc_order[T->mode]);
+            if (H.tc_order[T->mode] == GOFMM_ORDER_READY && !F->tasks.empty()) ready_tiles(*F, nrt);
+        }
     }
     if (T->r_cap < r_pad) {
         for (int i = 0; i < 3; ++i) {
@@ -2188,12 +2341,23 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
         if (F.tasks.empty()) return;
         if (F.counters_nrt < n_rtiles) fail(GOFMM_ERR_ARG, "fused plan not prepared for this r");
         CUDA_OK(cudaMemsetAsync(F.d_counters, 0, (size_t(F.ncounters) * n_rtiles + 1) * sizeof(int), s));
-        const auto tl = fused_tiles(F, n_rtiles, H.tc_order[T.mode]);
         TcParams q{};
         q.nsegs = 1;
         q.err = T.d_err;
-        q.tiles = tl.first;
-        q.ntiles = tl.second;
+        if (H.tc_order[T.mode] == GOFMM_ORDER_READY) {
+            // list part and queued part; the queue and the pending counts
+            // start from their initial copies
+            TcFused::Ready& R = ready_tiles(F, n_rtiles);
+            CUDA_OK(cudaMemcpyAsync(R.queue, R.queue0, size_t(2 + R.n) * sizeof(int), cudaMemcpyDeviceToDevice, s));
+            if (R.n) CUDA_OK(cudaMemcpyAsync(R.pending, R.pending0, size_t(R.n) * sizeof(int), cudaMemcpyDeviceToDevice, s));
+            q.tiles = R.tiles;
+            q.ntiles = R.n_static + R.n;
+            q.ready = TcReady{R.queue, R.pending, R.cons_off, R.cons, R.req, R.n_static, R.n};
+        } else {
+            const auto tl = fused_tiles(F, n_rtiles, H.tc_order[T.mode]);
+            q.tiles = tl.first;
+            q.ntiles = tl.second;
+        }
         TcSeg g = make_seg(T, T.launches.front(), T.rt_hi, T.rt_lo, U, ldu, D.d_idx, r);
         g.tasks = F.d_tasks;
         g.slabs = F.d_slabs;
@@ -2336,6 +2500,11 @@ static void free_prec(TcPrec*& T) {
             dfree(F->d_slabs_stall);
             dfree(F->d_counters);
             for (auto& kv : F->tiles) dfree(kv.second.first);
+            for (auto& kv : F->ready) {
+                TcFused::Ready& R = kv.second;
+                dfree(R.tiles); dfree(R.queue); dfree(R.queue0); dfree(R.pending); dfree(R.pending0);
+                dfree(R.cons_off); dfree(R.cons); dfree(R.req);
+            }
         }
         for (int i = 0; i < 3; ++i) { dfree(T->rt_hi[i]); dfree(T->rt_lo[i]); }
         if (T->h_err) cudaFreeHost(T->h_err);

@@ -112,6 +112,26 @@ constexpr int kMaxSegs = 64;  // segments per launch (kernel parameters, by valu
 constexpr int kClaimSlots = 64;  // per-stage launches of one evaluation that claim tiles dynamically
 
 
+// Ready queue of a dependency-driven launch of one evaluation (order
+// GOFMM_ORDER_READY).  The tiles tiles[0 .. n_static) are claimed in list
+// order; the tiles tiles[n_static .. n_static + n) (the downward pushes and
+// the leaves) only through a FIFO that holds a tile once every counter it
+// waits for is complete: the epilogue that brings a counter to its final
+// arrival count req[c] takes one from the pending count of each queued tile
+// waiting on it (cons) and appends the tiles that reach zero.  A producer
+// takes a ready tile first, else the next tile of the list, else (list
+// exhausted) waits for the next queue slot.  All ints, reset before every
+// launch: queue = {tail (slots reserved), head (slots claimed), n entries,
+// -1 until written}, pending = the initial counts.
+struct TcReady {
+    int* queue;
+    int* pending;
+    const int32_t* cons_off;  // [ncounters * r-tiles + 1]
+    const int32_t* cons;      // queued-tile numbers (0 .. n) waiting on (counter, r-tile)
+    const int32_t* req;       // [ncounters]: arrivals that complete a counter
+    int n_static, n;
+};
+
 struct TcParams {
     const TcTile* tiles;  // merged tile list; nullptr: every segment brings its own (TcSeg::tiles)
     int ntiles;
@@ -122,6 +142,7 @@ struct TcParams {
     // dependency arrays, which needs every CTA resident: a cooperative
     // launch); nullptr: static round-robin split, no waits
     int* tile_next;
+    TcReady ready;  // queue == nullptr: no ready queue
     TcSeg segs[kMaxSegs];
 };
 
@@ -159,6 +180,25 @@ struct TcFused {
     int* d_counters = nullptr;  // ncounters x r-tiles of the largest r prepared (+ tile counter)
     int counters_nrt = 0;
     std::vector<int32_t> deps_host;
+    // host copies for the ready-queue tile lists: task-level dependency
+    // offsets, each task's stage, and the (counter, count) pairs of its slabs
+    std::vector<int32_t> dep_off_host;
+    std::vector<int8_t> task_stage;
+    // ready-queue form per r-tile count: tiles (list part, then queued part)
+    // and the device arrays of TcReady (queue and pending reset per launch
+    // from their initial copies)
+    struct Ready {
+        TcTile* tiles = nullptr;
+        int n_static = 0, n = 0;
+        int* queue = nullptr;
+        int* queue0 = nullptr;
+        int* pending = nullptr;
+        int* pending0 = nullptr;
+        int32_t* cons_off = nullptr;
+        int32_t* cons = nullptr;
+        int32_t* req = nullptr;
+    };
+    std::map<int, Ready> ready;
     int32_t* d_deps_stall = nullptr;  // diagnostic copies with one unreachable arrival count
     TcSlab* d_slabs_stall = nullptr;
     bool stall_next = false;
@@ -206,7 +246,11 @@ void launch_gemm_mode(int mode, int piece, const TcParams& p, int num_sms, cudaS
 void launch_gemm_coop_mode(int mode, int piece, const TcParams& p, int num_sms, cudaStream_t s, bool gen);
 // the fused plan's task order for a GOFMM_ORDER_* value
 inline const std::vector<int32_t>& fused_order(const TcFused& F, int order) {
-    return order == GOFMM_ORDER_LOCAL ? F.order_local : order == GOFMM_ORDER_SCHEDULE ? F.order_sched : F.order;
+    // (the ready-queue form takes its list part from the locality order; a
+    // batch, which has no ready queue, runs it as the locality order)
+    return order == GOFMM_ORDER_LOCAL || order == GOFMM_ORDER_READY ? F.order_local
+           : order == GOFMM_ORDER_SCHEDULE                        ? F.order_sched
+                                                                  : F.order;
 }
 // device tile list of one launch alone for n_rtiles r-tiles (cached in the launch)
 std::pair<TcTile*, int> launch_tiles(TcLaunch& l, int n_rtiles, int order, bool pair = false);
