@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--no-study", action="store_true", help="skip the HSS-vs-FMM accuracy/time study")
     ap.add_argument("--n", type=int, default=0,
                     help="profiling only: the same recipe at another N (not a bench line)")
+    ap.add_argument("--budget", type=float, default=0.0,
+                    help="profiling only, with --n: another near-field budget (e.g. 0.06 at N = 32768 keeps "
+                         "the 15 near leaves per leaf of N = 65536 at 3 %%)")
     return ap.parse_args()
 
 
@@ -259,7 +262,7 @@ def whole_job_value(n, r, world, ms_per_rank, reduce_max):
 
 # -------------------------------------------------------- batching/serving --
 SCHED_NAMES = ["fused", "staged", "pair", "hybrid"]  # GOFMM_SCHED_*
-ORDER_NAMES = ["critical", "local", "schedule", "ready"]  # GOFMM_ORDER_*
+ORDER_NAMES = ["critical", "local", "schedule", "ready", "levels"]  # GOFMM_ORDER_*
 
 
 def compress_many(G, works, device):
@@ -579,7 +582,7 @@ def native_arm(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    w = WORKLOAD if not args.n else wl.scaled(WORKLOAD, args.n)
+    w = WORKLOAD if not args.n else wl.scaled(WORKLOAD, args.n, **({"budget": args.budget} if args.budget else {}))
     prec_name = args.precision
     # host-only compression of the batching and serving matrices, overlapped
     # with the throughput measurement below

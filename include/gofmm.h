@@ -90,6 +90,10 @@ extern "C" {
                                   leaves taken from a queue of tiles whose
                                   inputs are complete (a batch: the locality
                                   order); staged: heap order                 */
+#define GOFMM_ORDER_LEVELS 4   /* fused: the upward pass, then S2S level by
+                                  level from the top, the pushes into a level
+                                  after the S2S of the next level, then the
+                                  leaves; staged: heap order                 */
 
 /*
  * Entry callback: fill out[i*nJ + j] = K(I[i], J[j]) for 0 <= i < nI,

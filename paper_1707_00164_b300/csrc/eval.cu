@@ -875,7 +875,7 @@ void device_set_tc_config(Handle& H, int precision, int piece, int schedule, int
     if (piece != 128 && piece != 256) fail(GOFMM_ERR_ARG, "piece must be 128 or 256");
     if (schedule < GOFMM_SCHED_FUSED || schedule > GOFMM_SCHED_HYBRID) fail(GOFMM_ERR_ARG, "unknown schedule");
     if (order != GOFMM_ORDER_CRITICAL && order != GOFMM_ORDER_LOCAL && order != GOFMM_ORDER_SCHEDULE &&
-        order != GOFMM_ORDER_READY)
+        order != GOFMM_ORDER_READY && order != GOFMM_ORDER_LEVELS)
         fail(GOFMM_ERR_ARG, "unknown order");
     const int mode = mode_of(precision);
     if (piece != H.tc_piece[mode] && H.inflight > 0)

@@ -1732,6 +1732,53 @@ static void build_fused(const Structure& st, TcPrec& T, TcFused& F, unsigned sta
             }
         }
     }
+    // Level order: the upward pass (as in the locality order), then the S2S
+    // tasks level by level from the top (heap order inside a level), with the
+    // pushes into level l placed after the S2S tasks of level l + 1: when a
+    // push is claimed, its node's S2S and its parent's push were claimed a
+    // whole level of S2S work earlier, so the downward pass runs beside the
+    // far field instead of after it; then the pushes into the deepest level
+    // and the leaves.  Topological (checked below).
+    {
+        int L = 0;
+        for (size_t t = 0; t < nt; ++t) L = std::max(L, group[t].second);
+        std::vector<std::vector<int32_t>> s2s(size_t(L) + 1), push(size_t(L) + 1);
+        std::vector<int32_t> up, leaves;
+        for (int32_t t : F.order_local) {
+            const int stg = group[size_t(t)].first, lev = group[size_t(t)].second;
+            if (stg == 1) up.push_back(t);
+            else if (stg == 2) s2s[size_t(lev)].push_back(t);
+            else if (stg == 3) push[size_t(lev)].push_back(t);
+            else leaves.push_back(t);
+        }
+        auto heap = [&](std::vector<int32_t>& v) {
+            std::stable_sort(v.begin(), v.end(),
+                             [&](int32_t a, int32_t b) { return node_of[size_t(a)] < node_of[size_t(b)]; });
+        };
+        F.order_levels = up;
+        for (int l = 0; l <= L; ++l) {
+            heap(s2s[size_t(l)]);
+            F.order_levels.insert(F.order_levels.end(), s2s[size_t(l)].begin(), s2s[size_t(l)].end());
+            if (l >= 1) {
+                heap(push[size_t(l - 1)]);
+                F.order_levels.insert(F.order_levels.end(), push[size_t(l - 1)].begin(), push[size_t(l - 1)].end());
+            }
+        }
+        heap(push[size_t(L)]);
+        F.order_levels.insert(F.order_levels.end(), push[size_t(L)].begin(), push[size_t(L)].end());
+        F.order_levels.insert(F.order_levels.end(), leaves.begin(), leaves.end());
+        if (F.order_levels.size() != nt) fail(GOFMM_ERR_ARG, "level order does not cover the fused plan");
+        std::vector<int64_t> pos(nt);
+        for (size_t i = 0; i < nt; ++i) pos[size_t(F.order_levels[i])] = int64_t(i);
+        std::vector<std::vector<int32_t>> prod(size_t(F.ncounters));
+        for (size_t t = 0; t < nt; ++t)
+            for (int i = 0; i < 2; ++i)
+                if (sig[2 * t + i] >= 0) prod[size_t(sig[2 * t + i])].push_back(int32_t(t));
+        for (size_t t = 0; t < nt; ++t)
+            for (int32_t d = all_off[t]; d < all_off[t + 1]; ++d)
+                for (int32_t u : prod[size_t(all_deps[2 * d])])
+                    if (pos[size_t(u)] > pos[t]) fail(GOFMM_ERR_ARG, "level order is not topological");
+    }
     F.d_tasks = dupload(F.tasks);
     F.d_slabs = dupload(F.slabs);
     F.d_dep_off = dupload(dep_off);
@@ -1817,7 +1864,7 @@ static TcFused::Ready& ready_tiles(TcFused& F, int n_rtiles) {
 // Tile list of the fused launch: tasks in the given order (GOFMM_ORDER_*),
 // the r-tiles of a task adjacent.
 static std::pair<TcTile*, int> fused_tiles(TcFused& F, int n_rtiles, int order) {
-    const int key = n_rtiles * 4 + order;
+    const int key = n_rtiles * 8 + order;  // GOFMM_ORDER_* < 8
     auto it = F.tiles.find(key);
     if (it != F.tiles.end()) return it->second;
     std::vector<TcTile> t;

@@ -170,6 +170,7 @@ struct TcFused {
     std::vector<int32_t> order;        // tasks in a topological, critical-path-first order
     std::vector<int32_t> order_local;  // topological; groups by critical path, heap order inside
     std::vector<int32_t> order_sched;  // a simulated list schedule's order (topological)
+    std::vector<int32_t> order_levels;  // S2S top-down, each push level one S2S level later (topological)
     int piece = 256;                   // task piece height of the plan
     TcTask* d_tasks = nullptr;
     TcSlab* d_slabs = nullptr;
@@ -250,6 +251,7 @@ inline const std::vector<int32_t>& fused_order(const TcFused& F, int order) {
     // batch, which has no ready queue, runs it as the locality order)
     return order == GOFMM_ORDER_LOCAL || order == GOFMM_ORDER_READY ? F.order_local
            : order == GOFMM_ORDER_SCHEDULE                        ? F.order_sched
+           : order == GOFMM_ORDER_LEVELS                          ? F.order_levels
                                                                   : F.order;
 }
 // device tile list of one launch alone for n_rtiles r-tiles (cached in the launch)

@@ -448,7 +448,7 @@ TuneResult autotune(Handle& H, int64_t r, int precision, const char* cache_path,
     // order never won); the single dependency-driven launch every order, the
     // hybrid the critical-path and locality orders
     const int cands[8][2] = {{GOFMM_SCHED_FUSED, GOFMM_ORDER_CRITICAL},  {GOFMM_SCHED_FUSED, GOFMM_ORDER_LOCAL},
-                             {GOFMM_SCHED_FUSED, GOFMM_ORDER_SCHEDULE},  {GOFMM_SCHED_FUSED, GOFMM_ORDER_READY},
+                             {GOFMM_SCHED_FUSED, GOFMM_ORDER_LEVELS},    {GOFMM_SCHED_FUSED, GOFMM_ORDER_READY},
                              {GOFMM_SCHED_STAGED, GOFMM_ORDER_LOCAL},    {GOFMM_SCHED_PAIR, GOFMM_ORDER_LOCAL},
                              {GOFMM_SCHED_HYBRID, GOFMM_ORDER_CRITICAL}, {GOFMM_SCHED_HYBRID, GOFMM_ORDER_LOCAL}};
     float best = 0.f;

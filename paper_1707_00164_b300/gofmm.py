@@ -28,7 +28,7 @@ PREC_FP64, PREC_FP32, PREC_TF32, PREC_BF16, PREC_BF16X3 = 0, 1, 2, 3, 4
 PRECISIONS = {"fp64": PREC_FP64, "fp32": PREC_FP32, "tf32": PREC_TF32, "bf16": PREC_BF16,
               "bf16x3": PREC_BF16X3}
 SCHED_FUSED, SCHED_STAGED, SCHED_PAIR, SCHED_HYBRID = 0, 1, 2, 3
-ORDER_CRITICAL, ORDER_LOCAL, ORDER_SCHEDULE, ORDER_READY = 0, 1, 2, 3
+ORDER_CRITICAL, ORDER_LOCAL, ORDER_SCHEDULE, ORDER_READY, ORDER_LEVELS = 0, 1, 2, 3, 4
 
 BLOCK_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(C.c_int64), C.c_int64,
                        C.POINTER(C.c_int64), C.c_int64, C.POINTER(C.c_double))

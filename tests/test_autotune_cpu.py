@@ -39,7 +39,9 @@ def test_config_defaults_and_validation():
     assert G.get_tc_config(h, G.PREC_BF16)["order"] == G.ORDER_SCHEDULE
     G.set_tc_config(h, G.PREC_BF16, 256, G.SCHED_FUSED, G.ORDER_READY)
     assert G.get_tc_config(h, G.PREC_BF16)["order"] == G.ORDER_READY
-    for args in [(G.PREC_BF16, 64, 0, 0), (G.PREC_BF16, 256, 4, 0), (G.PREC_BF16, 256, 0, 4),
+    G.set_tc_config(h, G.PREC_BF16, 256, G.SCHED_FUSED, G.ORDER_LEVELS)
+    assert G.get_tc_config(h, G.PREC_BF16)["order"] == G.ORDER_LEVELS
+    for args in [(G.PREC_BF16, 64, 0, 0), (G.PREC_BF16, 256, 4, 0), (G.PREC_BF16, 256, 0, 5),
                  (G.PREC_FP32, 256, 0, 0), (G.PREC_FP64, 128, 0, 0)]:
         with pytest.raises(G.GofmmError) as e:
             G.set_tc_config(h, *args)

@@ -25,7 +25,7 @@ PRECS = [G.PREC_TF32, G.PREC_BF16, G.PREC_BF16X3]
 NAMES = {G.PREC_TF32: "tf32", G.PREC_BF16: "bf16", G.PREC_BF16X3: "bf16x3"}
 TOL = {G.PREC_TF32: 5e-3, G.PREC_BF16: 2e-2, G.PREC_BF16X3: 1e-4}
 CONFIGS = [(p, s, o) for p in (256, 128) for s in (G.SCHED_FUSED, G.SCHED_STAGED, G.SCHED_PAIR, G.SCHED_HYBRID)
-           for o in (G.ORDER_CRITICAL, G.ORDER_LOCAL, G.ORDER_SCHEDULE, G.ORDER_READY)]
+           for o in (G.ORDER_CRITICAL, G.ORDER_LOCAL, G.ORDER_SCHEDULE, G.ORDER_READY, G.ORDER_LEVELS)]
 
 
 def run(h, Wt, prec):

@@ -75,7 +75,7 @@ def test_generated_blocks_every_configuration_bitwise_equal():
     out = []
     for piece in (256, 128):
         for sched in (G.SCHED_FUSED, G.SCHED_STAGED, G.SCHED_HYBRID):
-            for order in (G.ORDER_CRITICAL, G.ORDER_LOCAL, G.ORDER_SCHEDULE, G.ORDER_READY):
+            for order in (G.ORDER_CRITICAL, G.ORDER_LOCAL, G.ORDER_SCHEDULE, G.ORDER_READY, G.ORDER_LEVELS):
                 G.set_tc_config(h, prec, piece, sched, order)
                 out.append(run(h, W, prec))
     assert all(np.array_equal(o, out[0]) for o in out)
