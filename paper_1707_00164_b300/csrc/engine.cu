@@ -472,7 +472,7 @@ Batch* batch_create(Handle* const* hs, const int64_t* r, int count, int precisio
                     more = true;
                     const int32_t task = (*orders[k])[pos[k]++];
                     const BatchItem& it = B->items[bf.items[k]];
-                    task_tiles(tiles, int32_t(k), task, it.T->fused.tasks[size_t(task)], it.n_rtiles, it.T->piece);
+                    task_tiles(tiles, int32_t(k), task, it.T->fused.tasks[size_t(task)], it.n_rtiles);
                 }
             }
             bf.d_tiles = dupload(tiles);
@@ -504,7 +504,7 @@ Batch* batch_create(Handle* const* hs, const int64_t* r, int count, int precisio
                 bl.gen = bl.gen || B->items[i].T->gen;
                 for (size_t t = 0; t < l.tasks.size(); ++t) {
                     std::vector<TcTile> tt;
-                    task_tiles(tt, int32_t(k), int32_t(t), l.tasks[t], B->items[i].n_rtiles, B->items[i].T->piece);
+                    task_tiles(tt, int32_t(k), int32_t(t), l.tasks[t], B->items[i].n_rtiles);
                     for (const TcTile& x : tt)
                         tiles.emplace_back(int64_t(l.tasks[t].nchunks) * l.tasks[t].n_pad * x.pad + 1, x);
                 }

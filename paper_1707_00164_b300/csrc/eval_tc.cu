@@ -91,7 +91,7 @@ struct Cfg {
     static constexpr int kKc = MODE == TC_TF32 ? 32 : 64;  // columns per chunk
     static constexpr int kStageK = kKc / 2 * kSub;          // columns per stage
     static constexpr int kEs = MODE == TC_TF32 ? 4 : 2;
-    static constexpr int kTmemCols = 2 * NMAX;  // two accumulators
+    static constexpr int kTmemCols = 2 * kAccBufCols;  // two accumulator buffers
     static_assert(kStages >= 2, "at least a double-buffered stage ring");
     // epilogue staging tile (hi and lo) of the kernels without generator warps
     static constexpr int kEpiBytes = (kSplit ? 2 : 1) * kTileBytes;
@@ -347,10 +347,10 @@ __device__ __forceinline__ TcTile fetch_tile(const TcParams& p, int t) {
 // r-tiles a tile covers: rt alone, or rt and rt + 1 (two accumulators fed
 // from one block stage)
 __device__ __forceinline__ int tile_width(const TcTile& tt) { return tt.pad == 2 ? 2 : 1; }
-// TMEM accumulator buffers (NMAX columns each) a tile takes: one, or both
-// when it has two accumulators of more than NMAX / 2 columns (two narrower
-// ones share a buffer, at columns 0 and NMAX / 2)
-__device__ __forceinline__ int acc_buffers(int nw, int n_pad, int nmax) { return nw == 2 && 2 * n_pad > nmax ? 2 : 1; }
+// TMEM accumulator buffers (kAccBufCols columns each) a tile takes: one, or
+// both when it has two accumulators of more than kAccBufCols / 2 columns (two
+// narrower ones share a buffer, at columns 0 and kAccBufCols / 2)
+__device__ __forceinline__ int acc_buffers(int nw, int n_pad) { return nw == 2 && 2 * n_pad > kAccBufCols ? 2 : 1; }
 
 // Epilogue of one tile: the accumulator rows of this thread (one column j
 // of r) for the task's n_pad block rows, read from TMEM at taddr and written
@@ -928,15 +928,15 @@ __global__ void __launch_bounds__(GEN ? kGenThreads : 192, 1) tc_gemm_kernel(con
                 const TcTile tt = fetch_tile(p, t);
                 const TcTask tk = p.segs[tt.seg].tasks[tt.task];
                 const int nw = tile_width(tt);
-                const int nb = acc_buffers(nw, tk.n_pad, NMAX);
+                const int nb = acc_buffers(nw, tk.n_pad);
                 const int b0 = nb == 2 ? 0 : bnext;
                 if (nb == 1) bnext ^= 1;
                 for (int b = 0; b < nb && ok; ++b)
                     ok = mbar_wait(tempty_bar(b0 + b), ((fills >> (b0 + b)) & 1u) ^ 1u, p.err, kErrMma);
                 if (!ok) break;
                 tc_fence_after();
-                const uint32_t tacc = tmem + uint32_t(b0 * NMAX);  // r-tile rt + w: tacc + w * acc_step
-                const uint32_t acc_step = uint32_t(nb == 2 ? NMAX : NMAX / 2);
+                const uint32_t tacc = tmem + uint32_t(b0 * kAccBufCols);  // r-tile rt + w: tacc + w * acc_step
+                const uint32_t acc_step = uint32_t(nb == 2 ? kAccBufCols : kAccBufCols / 2);
                 const uint32_t idesc = make_idesc(MODE == TC_TF32 ? 2 : 1, tk.n_pad);
                 const uint32_t b_half = uint32_t(tk.n_pad) * 64u;
                 for (int q = 0; q < 2 * tk.nchunks / C::kSub; ++q) {
@@ -1014,10 +1014,10 @@ __global__ void __launch_bounds__(GEN ? kGenThreads : 192, 1) tc_gemm_kernel(con
             const TcTask tk = sg.tasks[tt.task];
             const int rt = tt.rt;
             const int nw = tile_width(tt);
-            const int nb = acc_buffers(nw, tk.n_pad, NMAX);
+            const int nb = acc_buffers(nw, tk.n_pad);
             const int b0 = nb == 2 ? 0 : bnext;
             if (nb == 1) bnext ^= 1;
-            const int acc_step = nb == 2 ? NMAX : NMAX / 2;
+            const int acc_step = nb == 2 ? kAccBufCols : kAccBufCols / 2;
             bool ok = true;
             for (int b = 0; b < nb && ok; ++b)
                 ok = mbar_wait(tfull_bar(b0 + b), (fills >> (b0 + b)) & 1u, p.err, kErrEpilogue);
@@ -1032,7 +1032,7 @@ __global__ void __launch_bounds__(GEN ? kGenThreads : 192, 1) tc_gemm_kernel(con
             // in-place S2N pushes touch valid elements alone.
             const bool staged = !GEN && tk.out_kind != OUT_U && !tk.accumulate;
             for (int w = 0; w < nw; ++w) {
-                const uint32_t taddr = tmem + uint32_t(b0 * NMAX + w * acc_step) + (uint32_t(q4 * 32) << 16);
+                const uint32_t taddr = tmem + uint32_t(b0 * kAccBufCols + w * acc_step) + (uint32_t(q4 * 32) << 16);
                 if (staged)
                     write_tile_staged<MODE>(sg, tk, rt + w, row, taddr, stg, store_thread);
                 else
@@ -1802,7 +1802,7 @@ static TcFused::Ready& ready_tiles(TcFused& F, int n_rtiles) {
     for (int32_t k : F.order_local) {
         const bool q = F.task_stage[size_t(k)] >= 3;
         const size_t before = q ? queued.size() : tiles.size();
-        task_tiles(q ? queued : tiles, 0, k, F.tasks[size_t(k)], n_rtiles, F.piece);
+        task_tiles(q ? queued : tiles, 0, k, F.tasks[size_t(k)], n_rtiles);
         if (q)
             for (size_t i = before; i < queued.size(); ++i) qtask.push_back(k);
     }
@@ -1869,7 +1869,7 @@ static std::pair<TcTile*, int> fused_tiles(TcFused& F, int n_rtiles, int order) 
     if (it != F.tiles.end()) return it->second;
     std::vector<TcTile> t;
     for (int32_t k : fused_order(F, order))
-        task_tiles(t, 0, k, F.tasks[size_t(k)], n_rtiles, F.piece);
+        task_tiles(t, 0, k, F.tasks[size_t(k)], n_rtiles);
     auto v = std::make_pair(dupload(t), int(t.size()));
     F.tiles[key] = v;
     return v;
@@ -2087,7 +2087,7 @@ std::pair<TcTile*, int> launch_tiles(TcLaunch& l, int n_rtiles, int order, bool 
         if (pair)  // a tile is one r-tile pair of the SM-pair kernel
             for (int rt = 0; rt < n_rtiles; ++rt) t.push_back(TcTile{0, k, rt, 0});
         else
-            task_tiles(t, 0, k, l.tasks[size_t(k)], n_rtiles, l.piece);
+            task_tiles(t, 0, k, l.tasks[size_t(k)], n_rtiles);
     }
     auto v = std::make_pair(dupload(t), int(t.size()));
     l.tiles[key] = v;

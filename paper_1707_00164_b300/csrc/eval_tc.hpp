@@ -49,19 +49,20 @@ struct TcTile {
 // Tiles of one task over n_rtiles 128-column tiles of r.  Two r-tiles per
 // tile feed two accumulators from each staged block stage: fewer staged
 // bytes per flop (a third fewer for a 256-row block, a quarter for 128
-// rows).  Accumulators of at most piece / 2 columns share one of the two
-// TMEM buffers, so tiles still alternate buffers and the epilogue of one
-// overlaps the MMAs of the next: such tasks take two r-tiles from
-// kTwoRtMinChunksNarrow chunks on.  Wider accumulators take both buffers,
-// which exposes the epilogue: only tasks of kTwoRtMinChunksWide chunks or
-// more that write a right-hand-side buffer (the leaves' scattered U rows
-// are slower to write) take two r-tiles then.
+// rows), and the block is read once per pair of r-tiles.  TMEM holds two
+// accumulator buffers of kAccBufCols columns; accumulators of at most
+// kAccBufCols / 2 columns share one buffer, so tiles still alternate buffers
+// and the epilogue of one overlaps the MMAs of the next: such tasks take two
+// r-tiles from kTwoRtMinChunksNarrow chunks on.  Wider accumulators take both
+// buffers, which exposes the epilogue: only tasks of kTwoRtMinChunksWide
+// chunks or more that write a right-hand-side buffer (the leaves' scattered
+// U rows are slower to write) take two r-tiles then.
+constexpr int kAccBufCols = 256;
 constexpr int kTwoRtMinChunksNarrow = 4;
 constexpr int kTwoRtMinChunksWide = 16;
-inline void task_tiles(std::vector<TcTile>& out, int32_t seg, int32_t task, const TcTask& tk, int n_rtiles,
-                       int piece) {
-    const bool two = 2 * tk.n_pad <= piece ? tk.nchunks >= kTwoRtMinChunksNarrow
-                                           : tk.nchunks >= kTwoRtMinChunksWide && tk.out_kind != OUT_U;
+inline void task_tiles(std::vector<TcTile>& out, int32_t seg, int32_t task, const TcTask& tk, int n_rtiles) {
+    const bool two = 2 * tk.n_pad <= kAccBufCols ? tk.nchunks >= kTwoRtMinChunksNarrow
+                                                 : tk.nchunks >= kTwoRtMinChunksWide && tk.out_kind != OUT_U;
     for (int rt = 0; rt < n_rtiles;) {
         const int w = two && rt + 1 < n_rtiles ? 2 : 1;
         out.push_back(TcTile{seg, task, int32_t(rt), int32_t(w)});
