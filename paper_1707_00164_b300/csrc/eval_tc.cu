@@ -351,6 +351,16 @@ __device__ __forceinline__ int tile_width(const TcTile& tt) { return tt.pad == 2
 // both when it has two accumulators of more than kAccBufCols / 2 columns (two
 // narrower ones share a buffer, at columns 0 and kAccBufCols / 2)
 __device__ __forceinline__ int acc_buffers(int nw, int n_pad) { return nw == 2 && 2 * n_pad > kAccBufCols ? 2 : 1; }
+// Row form of a tile (split BF16x3 only): a two-r-tile tile of a leaf task
+// (U rows, at most 128 of them) runs as ONE M = 128, N = 256 product per K
+// step, block rows x the two r-tiles' right-hand sides (the block as the A
+// operand, the two adjacent r-tile halves of the stage as one 256-row B
+// operand), instead of two M = 128 (r-tile) x N = n_pad products that each
+// read the block again: a quarter fewer shared-memory operand bytes per
+// flop.  The accumulator is then block row x r (TMEM lane = U row).
+__device__ __forceinline__ bool row_form(const TcTask& tk, int nw, bool split) {
+    return split && nw == 2 && tk.out_kind == OUT_U && !tk.accumulate && tk.n_pad <= 128;
+}
 
 // Epilogue of one tile: the accumulator rows of this thread (one column j
 // of r) for the task's n_pad block rows, read from TMEM at taddr and written
@@ -466,6 +476,31 @@ __device__ __forceinline__ void write_tile(const TcSeg& sg, const TcTask& tk, in
 // j >= r) and one thread stores each 16 KB chunk tile (and its lo copy) with
 // a bulk copy.  The store thread waits for the previous chunk's copies to
 // have read the staging tile before it is written again.
+// Epilogue of a row-form tile: this thread's accumulator lane is block row
+// n of the task, its 256 columns the r-tiles rt and rt + 1; written as U row
+// perm[out_pos + n] (FP32), 16 bytes per store where U allows it.
+__device__ __forceinline__ void write_rows(const TcSeg& sg, const TcTask& tk, int rt, int n, uint32_t taddr) {
+    const bool rv = n < tk.m;
+    float* urow = sg.U + (rv ? sg.perm[tk.out_pos + n] : 0) * sg.ldu;
+    const bool vec = ((reinterpret_cast<uintptr_t>(sg.U) | (uintptr_t(sg.ldu) * 4u)) & 15u) == 0;
+    for (int c0 = 0; c0 < 2 * 128; c0 += 32) {
+        const int j0 = rt * 128 + c0;
+        if (j0 >= sg.r) break;  // the same for the whole warp
+        float v[32];
+        tmem_ld32(taddr + uint32_t(c0), v);
+        if (!rv) continue;
+        if (vec && j0 + 32 <= sg.r) {
+#pragma unroll
+            for (int e = 0; e < 32; e += 4)
+                *reinterpret_cast<float4*>(urow + j0 + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e)
+                if (j0 + e < sg.r) urow[j0 + e] = v[e];
+        }
+    }
+}
+
 template <int MODE>
 __device__ __forceinline__ void write_tile_staged(const TcSeg& sg, const TcTask& tk, int rt, int row, uint32_t taddr,
                                                   uint8_t* stg, bool store_thread) {
@@ -937,7 +972,8 @@ __global__ void __launch_bounds__(GEN ? kGenThreads : 192, 1) tc_gemm_kernel(con
                 tc_fence_after();
                 const uint32_t tacc = tmem + uint32_t(b0 * kAccBufCols);  // r-tile rt + w: tacc + w * acc_step
                 const uint32_t acc_step = uint32_t(nb == 2 ? kAccBufCols : kAccBufCols / 2);
-                const uint32_t idesc = make_idesc(MODE == TC_TF32 ? 2 : 1, tk.n_pad);
+                const bool rowf = row_form(tk, nw, C::kSplit);
+                const uint32_t idesc = make_idesc(MODE == TC_TF32 ? 2 : 1, rowf ? 2 * 128 : tk.n_pad);
                 const uint32_t b_half = uint32_t(tk.n_pad) * 64u;
                 for (int q = 0; q < 2 * tk.nchunks / C::kSub; ++q) {
                     if (!mbar_wait(full_bar(stage), phase, p.err, kErrMma)) { ok = false; break; }
@@ -954,6 +990,22 @@ __global__ void __launch_bounds__(GEN ? kGenThreads : 192, 1) tc_gemm_kernel(con
                     // one descriptor per stage; the operands' descriptors differ
                     // from it by their shared-memory offsets (in 16-byte units)
                     const uint64_t d0 = sw64_desc(sA(stage, 0, 0));
+                    if constexpr (C::kSplit) {
+                        if (rowf) {  // block (M = 128) x both r-tiles (N = 256), hi.hi + lo.hi + hi.lo
+                            constexpr uint64_t lo = uint64_t(C::kPart >> 4);
+                            const uint64_t dk = d0 + (uint32_t(2 * C::kAUnit) >> 4);
+#pragma unroll
+                            for (int kk = 0; kk < 2; ++kk) {
+                                const uint64_t off = uint64_t(kk * 2);
+                                mma<MODE>(tacc, dk + off, d0 + off, idesc, (q > 0 || kk > 0) ? 1u : 0u);
+                                mma<MODE>(tacc, dk + lo + off, d0 + off, idesc, 1u);
+                                mma<MODE>(tacc, dk + off, d0 + lo + off, idesc, 1u);
+                            }
+                            mma_commit(empty_bar(stage));
+                            if (++stage == C::kStages) { stage = 0; phase ^= 1u; }
+                            continue;
+                        }
+                    }
 #pragma unroll
                     for (int hs = 0; hs < C::kSub; ++hs) {
                         const uint64_t db = d0 + (uint32_t(2 * C::kAUnit + hs * b_half) >> 4);
@@ -1031,7 +1083,14 @@ __global__ void __launch_bounds__(GEN ? kGenThreads : 192, 1) tc_gemm_kernel(con
             // stage reads was written earlier in the same evaluation; only the
             // in-place S2N pushes touch valid elements alone.
             const bool staged = !GEN && tk.out_kind != OUT_U && !tk.accumulate;
-            for (int w = 0; w < nw; ++w) {
+            if (row_form(tk, nw, C::kSplit)) {
+                write_rows(sg, tk, rt, row, tmem + uint32_t(b0 * kAccBufCols) + (uint32_t(q4 * 32) << 16));
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(tempty_bar(b0));
+                fills ^= 1u << b0;
+            }
+            for (int w = 0; w < nw && !row_form(tk, nw, C::kSplit); ++w) {
                 const uint32_t taddr = tmem + uint32_t(b0 * kAccBufCols + w * acc_step) + (uint32_t(q4 * 32) << 16);
                 if (staged)
                     write_tile_staged<MODE>(sg, tk, rt + w, row, taddr, stg, store_thread);
