@@ -319,12 +319,23 @@ def batching_bench(G, torch, dev, works, handles, steps, warmup, tuning=True):
     seq_ms = a.elapsed_time(b) / max(1, steps // 2)
     same = all(torch.equal(U, R) for U, R in zip(Us, seq_ref))
     nr = sum(w.n * w.r for w in works)
-    flops = 0.0
-    for w, h in zip(works, handles):
-        st = G.stats(h)
-        flops += w.r * (st["flops_n2s"] + st["flops_s2s"] + st["flops_s2n"] + st["flops_l2l"])
     peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
     peak = peaks.get("bf16_tflops", 1800.0) * NOMINAL_RATIO["bf16x3"]
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    # roofline of the batch: each instance's algorithmic flops (T part of P)
+    # and bytes (cached blocks and T entries once at 4 B, W read once,
+    # skeleton weights and potentials written and read once, U written once)
+    # against the split-BF16 tensor peak and the HBM bandwidth; the batch's
+    # bound is the sum over instances of the larger of the two times
+    flops = alg_bytes = bound_s = 0.0
+    for w, h in zip(works, handles):
+        st = G.stats(h)
+        f = w.r * (st["flops_n2s"] + st["flops_s2s"] + st["flops_s2n"] + st["flops_l2l"])
+        by = ((st["near_entries"] + st["far_entries"] + st["interp_t_entries"]) * 4 + w.n * w.r * 4
+              + 4 * st["skel_total"] * w.r * 4 + w.n * w.r * 4)
+        flops += f
+        alg_bytes += by
+        bound_s += max(f / (peak * 1e12), by / (hbm * 1e9))
     info = B.info()
     B.free()
     return {"workload": "64 Gaussian instances, N log-uniform [2048, 65536], d U{2..8}, h U[0.3, 1], "
@@ -333,6 +344,12 @@ def batching_bench(G, torch, dev, works, handles, steps, warmup, tuning=True):
             "unit": UNIT, "launches_per_batch": info["launches"], "graph": True,
             "flops_per_batch": flops, "tflops": flops / (ms / 1e3) / 1e12,
             "frac_of_split_bf16_peak": flops / (ms / 1e3) / 1e12 / peak,
+            "roofline": {"algorithmic_bytes": alg_bytes, "bound": "hbm" if alg_bytes / (hbm * 1e9) > flops / (peak * 1e12)
+                         else "tensor", "tensor_ms": flops / (peak * 1e12) * 1e3,
+                         "hbm_ms": alg_bytes / (hbm * 1e9) * 1e3, "bound_ms": bound_s * 1e3,
+                         "frac_of_bound": bound_s * 1e3 / ms, "hbm_gbs": hbm, "split_bf16_tflops": peak,
+                         "note": "per instance the larger of algorithmic flops / tensor peak and algorithmic bytes / "
+                                 "HBM bandwidth, summed over the instances (of measured peaks)"},
             "sequential_ms": seq_ms, "sequential_value": nr / (seq_ms / 1e3),
             "bitwise_equal_to_sequential": bool(same),
             "autotune": None if tune is None else {
