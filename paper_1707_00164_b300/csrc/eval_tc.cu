@@ -76,7 +76,7 @@ struct GenJob {
 // halves of two 128-row right-hand-side tiles and of one NMAX-row block tile
 // (twice for split BF16x3); as many stages as fit in about 200 KB of shared
 // memory, so a lower ceiling buys a deeper pipeline.
-template <int MODE, int NMAX = kMaxN>
+template <int MODE, int NMAX = kMaxN, int W = 2>
 struct Cfg {
     static constexpr bool kSplit = MODE == TC_BF16X3;
     // K-halves per stage: one for split BF16x3 (a stage of two r-tiles and a
@@ -84,7 +84,8 @@ struct Cfg {
     static constexpr int kSub = kSplit ? 1 : 2;
     static constexpr int kHalfA = 128 * 64;      // one K-half of a right-hand-side tile
     static constexpr int kAUnit = kSub * kHalfA;  // one r-tile's part of a stage
-    static constexpr int kPart = 2 * kAUnit + kSub * NMAX * 64;  // hi (or lo) part of a stage
+    static constexpr int kW = W;                  // r-tiles a stage can hold
+    static constexpr int kPart = kW * kAUnit + kSub * NMAX * 64;  // hi (or lo) part of a stage
     static constexpr int kStageBytes = (kSplit ? 2 : 1) * kPart;
     static constexpr int kStages = (200 * 1024 / kStageBytes) < 8 ? (200 * 1024 / kStageBytes) : 8;
     static constexpr int kSmem = kStages * kStageBytes + 1024 + 256;  // + alignment slack, barriers
@@ -103,10 +104,16 @@ struct Cfg {
     static_assert(kSmem + kGenBytes <= 227 * 1024, "shared memory per CTA with generator warps");
     static_assert(kSmem + kEpiBytes <= 227 * 1024, "shared memory per CTA with the epilogue staging tile");
 };
+// Stage layout of tc_gemm_kernel<MODE, NMAX, GEN>: the generator variant of
+// the 128-row kernel holds four r-tiles per stage, so a tile can cover four
+// r-tiles and each generated block stage serves all of them (each block is
+// generated once per four r-tiles instead of once per two).
+template <int MODE, int NMAX, bool GEN>
+using KCfg = Cfg<MODE, NMAX, (GEN && NMAX == 128) ? 4 : 2>;
 // dynamic shared memory of tc_gemm_kernel<MODE, NMAX, GEN>
 template <int MODE, int NMAX, bool GEN>
 constexpr int gemm_smem() {
-    return Cfg<MODE, NMAX>::kSmem + (GEN ? Cfg<MODE, NMAX>::kGenBytes : Cfg<MODE, NMAX>::kEpiBytes);
+    return KCfg<MODE, NMAX, GEN>::kSmem + (GEN ? KCfg<MODE, NMAX, GEN>::kGenBytes : KCfg<MODE, NMAX, GEN>::kEpiBytes);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -346,11 +353,17 @@ __device__ __forceinline__ TcTile fetch_tile(const TcParams& p, int t) {
 }
 // r-tiles a tile covers: rt alone, or rt and rt + 1 (two accumulators fed
 // from one block stage)
-__device__ __forceinline__ int tile_width(const TcTile& tt) { return tt.pad == 2 ? 2 : 1; }
+__device__ __forceinline__ int tile_width(const TcTile& tt) { return tt.pad == 2 || tt.pad == 4 ? tt.pad : 1; }
 // TMEM accumulator buffers (kAccBufCols columns each) a tile takes: one, or
 // both when it has two accumulators of more than kAccBufCols / 2 columns (two
 // narrower ones share a buffer, at columns 0 and kAccBufCols / 2)
-__device__ __forceinline__ int acc_buffers(int nw, int n_pad) { return nw == 2 && 2 * n_pad > kAccBufCols ? 2 : 1; }
+__device__ __forceinline__ int acc_buffers(int nw, int n_pad) {
+    return nw == 4 || (nw == 2 && 2 * n_pad > kAccBufCols) ? 2 : 1;
+}
+// TMEM columns between the accumulators of consecutive r-tiles of a tile:
+// a buffer each, or half a buffer (two per buffer; four r-tiles of at most
+// kAccBufCols / 2 columns fill both buffers)
+__device__ __forceinline__ int acc_stride(int nw, int nb) { return nb == 2 && nw == 2 ? kAccBufCols : kAccBufCols / 2; }
 // Row form of a tile (split BF16x3 only): a two-r-tile tile of a leaf task
 // (U rows, at most 128 of them) runs as ONE M = 128, N = 256 product per K
 // step, block rows x the two r-tiles' right-hand sides (the block as the A
@@ -683,7 +696,7 @@ __device__ __forceinline__ void gen_stage(GenRow<DP>& R, const GenJob& jb, const
 template <int MODE, int NMAX, int DP>
 __device__ __noinline__ int gen_loop(const TcParams& p, const GenJob* jobs, const float* colring, uint8_t* base,
                                      uint64_t* gbars, int& seq, int gw, int lane) {
-    using C = Cfg<MODE, NMAX>;
+    using C = KCfg<MODE, NMAX, true>;
     GenRow<DP> R;
     R.rows = -1;
     R.seg = R.rb = -1;
@@ -706,7 +719,7 @@ __device__ __noinline__ int gen_loop(const TcParams& p, const GenJob* jobs, cons
         if (jb.stop) return -1;
         const TcSeg& sg = p.segs[jb.seg];
         if (sg.dpad != DP) return sg.dpad;
-        uint8_t* bh = base + jb.stage * C::kStageBytes + 2 * C::kAUnit;
+        uint8_t* bh = base + jb.stage * C::kStageBytes + C::kW * C::kAUnit;
         uint8_t* bl = bh + C::kPart;  // split BF16x3: the lo copy of the stage
         const bool gauss = sg.gen_kind == GOFMM_GEN_GAUSSIAN;
         GenConst gc;
@@ -735,7 +748,7 @@ __device__ __noinline__ int gen_loop(const TcParams& p, const GenJob* jobs, cons
 // next.
 template <int MODE, int NMAX, bool GEN>
 __global__ void __launch_bounds__(GEN ? kGenThreads : 192, 1) tc_gemm_kernel(const __grid_constant__ TcParams p) {
-    using C = Cfg<MODE, NMAX>;
+    using C = KCfg<MODE, NMAX, GEN>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* bars = reinterpret_cast<uint64_t*>(base + C::kStages * C::kStageBytes);
@@ -762,10 +775,10 @@ __global__ void __launch_bounds__(GEN ? kGenThreads : 192, 1) tc_gemm_kernel(con
     // dynamic tile claiming from a counter (with dependency waits where the
     // segments carry dependency arrays), else a static round-robin split
     const bool dyn = p.tile_next != nullptr;
-    // stage s: A0_hi | A1_hi | B_hi | (A0_lo | A1_lo | B_lo): kSub K-halves of
-    // the right-hand-side tiles of r-tiles rt and rt + 1 and of the block tile
+    // stage s: A0_hi .. A(kW-1)_hi | B_hi | (A0_lo .. | B_lo): kSub K-halves of
+    // the right-hand-side tiles of r-tiles rt .. rt + kW - 1 and of the block tile
     auto sA = [&](int s, int lo, int w) { return s_base + s * C::kStageBytes + lo * C::kPart + w * C::kAUnit; };
-    auto sB = [&](int s, int lo) { return s_base + s * C::kStageBytes + lo * C::kPart + 2 * C::kAUnit; };
+    auto sB = [&](int s, int lo) { return s_base + s * C::kStageBytes + lo * C::kPart + C::kW * C::kAUnit; };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ntiles = p.ntiles;
@@ -971,7 +984,7 @@ __global__ void __launch_bounds__(GEN ? kGenThreads : 192, 1) tc_gemm_kernel(con
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t tacc = tmem + uint32_t(b0 * kAccBufCols);  // r-tile rt + w: tacc + w * acc_step
-                const uint32_t acc_step = uint32_t(nb == 2 ? kAccBufCols : kAccBufCols / 2);
+                const uint32_t acc_step = uint32_t(acc_stride(nw, nb));
                 const bool rowf = row_form(tk, nw, C::kSplit);
                 const uint32_t idesc = make_idesc(MODE == TC_TF32 ? 2 : 1, rowf ? 2 * 128 : tk.n_pad);
                 const uint32_t b_half = uint32_t(tk.n_pad) * 64u;
@@ -993,7 +1006,7 @@ __global__ void __launch_bounds__(GEN ? kGenThreads : 192, 1) tc_gemm_kernel(con
                     if constexpr (C::kSplit) {
                         if (rowf) {  // block (M = 128) x both r-tiles (N = 256), hi.hi + lo.hi + hi.lo
                             constexpr uint64_t lo = uint64_t(C::kPart >> 4);
-                            const uint64_t dk = d0 + (uint32_t(2 * C::kAUnit) >> 4);
+                            const uint64_t dk = d0 + (uint32_t(C::kW * C::kAUnit) >> 4);
 #pragma unroll
                             for (int kk = 0; kk < 2; ++kk) {
                                 const uint64_t off = uint64_t(kk * 2);
@@ -1008,13 +1021,13 @@ __global__ void __launch_bounds__(GEN ? kGenThreads : 192, 1) tc_gemm_kernel(con
                     }
 #pragma unroll
                     for (int hs = 0; hs < C::kSub; ++hs) {
-                        const uint64_t db = d0 + (uint32_t(2 * C::kAUnit + hs * b_half) >> 4);
+                        const uint64_t db = d0 + (uint32_t(C::kW * C::kAUnit + hs * b_half) >> 4);
 #pragma unroll
                         for (int kk = 0; kk < 2; ++kk) {
                             const uint64_t off = uint64_t(kk * 2);  // 32 bytes per MMA K step
                             const uint32_t acc_in = (q > 0 || hs > 0 || kk > 0) ? 1u : 0u;
 #pragma unroll
-                            for (int w = 0; w < 2; ++w) {
+                            for (int w = 0; w < C::kW; ++w) {
                                 if (w < nw) {
                                     const uint64_t da = d0 + uint64_t((w * C::kAUnit + hs * C::kHalfA) >> 4) + off;
                                     const uint32_t tw = tacc + uint32_t(w) * acc_step;
@@ -1069,7 +1082,8 @@ __global__ void __launch_bounds__(GEN ? kGenThreads : 192, 1) tc_gemm_kernel(con
             const int nb = acc_buffers(nw, tk.n_pad);
             const int b0 = nb == 2 ? 0 : bnext;
             if (nb == 1) bnext ^= 1;
-            const int acc_step = nb == 2 ? kAccBufCols : kAccBufCols / 2;
+            const int acc_step = acc_stride(nw, nb);
+            const int per_buf = nb == 2 ? nw / 2 : nw;  // accumulators in one buffer
             bool ok = true;
             for (int b = 0; b < nb && ok; ++b)
                 ok = mbar_wait(tfull_bar(b0 + b), (fills >> (b0 + b)) & 1u, p.err, kErrEpilogue);
@@ -1099,8 +1113,8 @@ __global__ void __launch_bounds__(GEN ? kGenThreads : 192, 1) tc_gemm_kernel(con
                 // an accumulator buffer is free for the MMAs of a later tile as
                 // soon as this tile's accumulators in it are read (a tile with
                 // two buffers frees the first before draining the second)
-                if (nb == 2 || w == nw - 1) {
-                    const int b = nb == 2 ? w : 0;
+                if ((w + 1) % per_buf == 0) {
+                    const int b = w / per_buf;
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(tempty_bar(b0 + b));
@@ -1593,6 +1607,7 @@ static void build_fused(const Structure& st, TcPrec& T, TcFused& F, unsigned sta
     std::vector<std::pair<int, int>> group;  // (stage, tree level) of every task
     std::vector<int64_t> node_of;
     F.piece = T.piece;
+    F.wmax = T.gen && T.piece == 128 ? 4 : 2;  // the kernel variant's stage holds four r-tiles
     F.tasks.clear();
     F.slabs.clear();
     F.task_stage.clear();
@@ -1861,7 +1876,7 @@ static TcFused::Ready& ready_tiles(TcFused& F, int n_rtiles) {
     for (int32_t k : F.order_local) {
         const bool q = F.task_stage[size_t(k)] >= 3;
         const size_t before = q ? queued.size() : tiles.size();
-        task_tiles(q ? queued : tiles, 0, k, F.tasks[size_t(k)], n_rtiles);
+        task_tiles(q ? queued : tiles, 0, k, F.tasks[size_t(k)], n_rtiles, F.wmax);
         if (q)
             for (size_t i = before; i < queued.size(); ++i) qtask.push_back(k);
     }
@@ -1891,7 +1906,7 @@ static TcFused::Ready& ready_tiles(TcFused& F, int n_rtiles) {
         d.erase(std::unique(d.begin(), d.end()), d.end());
         for (const auto& x : d) {
             need(x.first, x.second);
-            for (int w = 0; w < (t.pad == 2 ? 2 : 1); ++w) {
+            for (int w = 0; w < tile_width_host(t); ++w) {
                 cons[size_t(x.first) * size_t(n_rtiles) + size_t(t.rt + w)].push_back(i);
                 ++pending[size_t(i)];
             }
@@ -1928,7 +1943,7 @@ static std::pair<TcTile*, int> fused_tiles(TcFused& F, int n_rtiles, int order) 
     if (it != F.tiles.end()) return it->second;
     std::vector<TcTile> t;
     for (int32_t k : fused_order(F, order))
-        task_tiles(t, 0, k, F.tasks[size_t(k)], n_rtiles);
+        task_tiles(t, 0, k, F.tasks[size_t(k)], n_rtiles, F.wmax);
     auto v = std::make_pair(dupload(t), int(t.size()));
     F.tiles[key] = v;
     return v;
@@ -2060,6 +2075,7 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
         T.launches.push_back(std::move(tl));
     }
     T.b_bytes = bbytes;
+    for (TcLaunch& l : T.launches) l.wmax = T.gen && P == 128 ? 4 : 2;  // as the fused plans below
     // every range a kernel will touch, checked on the host before upload
     auto check = [](bool ok, const char* what) {
         if (!ok) fail(GOFMM_ERR_ARG, std::string("tensor-core plan out of range: ") + what);
@@ -2131,9 +2147,9 @@ static void set_smem_attr() {
 // share most of their far or near lists and re-read operands from L2.
 // With pair = true the list holds pairs of r-tiles (rt = pair index) for the
 // SM-pair kernel.
-std::pair<TcTile*, int> launch_tiles(TcLaunch& l, int n_rtiles, int order, bool pair) {
+std::pair<TcTile*, int> launch_tiles(TcLaunch& l, int n_rtiles, int order, bool pair, int wmax) {
     if (pair) n_rtiles = (n_rtiles + 1) / 2;
-    const int key = n_rtiles * 4 + (order != GOFMM_ORDER_CRITICAL ? 1 : 0) + (pair ? 2 : 0);
+    const int key = (n_rtiles * 4 + (order != GOFMM_ORDER_CRITICAL ? 1 : 0) + (pair ? 2 : 0)) * 8 + wmax;
     auto it = l.tiles.find(key);
     if (it != l.tiles.end()) return it->second;
     std::vector<int32_t> tasks(l.tasks.size());
@@ -2146,7 +2162,7 @@ std::pair<TcTile*, int> launch_tiles(TcLaunch& l, int n_rtiles, int order, bool 
         if (pair)  // a tile is one r-tile pair of the SM-pair kernel
             for (int rt = 0; rt < n_rtiles; ++rt) t.push_back(TcTile{0, k, rt, 0});
         else
-            task_tiles(t, 0, k, l.tasks[size_t(k)], n_rtiles);
+            task_tiles(t, 0, k, l.tasks[size_t(k)], n_rtiles, wmax);
     }
     auto v = std::make_pair(dupload(t), int(t.size()));
     l.tiles[key] = v;
@@ -2230,7 +2246,8 @@ void tc_prepare(Handle& H, DeviceState& D, int64_t r_max, int precision) {
     // every r-tile count up to the prepared one (the serving engine mixes r)
     for (TcLaunch& l : T->launches)
         for (int nrt = 1; nrt <= int(r_pad / 128); ++nrt)
-            launch_tiles(l, nrt, H.tc_order[T->mode], H.tc_schedule[T->mode] == GOFMM_SCHED_PAIR);
+            launch_tiles(l, nrt, H.tc_order[T->mode], H.tc_schedule[T->mode] == GOFMM_SCHED_PAIR,
+                         H.tc_schedule[T->mode] == GOFMM_SCHED_PAIR ? 2 : l.wmax);
     for (TcFused* F : {&T->fused, &T->fused_up, &T->fused_down}) {
         if (F->counters_nrt < int(r_pad / 128)) {
             dfree(F->d_counters);
@@ -2492,7 +2509,7 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
         int claim = 0;
         for (TcLaunch& l : T.launches) {
             if (l.stage != 2 || l.tasks.empty()) continue;
-            const auto tl = launch_tiles(l, n_rtiles, H.tc_order[T.mode]);
+            const auto tl = launch_tiles(l, n_rtiles, H.tc_order[T.mode], false, l.wmax);
             p.tiles = tl.first;
             p.ntiles = tl.second;
             p.segs[0] = make_seg(T, l, T.rt_hi, T.rt_lo, U, ldu, D.d_idx, r);
@@ -2515,7 +2532,7 @@ static int tc_launch_all(Handle& H, DeviceState& D, TcPrec& T, const float* W, i
         for (TcLaunch& l : T.launches) {
             while (stage_done < l.stage) CUDA_OK(cudaEventRecord(D.ev[++stage_done], s));
             if (l.tasks.empty()) continue;
-            const auto tl = launch_tiles(l, n_rtiles, H.tc_order[T.mode], pair);
+            const auto tl = launch_tiles(l, n_rtiles, H.tc_order[T.mode], pair, pair ? 2 : l.wmax);
             p.tiles = tl.first;
             p.ntiles = tl.second;
             p.segs[0] = make_seg(T, l, T.rt_hi, T.rt_lo, U, ldu, D.d_idx, r);

@@ -43,7 +43,7 @@ struct TcTask {
 };
 
 struct TcTile {
-    int32_t seg, task, rt, pad;  // pad = 2: r-tiles rt and rt + 1 (else rt alone)
+    int32_t seg, task, rt, pad;  // pad = 2 or 4: r-tiles rt .. rt + pad - 1 (else rt alone)
 };
 
 // Tiles of one task over n_rtiles 128-column tiles of r.  Two r-tiles per
@@ -60,15 +60,24 @@ struct TcTile {
 constexpr int kAccBufCols = 256;
 constexpr int kTwoRtMinChunksNarrow = 4;
 constexpr int kTwoRtMinChunksWide = 16;
-inline void task_tiles(std::vector<TcTile>& out, int32_t seg, int32_t task, const TcTask& tk, int n_rtiles) {
-    const bool two = 2 * tk.n_pad <= kAccBufCols ? tk.nchunks >= kTwoRtMinChunksNarrow
-                                                 : tk.nchunks >= kTwoRtMinChunksWide && tk.out_kind != OUT_U;
+// wmax = 4 (the generator variant of the 128-row kernel, whose stages hold
+// four r-tiles): narrow tasks take four r-tiles per tile where four remain,
+// filling both accumulator buffers; the block stage (generated in the
+// kernel) then serves four r-tiles.
+inline void task_tiles(std::vector<TcTile>& out, int32_t seg, int32_t task, const TcTask& tk, int n_rtiles,
+                       int wmax = 2) {
+    const bool narrow = 2 * tk.n_pad <= kAccBufCols;
+    const bool two = narrow ? tk.nchunks >= kTwoRtMinChunksNarrow
+                            : tk.nchunks >= kTwoRtMinChunksWide && tk.out_kind != OUT_U;
+    const bool four = wmax >= 4 && narrow && two;
     for (int rt = 0; rt < n_rtiles;) {
-        const int w = two && rt + 1 < n_rtiles ? 2 : 1;
+        const int w = four && rt + 3 < n_rtiles ? 4 : two && rt + 1 < n_rtiles ? 2 : 1;
         out.push_back(TcTile{seg, task, int32_t(rt), int32_t(w)});
         rt += w;
     }
 }
+// r-tiles of a tile (TcTile::pad)
+inline int tile_width_host(const TcTile& t) { return t.pad == 2 || t.pad == 4 ? t.pad : 1; }
 
 // One (evaluation, launch) pair inside a tensor-core launch: the tasks and
 // slabs of that launch of one compressed matrix, its B tiles, the RT buffers
@@ -161,7 +170,8 @@ struct TcLaunch {
     TcSlab* d_slabs = nullptr;
     int stage = 0;
     int piece = 256;  // task piece height of the plan
-    std::map<int, std::pair<TcTile*, int>> tiles;  // r-tiles -> tile list of this launch alone
+    int wmax = 2;     // r-tiles per tile at most in a launch of this plan's own kernel (task_tiles)
+    std::map<int, std::pair<TcTile*, int>> tiles;  // r-tiles, order, form -> tile list of this launch alone
 };
 
 // Every grouped GEMM of one evaluation as one dependency-driven launch.
@@ -173,6 +183,7 @@ struct TcFused {
     std::vector<int32_t> order_sched;  // a simulated list schedule's order (topological)
     std::vector<int32_t> order_levels;  // S2S top-down, each push level one S2S level later (topological)
     int piece = 256;                   // task piece height of the plan
+    int wmax = 2;                      // r-tiles per tile at most (task_tiles)
     TcTask* d_tasks = nullptr;
     TcSlab* d_slabs = nullptr;
     int32_t* d_dep_off = nullptr;
@@ -256,7 +267,7 @@ inline const std::vector<int32_t>& fused_order(const TcFused& F, int order) {
                                                                   : F.order;
 }
 // device tile list of one launch alone for n_rtiles r-tiles (cached in the launch)
-std::pair<TcTile*, int> launch_tiles(TcLaunch& l, int n_rtiles, int order, bool pair = false);
+std::pair<TcTile*, int> launch_tiles(TcLaunch& l, int n_rtiles, int order, bool pair = false, int wmax = 2);
 void tc_drop_plan(DeviceState& D, int precision);  // frees one mode's plan, stores and buffers
 void launch_gather(int mode, const TcPrec& T, const float* W, int64_t ldw, const int64_t* perm, uint8_t* wt_hi,
                    uint8_t* wt_lo, int r, cudaStream_t s);
