@@ -67,11 +67,13 @@ def test_generated_blocks_match_oracle(name, w, r, over, prec):
 
 
 def test_generated_blocks_every_configuration_bitwise_equal():
+    # r = 520: five r-tiles, so the 128-row generator kernel runs four-r-tile
+    # tiles (its stages hold four) beside a ragged single one
     w = wl.scaled(wl.C3, 3000)
     h, st, K = both(w, callback=False, cache_mode=G.CACHE_NONE, leaf_size=400, max_rank=300, tau=1e-6)
-    W = w.rhs(200)
+    W = w.rhs(520)
     prec = G.PREC_BF16X3
-    G.prepare(h, 200, prec)
+    G.prepare(h, 520, prec)
     out = []
     for piece in (256, 128):
         for sched in (G.SCHED_FUSED, G.SCHED_STAGED, G.SCHED_HYBRID):
@@ -79,7 +81,9 @@ def test_generated_blocks_every_configuration_bitwise_equal():
                 G.set_tc_config(h, prec, piece, sched, order)
                 out.append(run(h, W, prec))
     assert all(np.array_equal(o, out[0]) for o in out)
-    assert rel(out[0], O.evaluate(st, K, W)) <= TOL[prec]
+    ref = O.evaluate(st, K, W)
+    assert rel(out[0], ref) <= TOL[prec]
+    assert_tensor_close(out[0], ref, O.evaluate_abs(st, K, W), abs_product(K, W), prec)
     G.set_tc_config(h, prec, 128, G.SCHED_PAIR)
     with pytest.raises(G.GofmmError) as e:  # the pair kernel reads cached blocks only
         run(h, W, prec)
