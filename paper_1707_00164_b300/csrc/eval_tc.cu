@@ -351,12 +351,12 @@ __device__ __forceinline__ TcTile fetch_tile(const TcParams& p, int t) {
     tt.seg = k;
     return tt;
 }
-// r-tiles a tile covers: rt alone, or rt and rt + 1 (two accumulators fed
-// from one block stage)
+// r-tiles a tile covers: rt alone, or rt .. rt + 1 (rt .. rt + 3) with two
+// (four) accumulators fed from one block stage
 __device__ __forceinline__ int tile_width(const TcTile& tt) { return tt.pad == 2 || tt.pad == 4 ? tt.pad : 1; }
 // TMEM accumulator buffers (kAccBufCols columns each) a tile takes: one, or
-// both when it has two accumulators of more than kAccBufCols / 2 columns (two
-// narrower ones share a buffer, at columns 0 and kAccBufCols / 2)
+// both when it has two accumulators of more than kAccBufCols / 2 columns or
+// four (narrower ones share a buffer, at columns 0 and kAccBufCols / 2)
 __device__ __forceinline__ int acc_buffers(int nw, int n_pad) {
     return nw == 4 || (nw == 2 && 2 * n_pad > kAccBufCols) ? 2 : 1;
 }
