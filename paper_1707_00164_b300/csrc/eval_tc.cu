@@ -242,6 +242,9 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                  "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
 }
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -1084,6 +1087,25 @@ __global__ void __launch_bounds__(GEN ? kGenThreads : 192, 1) tc_gemm_kernel(con
             if (nb == 1) bnext ^= 1;
             const int acc_step = acc_stride(nw, nb);
             const int per_buf = nb == 2 ? nw / 2 : nw;  // accumulators in one buffer
+            if (tk.accumulate && tk.out_kind != OUT_U) {
+                // an in-place push adds to the node's u~ rows written long
+                // before (S2S): bring this thread's part of them into L2 while
+                // the MMAs run, so the read-modify-write below waits on L2,
+                // not DRAM, once per 32 rows
+                const int buf = tk.out_kind == OUT_WTIL ? 1 : 2;
+                for (int w = 0; w < nw; ++w) {
+                    if ((rt + w) * 128 + row >= sg.r) break;
+                    for (int c = 0; c * C::kKc < tk.n_pad; ++c) {
+                        const int64_t off = (int64_t(rt + w) * sg.rt_chunks[buf] + tk.out_pos + c) * kTileBytes;
+                        prefetch_l2(sg.rt_hi[buf] + off + swz(row, 0, 128));
+                        prefetch_l2(sg.rt_hi[buf] + off + swz(row, 64, 128));
+                        if constexpr (C::kSplit) {
+                            prefetch_l2(sg.rt_lo[buf] + off + swz(row, 0, 128));
+                            prefetch_l2(sg.rt_lo[buf] + off + swz(row, 64, 128));
+                        }
+                    }
+                }
+            }
             bool ok = true;
             for (int b = 0; b < nb && ok; ++b)
                 ok = mbar_wait(tfull_bar(b0 + b), (fills >> (b0 + b)) & 1u, p.err, kErrEpilogue);
