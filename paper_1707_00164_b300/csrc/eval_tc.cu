@@ -315,6 +315,17 @@ __device__ __forceinline__ uint32_t swz64(uint32_t row, uint32_t byte) {
 __device__ __forceinline__ uint32_t swz(uint32_t row, uint32_t byte, uint32_t rows) {
     return (byte >> 6) * rows * 64u + swz64(row, byte & 63u);
 }
+// Rows of r-tile rt of a right-hand-side (RT) tile that carry columns of r:
+// r rounded up to 16, minus the r-tiles before, at most 128.  Only these
+// rows are written (zeros from r on) and copied into shared memory, so a
+// K-half moves rt_rows * 64 bytes, a prefix of whole 8-row swizzle groups.
+// The stale rows past them in a stage only reach accumulator lanes of
+// columns j >= r (a lane of a transposed product is one column of r), and
+// nothing writes those lanes out.
+__device__ __forceinline__ int rt_rows(int r, int rt) {
+    const int v = ((r + 15) & ~15) - rt * 128;
+    return v < 0 ? 0 : v > 128 ? 128 : v;
+}
 
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -423,7 +434,9 @@ __device__ __forceinline__ void write_tile(const TcSeg& sg, const TcTask& tk, in
             }
             continue;
         }
-        if (tk.accumulate && !jv) continue;
+        // RT rows past rt_rows are never read: an in-place push skips the
+        // rows j >= r, a fresh output writes zeros up to r rounded to 16
+        if (tk.accumulate ? !jv : row >= rt_rows(sg.r, rt)) continue;
         // RT output: 32 consecutive k of this row, inside one chunk
         const int buf = tk.out_kind == OUT_WTIL ? 1 : 2;
         const int64_t chunk = tk.out_pos + n0 / C::kKc;
@@ -486,12 +499,6 @@ __device__ __forceinline__ void write_tile(const TcSeg& sg, const TcTask& tk, in
     }
 }
 
-// Epilogue of one tile whose output is a fresh RT segment (no accumulation):
-// chunk by chunk, the four epilogue warps write their rows into the staging
-// tile in the operand layout (zeros in the padding columns and in rows
-// j >= r) and one thread stores each 16 KB chunk tile (and its lo copy) with
-// a bulk copy.  The store thread waits for the previous chunk's copies to
-// have read the staging tile before it is written again.
 // Epilogue of a row-form tile: this thread's accumulator lane is block row
 // n of the task, its 256 columns the r-tiles rt and rt + 1; written as U row
 // perm[out_pos + n] (FP32), 16 bytes per store where U allows it.
@@ -517,6 +524,13 @@ __device__ __forceinline__ void write_rows(const TcSeg& sg, const TcTask& tk, in
     }
 }
 
+// Epilogue of one tile whose output is a fresh RT segment (no accumulation):
+// chunk by chunk, the four epilogue warps write their rows into the staging
+// tile in the operand layout (zeros in the padding columns and in rows
+// r .. rt_rows) and one thread stores the tile's rt_rows leading rows of
+// each K-half (the whole 16 KB chunk tile when they are all 128), and its lo
+// copy, with bulk copies.  The store thread waits for the previous chunk's
+// copies to have read the staging tile before it is written again.
 template <int MODE>
 __device__ __forceinline__ void write_tile_staged(const TcSeg& sg, const TcTask& tk, int rt, int row, uint32_t taddr,
                                                   uint8_t* stg, bool store_thread) {
@@ -524,6 +538,8 @@ __device__ __forceinline__ void write_tile_staged(const TcSeg& sg, const TcTask&
     const int j = rt * 128 + row;
     const bool jv = j < sg.r;
     const int buf = tk.out_kind == OUT_WTIL ? 1 : 2;
+    const int rows = rt_rows(sg.r, rt);  // rows of the tile that are stored
+    const bool rw = row < rows;
     for (int ch = 0; ch * C::kKc < tk.out_cols; ++ch) {
         if (store_thread) bulk_wait_read();
         epi_bar_sync();
@@ -541,6 +557,7 @@ __device__ __forceinline__ void write_tile_staged(const TcSeg& sg, const TcTask&
                 for (int e = 0; e < 32; ++e) v[e] = 0.f;
             }
             const uint32_t byte0 = uint32_t(h * C::kEs);
+            if (!rw) continue;
             if constexpr (MODE == TC_TF32) {
 #pragma unroll
                 for (int piece = 0; piece < 8; ++piece)
@@ -568,8 +585,17 @@ __device__ __forceinline__ void write_tile_staged(const TcSeg& sg, const TcTask&
         epi_bar_sync();
         if (store_thread) {
             const int64_t at = (int64_t(rt) * sg.rt_chunks[buf] + tk.out_pos + ch) * kTileBytes;
-            bulk_s2g(sg.rt_hi[buf] + at, smem_u32(stg), kTileBytes);
-            if constexpr (C::kSplit) bulk_s2g(sg.rt_lo[buf] + at, smem_u32(stg + kTileBytes), kTileBytes);
+            if (rows == 128) {
+                bulk_s2g(sg.rt_hi[buf] + at, smem_u32(stg), kTileBytes);
+                if constexpr (C::kSplit) bulk_s2g(sg.rt_lo[buf] + at, smem_u32(stg + kTileBytes), kTileBytes);
+            } else {  // the leading rows of each K-half
+                for (int hf = 0; hf < 2; ++hf) {
+                    const uint32_t o = uint32_t(hf) * (kTileBytes / 2);
+                    bulk_s2g(sg.rt_hi[buf] + at + o, smem_u32(stg + o), uint32_t(rows) * 64u);
+                    if constexpr (C::kSplit)
+                        bulk_s2g(sg.rt_lo[buf] + at + o, smem_u32(stg + kTileBytes + o), uint32_t(rows) * 64u);
+                }
+            }
             bulk_commit();
         }
     }
@@ -850,6 +876,8 @@ __global__ void __launch_bounds__(GEN ? kGenThreads : 192, 1) tc_gemm_kernel(con
                 const int rt = tt.rt;
                 const int nw = tile_width(tt);
                 const uint32_t b_half = uint32_t(tk.n_pad) * 64u;  // one K-half of a block chunk tile
+                uint32_t a_stage = 0;  // right-hand-side bytes of one stage (hi or lo part)
+                for (int w = 0; w < nw; ++w) a_stage += uint32_t(C::kSub * rt_rows(sg.r, rt + w)) * 64u;
                 if (dyn && sg.dep_off) {
                     // results of other tiles of this launch the task needs
                     // before it starts (the operands are waited for slab by slab)
@@ -924,11 +952,24 @@ __global__ void __launch_bounds__(GEN ? kGenThreads : 192, 1) tc_gemm_kernel(con
                         // stage q: K-halves [q kSub, (q + 1) kSub) of the slab's chunks
                         const int64_t ah = int64_t(q) * C::kAUnit;
                         const int64_t bh = int64_t(q) * b_stage;
-                        mbar_expect_tx(full_bar(stage), (C::kSplit ? 2u : 1u) * (uint32_t(nw) * C::kAUnit + b_stage));
+                        // r-tiles past r / 16 rows: only their leading rows (rt_rows)
+                        mbar_expect_tx(full_bar(stage), (C::kSplit ? 2u : 1u) * (a_stage + b_stage));
                         for (int w = 0; w < nw; ++w) {
-                            bulk_g2s(sA(stage, 0, w), a_hi + w * a_rt + ah, C::kAUnit, full_bar(stage));
-                            if constexpr (C::kSplit)
-                                bulk_g2s(sA(stage, 1, w), a_lo + w * a_rt + ah, C::kAUnit, full_bar(stage));
+                            const uint32_t ab = uint32_t(rt_rows(sg.r, rt + w)) * 64u;
+                            if (ab == 128u * 64u) {
+                                bulk_g2s(sA(stage, 0, w), a_hi + w * a_rt + ah, C::kAUnit, full_bar(stage));
+                                if constexpr (C::kSplit)
+                                    bulk_g2s(sA(stage, 1, w), a_lo + w * a_rt + ah, C::kAUnit, full_bar(stage));
+                                continue;
+                            }
+#pragma unroll
+                            for (int hs = 0; hs < C::kSub; ++hs) {
+                                bulk_g2s(sA(stage, 0, w) + hs * C::kHalfA, a_hi + w * a_rt + ah + hs * C::kHalfA, ab,
+                                         full_bar(stage));
+                                if constexpr (C::kSplit)
+                                    bulk_g2s(sA(stage, 1, w) + hs * C::kHalfA, a_lo + w * a_rt + ah + hs * C::kHalfA,
+                                             ab, full_bar(stage));
+                            }
                         }
                         if (!gen) {
                             bulk_g2s(sB(stage, 0), sg.b_hi + sl.b_off + bh, b_stage, full_bar(stage));
@@ -1115,9 +1156,9 @@ __global__ void __launch_bounds__(GEN ? kGenThreads : 192, 1) tc_gemm_kernel(con
             if (!ok) break;
             tc_fence_after();
             // RT outputs write the whole output segment of the task (zeros in the
-            // padding columns and in rows j >= r), so every RT element a later
-            // stage reads was written earlier in the same evaluation; only the
-            // in-place S2N pushes touch valid elements alone.
+            // padding columns and in rows r .. rt_rows), so every RT element a
+            // later stage reads was written earlier in the same evaluation; only
+            // the in-place S2N pushes touch valid elements alone.
             const bool staged = !GEN && tk.out_kind != OUT_U && !tk.accumulate;
             if (row_form(tk, nw, C::kSplit)) {
                 write_rows(sg, tk, rt, row, tmem + uint32_t(b0 * kAccBufCols) + (uint32_t(q4 * 32) << 16));
@@ -1374,7 +1415,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
                 const int rt = 2 * tt.rt + int(crank);
                 const bool live = rt * 128 < sg.r;  // the odd half of the last pair may be padding
                 const uint32_t half = uint32_t(tk.n_pad) / 2u * 128u;
-                const uint32_t a_bytes = live ? uint32_t(kTileBytes) : 0u;
+                const uint32_t a_rows = uint32_t(rt_rows(sg.r, rt));  // leading rows of each K-half
+                const uint32_t a_bytes = 2u * a_rows * 64u;
                 for (int si = tk.slab0; si < tk.slab1 && ok; ++si) {
                     const TcSlab sl = sg.slabs[si];
                     if (sl.gen) {  // the pair schedule runs cached blocks only (the host refuses generated plans)
@@ -1389,16 +1431,27 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(192, 1)
                     for (int c = 0; c < sl.nchunks; ++c) {
                         if (!mbar_wait(empty_bar(stage), phase ^ 1u, p.err, kErrProducer)) { ok = false; break; }
                         mbar_expect_tx(full_bar(stage), (C::kSplit ? 2u : 1u) * (a_bytes + half));
-                        if (live)
+                        if (a_rows == 128)
                             bulk_g2s(sA(stage, 0), sg.rt_hi[sl.a_buf] + a_off + int64_t(c) * kTileBytes, kTileBytes,
                                      full_bar(stage));
+                        else if (live)
+                            for (int hf = 0; hf < 2; ++hf)
+                                bulk_g2s(sA(stage, 0) + hf * (kTileBytes / 2),
+                                         sg.rt_hi[sl.a_buf] + a_off + int64_t(c) * kTileBytes + hf * (kTileBytes / 2),
+                                         a_rows * 64u, full_bar(stage));
                         for (int h = 0; h < 2; ++h)
                             bulk_g2s(sB(stage, 0) + h * C::kBQuarter, sg.b_hi + b_off + int64_t(c) * b_row + h * (b_row / 2),
                                      qrt, full_bar(stage));
                         if constexpr (C::kSplit) {
-                            if (live)
+                            if (a_rows == 128)
                                 bulk_g2s(sA(stage, 1), sg.rt_lo[sl.a_buf] + a_off + int64_t(c) * kTileBytes,
                                          kTileBytes, full_bar(stage));
+                            else if (live)
+                                for (int hf = 0; hf < 2; ++hf)
+                                    bulk_g2s(sA(stage, 1) + hf * (kTileBytes / 2),
+                                             sg.rt_lo[sl.a_buf] + a_off + int64_t(c) * kTileBytes +
+                                                 hf * (kTileBytes / 2),
+                                             a_rows * 64u, full_bar(stage));
                             for (int h = 0; h < 2; ++h)
                                 bulk_g2s(sB(stage, 1) + h * C::kBQuarter,
                                          sg.b_lo + b_off + int64_t(c) * b_row + h * (b_row / 2), qrt, full_bar(stage));
@@ -1529,8 +1582,9 @@ __global__ void __launch_bounds__(256) tc_gather_kernel(const float* __restrict_
     const int rt = blockIdx.y;
     const int64_t pos = chunk_pos[c];
     const int valid = chunk_valid[c];
-    for (int e = threadIdx.x; e < 128 * C::kKc; e += blockDim.x) {
-        const int k = e / 128, jj = e % 128, j = rt * 128 + jj;
+    const int rows = rt_rows(r, rt);  // the rows later copies read (zeros from r on)
+    for (int e = threadIdx.x; e < rows * C::kKc; e += blockDim.x) {
+        const int k = e / rows, jj = e % rows, j = rt * 128 + jj;
         float x = 0.f;
         if (k < valid && j < r) x = W[perm[pos + k] * ldw + j];
         const uint32_t at = swz(uint32_t(jj), uint32_t(k * C::kEs), 128);
@@ -1546,6 +1600,7 @@ __global__ void __launch_bounds__(256) tc_gather_kernel(const float* __restrict_
     __syncthreads();
     const int64_t off = (int64_t(rt) * wt_chunks + c) * kTileBytes;
     for (int e = threadIdx.x; e < kTileBytes / 16; e += blockDim.x) {
+        if ((e % (kTileBytes / 32)) / 4 >= rows) continue;  // 16-byte group -> row of its K-half
         reinterpret_cast<uint4*>(wt_hi + off)[e] = reinterpret_cast<const uint4*>(hi)[e];
         if constexpr (C::kSplit) reinterpret_cast<uint4*>(wt_lo + off)[e] = reinterpret_cast<const uint4*>(lo)[e];
     }
