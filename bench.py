@@ -830,6 +830,11 @@ def native_arm(args):
         "s2n": (r * st["flops_s2n"], st["interp_t_entries"] * be + 2 * st["skel_total"] * r * be),
         "leaf": (r * st["flops_l2l"], st["near_entries"] * be + w.n * r * be + w.n * r * 4),
     }
+    if st_ms["s2n"] < 0.01 * st_ms["s2s"]:
+        # the tensor-core plan pulls each node's parent part into its S2S
+        # task (no S2N launches): the S2N work is timed with S2S
+        fs, bs = stage_work.pop("s2n")
+        stage_work["s2s"] = (stage_work["s2s"][0] + fs, stage_work["s2s"][1] + bs)
     per_stage = {}
     for k, (fl, by) in stage_work.items():
         t = st_ms[k] / 1e3

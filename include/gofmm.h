@@ -74,8 +74,9 @@ extern "C" {
 #define GOFMM_SCHED_PAIR 2     /* one launch per stage on SM pairs: M = 256
                                   MMAs over two r-tiles (tcgen05 cta_group::2) */
 #define GOFMM_SCHED_HYBRID 3   /* upward pass in one dependency-driven launch,
-                                  S2S in one launch, downward pass and leaves
-                                  in one dependency-driven launch             */
+                                  S2S (with the S2N parent parts) one launch
+                                  per level, leaves in one dependency-driven
+                                  launch                                      */
 #define GOFMM_ORDER_CRITICAL 0 /* fused launch: longest dependent chain first;
                                   staged launches: heaviest task first       */
 #define GOFMM_ORDER_LOCAL 1    /* fused: topological, (stage, level) groups by
@@ -86,14 +87,13 @@ extern "C" {
                                   be ready first, critical path among those
                                   ready); staged: heap order                 */
 #define GOFMM_ORDER_READY 3    /* fused: the upward pass and S2S in the
-                                  locality order, the downward pushes and the
-                                  leaves taken from a queue of tiles whose
-                                  inputs are complete (a batch: the locality
-                                  order); staged: heap order                 */
+                                  locality order, the leaves taken from a
+                                  queue of tiles whose inputs are complete
+                                  (a batch: the locality order); staged:
+                                  heap order                                 */
 #define GOFMM_ORDER_LEVELS 4   /* fused: the upward pass, then S2S level by
-                                  level from the top, the pushes into a level
-                                  after the S2S of the next level, then the
-                                  leaves; staged: heap order                 */
+                                  level from the top, then the leaves;
+                                  staged: heap order                         */
 
 /*
  * Entry callback: fill out[i*nJ + j] = K(I[i], J[j]) for 0 <= i < nI,
@@ -415,8 +415,11 @@ int gofmm_stats(const gofmm_handle* h, gofmm_stats_t* s);
  * cores) the stages are timed one by one.  enable = 0: off (repeated calls may replay a CUDA
  * graph).  gofmm_stage_times then synchronises on the last
  * event and fills ms[0..5] with the milliseconds of the last call's stages
- * (0 gather of W into tree order, 1 N2S upward pass, 2 S2S (one launch),
- * 3 S2N pushes level by level, 4 leaf S2N+L2L with scatter, 5 whole call)
+ * (0 gather of W into tree order, 1 N2S upward pass, 2 S2S (on the CUDA
+ * cores one launch; on the tensor cores one launch per level, top-down, each
+ * node's task also taking its parent's S2N part), 3 S2N pushes level by level
+ * (CUDA cores; zero on the tensor cores), 4 leaf S2N+L2L with scatter,
+ * 5 whole call)
  * and, if n > 6, ms[6] with the number of kernels the call launched.
  */
 int gofmm_set_timing(gofmm_handle* h, int enable);

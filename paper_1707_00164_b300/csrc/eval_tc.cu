@@ -434,8 +434,8 @@ __device__ __forceinline__ void write_tile(const TcSeg& sg, const TcTask& tk, in
             }
             continue;
         }
-        // RT rows past rt_rows are never read: an in-place push skips the
-        // rows j >= r, a fresh output writes zeros up to r rounded to 16
+        // RT rows past rt_rows are never read: an accumulating output skips
+        // the rows j >= r, a fresh output writes zeros up to r rounded to 16
         if (tk.accumulate ? !jv : row >= rt_rows(sg.r, rt)) continue;
         // RT output: 32 consecutive k of this row, inside one chunk
         const int buf = tk.out_kind == OUT_WTIL ? 1 : 2;
@@ -1129,10 +1129,11 @@ __global__ void __launch_bounds__(GEN ? kGenThreads : 192, 1) tc_gemm_kernel(con
             const int acc_step = acc_stride(nw, nb);
             const int per_buf = nb == 2 ? nw / 2 : nw;  // accumulators in one buffer
             if (tk.accumulate && tk.out_kind != OUT_U) {
-                // an in-place push adds to the node's u~ rows written long
-                // before (S2S): bring this thread's part of them into L2 while
+                // an accumulating right-hand-side output adds to rows written
+                // long before: bring this thread's part of them into L2 while
                 // the MMAs run, so the read-modify-write below waits on L2,
-                // not DRAM, once per 32 rows
+                // not DRAM, once per 32 rows (the plans built here have no
+                // such task: the downward pass pulls, see build_tc_plan)
                 const int buf = tk.out_kind == OUT_WTIL ? 1 : 2;
                 for (int w = 0; w < nw; ++w) {
                     if ((rt + w) * 128 + row >= sg.r) break;
@@ -1158,7 +1159,7 @@ __global__ void __launch_bounds__(GEN ? kGenThreads : 192, 1) tc_gemm_kernel(con
             // RT outputs write the whole output segment of the task (zeros in the
             // padding columns and in rows r .. rt_rows), so every RT element a
             // later stage reads was written earlier in the same evaluation; only
-            // the in-place S2N pushes touch valid elements alone.
+            // accumulating outputs touch valid elements alone.
             const bool staged = !GEN && tk.out_kind != OUT_U && !tk.accumulate;
             if (row_form(tk, nw, C::kSplit)) {
                 write_rows(sg, tk, rt, row, tmem + uint32_t(b0 * kAccBufCols) + (uint32_t(q4 * 32) << 16));
@@ -1642,7 +1643,8 @@ __global__ void tc_tile_kernel(const TileJob* __restrict__ jobs, const float* __
 // ------------------------------------------------------------------ host --
 // One launch for every grouped GEMM of an evaluation.  Completion counters
 // per (node, r-tile): w~ written (N2S), u~ written by S2S, u~ final (after
-// the S2N push when there is one).  Each task waits for the counters of what
+// the S2N push when there is one; with the S2N parent part pulled into the
+// S2S task, as build_tc_plan does, that is the S2S task itself).  Each task waits for the counters of what
 // it reads and bumps the counters of what it writes; tasks are ordered by
 // the length of the dependent work that follows them (critical path first),
 // which is a topological order.
@@ -1745,7 +1747,8 @@ static void build_fused(const Structure& st, TcPrec& T, TcFused& F, unsigned sta
             std::sort(d.begin(), d.end());
             d.erase(std::unique(d.begin(), d.end()), d.end());
             // the slabs' operand dependencies are waited for slab by slab in
-            // the kernel; the rest (an S2N push waiting for its node's S2S
+            // the kernel (an S2S task's last slab, its parent's u~, only after
+            // its far field); the rest (an S2N push waiting for its node's S2S
             // result) before the first copy
             for (auto& x : d) {
                 if (std::find(slab_deps.begin(), slab_deps.end(), x) != slab_deps.end()) continue;
@@ -1884,12 +1887,12 @@ static void build_fused(const Structure& st, TcPrec& T, TcFused& F, unsigned sta
         }
     }
     // Level order: the upward pass (as in the locality order), then the S2S
-    // tasks level by level from the top (heap order inside a level), with the
-    // pushes into level l placed after the S2S tasks of level l + 1: when a
-    // push is claimed, its node's S2S and its parent's push were claimed a
-    // whole level of S2S work earlier, so the downward pass runs beside the
-    // far field instead of after it; then the pushes into the deepest level
-    // and the leaves.  Topological (checked below).
+    // tasks level by level from the top (heap order inside a level), with
+    // S2N pushes into level l, where a plan has them, placed after the S2S
+    // tasks of level l + 1; then the leaves.  With the parent part pulled
+    // into each S2S task (build_tc_plan) a node's task is claimed a whole
+    // level after its parent's, so its wait before the last slab is short.
+    // Topological (checked below).
     {
         int L = 0;
         for (size_t t = 0; t < nt; ++t) L = std::max(L, group[t].second);
@@ -1941,7 +1944,8 @@ static void build_fused(const Structure& st, TcPrec& T, TcFused& F, unsigned sta
 
 // Ready-queue form of the fused launch for n_rtiles r-tiles: the upward
 // pass and S2S tiles in the locality order (claimed in list order), then the
-// push and leaf tiles, which enter the launch's queue once complete: for
+// push (where a plan has them) and leaf tiles, which enter the launch's
+// queue once complete: for
 // each of them the (counter, r-tile) pairs it waits for (its task's
 // dependencies and its slabs' operand counters over its r-tiles), inverted
 // into per-pair consumer lists; those with none start in the queue.
@@ -2060,97 +2064,142 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
 
     int64_t bbytes = 0;
     T.launches.clear();
-    for (const Launch& l : D.launches) {
-        TcLaunch tl;
-        tl.stage = l.stage;
-        for (const Task& t : l.tasks) {
-            int64_t out_base;
-            const int okind = task_out(t.flags);
-            if (okind == OUT_U) out_base = t.out_row;
-            else out_base = node_chunk.at(node_at_skel.at(t.out_row));
-            for (int64_t q = 0; q * P < std::max<int64_t>(t.m, 1); ++q) {
-                const int32_t mq = int32_t(std::min<int64_t>(P, t.m - q * P));
-                TcTask tt{};
-                tt.out_pos = okind == OUT_U ? out_base + q * P : out_base + q * P / kc;
-                tt.m = mq;
-                tt.n_pad = std::max(16, (mq + 15) / 16 * 16);
-                tt.slab0 = int32_t(tl.slabs.size());
-                tt.out_kind = okind;
-                tt.accumulate = task_accumulate(t.flags) ? 1 : 0;
-                tt.out_cols = okind == OUT_U ? tt.n_pad : int32_t(std::min<int64_t>(P, padk(t.m) - q * P));
-                for (int si = t.slab0; si < t.slab1; ++si) {
-                    const Slab& s = l.slabs[si];
-                    TcSlab ts{};
-                    ts.a_buf = s.b_src;
-                    ts.a_node0 = ts.a_node1 = -1;
-                    ts.dep_c0 = ts.dep_c1 = -1;
-                    if (s.b_src != B_WT) {
-                        const int64_t a = node_at_skel.at(s.b_row);
-                        ts.a_node0 = int32_t(a);
-                        if (s.k != int64_t(st.skel[a].size())) ts.a_node1 = int32_t(a + 1);  // [w~_l; w~_r]
-                    }
-                    if (s.a_src == A_GEN) {
-                        // block entries generated in the kernel from the row
-                        // list (this piece's rows) and the column list
-                        const int64_t a = s.b_src == B_WT ? leaf_at_pos.at(s.b_row) : node_at_skel.at(s.b_row);
-                        ts.a_chunk0 = int32_t(s.b_src == B_WT ? leaf_chunk[a] : node_chunk[a]);
-                        ts.nchunks = int32_t(padk(s.k) / kc);
-                        ts.gen = 1;
-                        ts.b_off = s.a_off + q * P;
-                        ts.gen_cols = s.a_col;
-                        ts.k = s.k;
-                        T.gen = true;
-                        tt.nchunks += ts.nchunks;
-                        tl.slabs.push_back(ts);
-                        continue;
-                    }
-                    int64_t ksplit = s.k, kgap = 0, kpad;
-                    if (s.b_src == B_WT) {
-                        const int64_t a = leaf_at_pos.at(s.b_row);
-                        ts.a_chunk0 = int32_t(leaf_chunk[a]);
-                        kpad = padk(s.k);
-                    } else {
-                        const int64_t a = node_at_skel.at(s.b_row);
-                        const int64_t sa = int64_t(st.skel[a].size());
-                        ts.a_chunk0 = int32_t(node_chunk[a]);
-                        if (s.k == sa) {
-                            kpad = padk(sa);
-                        } else {  // [w~_l; w~_r]: two adjacent sibling segments
-                            const int64_t sb = int64_t(st.skel[a + 1].size());
-                            if (s.k != sa + sb || node_chunk[a + 1] != node_chunk[a] + padk(sa) / kc)
-                                fail(GOFMM_ERR_ARG, "unexpected slab layout in the tensor-core plan");
-                            ksplit = sa;
-                            kgap = padk(sa) - sa;
-                            kpad = padk(sa) + padk(sb);
-                        }
-                    }
-                    ts.nchunks = int32_t(kpad / kc);
-                    ts.b_off = bbytes;
-                    TileJob jb{};
-                    jb.src_off = s.a_off + q * P * int64_t(s.lda);
-                    jb.dst_off = bbytes;
-                    jb.src_ld = s.lda;
-                    jb.m = mq;
-                    jb.k = s.k;
-                    jb.n_pad = tt.n_pad;
-                    jb.nchunks = ts.nchunks;
-                    jb.k_split = int32_t(ksplit);
-                    jb.k_gap = int32_t(kgap);
-                    jb.src_store = s.a_src;
-                    jobs.push_back(jb);
-                    bbytes += int64_t(ts.nchunks) * tt.n_pad * 128;
+    // one task of the plan with the given slabs, as task pieces of at most P rows
+    auto emit = [&](TcLaunch& tl, const Task& t, const std::vector<const Slab*>& slabs, bool acc) {
+        int64_t out_base;
+        const int okind = task_out(t.flags);
+        if (okind == OUT_U) out_base = t.out_row;
+        else out_base = node_chunk.at(node_at_skel.at(t.out_row));
+        for (int64_t q = 0; q * P < std::max<int64_t>(t.m, 1); ++q) {
+            const int32_t mq = int32_t(std::min<int64_t>(P, t.m - q * P));
+            TcTask tt{};
+            tt.out_pos = okind == OUT_U ? out_base + q * P : out_base + q * P / kc;
+            tt.m = mq;
+            tt.n_pad = std::max(16, (mq + 15) / 16 * 16);
+            tt.slab0 = int32_t(tl.slabs.size());
+            tt.out_kind = okind;
+            tt.accumulate = acc ? 1 : 0;
+            tt.out_cols = okind == OUT_U ? tt.n_pad : int32_t(std::min<int64_t>(P, padk(t.m) - q * P));
+            for (const Slab* sp : slabs) {
+                const Slab& s = *sp;
+                TcSlab ts{};
+                ts.a_buf = s.b_src;
+                ts.a_node0 = ts.a_node1 = -1;
+                ts.dep_c0 = ts.dep_c1 = -1;
+                if (s.b_src != B_WT) {
+                    const int64_t a = node_at_skel.at(s.b_row);
+                    ts.a_node0 = int32_t(a);
+                    if (s.k != int64_t(st.skel[a].size())) ts.a_node1 = int32_t(a + 1);  // [w~_l; w~_r]
+                }
+                if (s.a_src == A_GEN) {
+                    // block entries generated in the kernel from the row
+                    // list (this piece's rows) and the column list
+                    const int64_t a = s.b_src == B_WT ? leaf_at_pos.at(s.b_row) : node_at_skel.at(s.b_row);
+                    ts.a_chunk0 = int32_t(s.b_src == B_WT ? leaf_chunk[a] : node_chunk[a]);
+                    ts.nchunks = int32_t(padk(s.k) / kc);
+                    ts.gen = 1;
+                    ts.b_off = s.a_off + q * P;
+                    ts.gen_cols = s.a_col;
+                    ts.k = s.k;
+                    T.gen = true;
                     tt.nchunks += ts.nchunks;
                     tl.slabs.push_back(ts);
+                    continue;
                 }
-                tt.slab1 = int32_t(tl.slabs.size());
-                tl.tasks.push_back(tt);
-                tl.task_node.push_back(okind == OUT_U ? st.leaf_node(leaf_at_pos.at(t.out_row))
-                                                      : node_at_skel.at(t.out_row));
+                int64_t ksplit = s.k, kgap = 0, kpad;
+                if (s.b_src == B_WT) {
+                    const int64_t a = leaf_at_pos.at(s.b_row);
+                    ts.a_chunk0 = int32_t(leaf_chunk[a]);
+                    kpad = padk(s.k);
+                } else {
+                    const int64_t a = node_at_skel.at(s.b_row);
+                    const int64_t sa = int64_t(st.skel[a].size());
+                    ts.a_chunk0 = int32_t(node_chunk[a]);
+                    if (s.k == sa) {
+                        kpad = padk(sa);
+                    } else {  // [w~_l; w~_r]: two adjacent sibling segments
+                        const int64_t sb = int64_t(st.skel[a + 1].size());
+                        if (s.k != sa + sb || node_chunk[a + 1] != node_chunk[a] + padk(sa) / kc)
+                            fail(GOFMM_ERR_ARG, "unexpected slab layout in the tensor-core plan");
+                        ksplit = sa;
+                        kgap = padk(sa) - sa;
+                        kpad = padk(sa) + padk(sb);
+                    }
+                }
+                ts.nchunks = int32_t(kpad / kc);
+                ts.b_off = bbytes;
+                TileJob jb{};
+                jb.src_off = s.a_off + q * P * int64_t(s.lda);
+                jb.dst_off = bbytes;
+                jb.src_ld = s.lda;
+                jb.m = mq;
+                jb.k = s.k;
+                jb.n_pad = tt.n_pad;
+                jb.nchunks = ts.nchunks;
+                jb.k_split = int32_t(ksplit);
+                jb.k_gap = int32_t(kgap);
+                jb.src_store = s.a_src;
+                jobs.push_back(jb);
+                bbytes += int64_t(ts.nchunks) * tt.n_pad * 128;
+                tt.nchunks += ts.nchunks;
+                tl.slabs.push_back(ts);
             }
+            tt.slab1 = int32_t(tl.slabs.size());
+            tl.tasks.push_back(tt);
+            tl.task_node.push_back(okind == OUT_U ? st.leaf_node(leaf_at_pos.at(t.out_row))
+                                                  : node_at_skel.at(t.out_row));
         }
-        tl.piece = T.piece;
-        T.launches.push_back(std::move(tl));
+    };
+    // The downward pass pulls instead of pushing: a node's S2S task takes
+    // the S2N slab of its parent's push into it, (P^T_{p~[l~r~]})[rows of the
+    // node] u~_p, as its last slab, so u~ of the node is written once, final
+    // (far field + parent part, one accumulation).  Every task of a level
+    // then reads its parent's final u~: the per-stage launches run the S2S
+    // tasks level by level from the top, and a dependency-driven launch
+    // waits for the parent only before that last slab, after the node's far
+    // field.  The separate in-place S2N launches go away.
+    std::map<int64_t, const Slab*> pull;  // node -> its parent's push slab into it
+    for (const Launch& l : D.launches)
+        if (l.stage == 3)
+            for (const Task& t : l.tasks) {
+                if (t.slab1 - t.slab0 != 1) fail(GOFMM_ERR_ARG, "unexpected S2N task in the tensor-core plan");
+                pull[node_at_skel.at(t.out_row)] = &l.slabs[size_t(t.slab0)];
+            }
+    for (const Launch& l : D.launches) {
+        if (l.stage == 3) continue;
+        auto slabs_of = [&](const Task& t) {
+            std::vector<const Slab*> v;
+            for (int si = t.slab0; si < t.slab1; ++si) v.push_back(&l.slabs[size_t(si)]);
+            return v;
+        };
+        if (l.stage != 2) {
+            TcLaunch tl;
+            tl.stage = l.stage;
+            for (const Task& t : l.tasks) emit(tl, t, slabs_of(t), task_accumulate(t.flags));
+            tl.piece = T.piece;
+            T.launches.push_back(std::move(tl));
+            continue;
+        }
+        // S2S: one launch per tree level, top-down (the order inside a level kept)
+        std::map<int, TcLaunch> lv;
+        for (const Task& t : l.tasks) {
+            const int64_t h = node_at_skel.at(t.out_row);
+            int lev = 0;
+            for (int64_t x = h + 1; x > 1; x >>= 1) ++lev;
+            auto v = slabs_of(t);
+            const auto it = pull.find(h);
+            if (it != pull.end()) v.push_back(it->second);
+            TcLaunch& tl = lv[lev];
+            tl.stage = 2;
+            emit(tl, t, v, task_accumulate(t.flags));
+            pull.erase(h);
+        }
+        for (auto& e : lv) {
+            e.second.piece = T.piece;
+            T.launches.push_back(std::move(e.second));
+        }
     }
+    if (!pull.empty()) fail(GOFMM_ERR_ARG, "an S2N push into a node without an S2S task");
     T.b_bytes = bbytes;
     for (TcLaunch& l : T.launches) l.wmax = T.gen && P == 128 ? 4 : 2;  // as the fused plans below
     // every range a kernel will touch, checked on the host before upload

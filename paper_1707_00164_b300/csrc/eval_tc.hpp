@@ -124,8 +124,9 @@ constexpr int kClaimSlots = 64;  // per-stage launches of one evaluation that cl
 
 // Ready queue of a dependency-driven launch of one evaluation (order
 // GOFMM_ORDER_READY).  The tiles tiles[0 .. n_static) are claimed in list
-// order; the tiles tiles[n_static .. n_static + n) (the downward pushes and
-// the leaves) only through a FIFO that holds a tile once every counter it
+// order; the tiles tiles[n_static .. n_static + n) (the downward pushes,
+// where a plan has them, and the leaves) only through a FIFO that holds a
+// tile once every counter it
 // waits for is complete: the epilogue that brings a counter to its final
 // arrival count req[c] takes one from the pending count of each queued tile
 // waiting on it (cons) and appends the tiles that reach zero.  A producer
@@ -181,7 +182,7 @@ struct TcFused {
     std::vector<int32_t> order;        // tasks in a topological, critical-path-first order
     std::vector<int32_t> order_local;  // topological; groups by critical path, heap order inside
     std::vector<int32_t> order_sched;  // a simulated list schedule's order (topological)
-    std::vector<int32_t> order_levels;  // S2S top-down, each push level one S2S level later (topological)
+    std::vector<int32_t> order_levels;  // S2S top-down (push levels, if any, one S2S level later), then leaves
     int piece = 256;                   // task piece height of the plan
     int wmax = 2;                      // r-tiles per tile at most (task_tiles)
     TcTask* d_tasks = nullptr;
