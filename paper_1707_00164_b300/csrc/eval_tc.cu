@@ -1610,7 +1610,8 @@ __global__ void __launch_bounds__(256) tc_gather_kernel(const float* __restrict_
 // Plan store blocks (row-major FP32) -> B tiles (prepare time).
 template <int MODE>
 __global__ void tc_tile_kernel(const TileJob* __restrict__ jobs, const float* __restrict__ kstore,
-                               const float* __restrict__ pstore, uint8_t* b_hi, uint8_t* b_lo) {
+                               const float* __restrict__ pstore, const int32_t* __restrict__ col_maps,
+                               uint8_t* b_hi, uint8_t* b_lo) {
     using C = Cfg<MODE>;
     const TileJob jb = jobs[blockIdx.x];
     const float* src = (jb.src_store == A_KSTORE ? kstore : pstore) + jb.src_off;
@@ -1621,7 +1622,8 @@ __global__ void tc_tile_kernel(const TileJob* __restrict__ jobs, const float* __
         const int n = rem / C::kKc, kk = rem % C::kKc;
         const int col = ch * C::kKc + kk;
         int sc = -1;
-        if (col < jb.k_split) sc = col;
+        if (jb.col_map_off >= 0) sc = col_maps[jb.col_map_off + col];
+        else if (col < jb.k_split) sc = col;
         else if (col >= jb.k_split + jb.k_gap) sc = col - jb.k_gap;
         float x = 0.f;
         if (n < jb.m && sc >= 0 && sc < jb.k) x = src[int64_t(n) * jb.src_ld + sc];
@@ -2030,7 +2032,8 @@ static std::pair<TcTile*, int> fused_tiles(TcFused& F, int n_rtiles, int order) 
     return v;
 }
 
-static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::vector<TileJob>& jobs) {
+static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::vector<TileJob>& jobs,
+                          std::vector<int32_t>& col_maps) {
     const int64_t nn = st.n_nodes(), nl = st.n_leaves();
     const int kc = T.kc;
     const int64_t P = T.piece;
@@ -2064,8 +2067,14 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
 
     int64_t bbytes = 0;
     T.launches.clear();
-    // one task of the plan with the given slabs, as task pieces of at most P rows
-    auto emit = [&](TcLaunch& tl, const Task& t, const std::vector<const Slab*>& slabs, bool acc) {
+    // one task of the plan with the given slabs, as task pieces of at most P
+    // rows; a slab may carry a column map of its block (SlabRef::cmap, with
+    // SlabRef::kpad columns in chunks of kc)
+    struct SlabRef {
+        const Slab* s;
+        int64_t cmap = -1, kpad = -1;
+    };
+    auto emit = [&](TcLaunch& tl, const Task& t, const std::vector<SlabRef>& slabs, bool acc) {
         int64_t out_base;
         const int okind = task_out(t.flags);
         if (okind == OUT_U) out_base = t.out_row;
@@ -2080,8 +2089,8 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
             tt.out_kind = okind;
             tt.accumulate = acc ? 1 : 0;
             tt.out_cols = okind == OUT_U ? tt.n_pad : int32_t(std::min<int64_t>(P, padk(t.m) - q * P));
-            for (const Slab* sp : slabs) {
-                const Slab& s = *sp;
+            for (const SlabRef& ref : slabs) {
+                const Slab& s = *ref.s;
                 TcSlab ts{};
                 ts.a_buf = s.b_src;
                 ts.a_node0 = ts.a_node1 = -1;
@@ -2110,7 +2119,7 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
                 if (s.b_src == B_WT) {
                     const int64_t a = leaf_at_pos.at(s.b_row);
                     ts.a_chunk0 = int32_t(leaf_chunk[a]);
-                    kpad = padk(s.k);
+                    kpad = ref.kpad >= 0 ? ref.kpad : padk(s.k);
                 } else {
                     const int64_t a = node_at_skel.at(s.b_row);
                     const int64_t sa = int64_t(st.skel[a].size());
@@ -2131,6 +2140,7 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
                 TileJob jb{};
                 jb.src_off = s.a_off + q * P * int64_t(s.lda);
                 jb.dst_off = bbytes;
+                jb.col_map_off = ref.cmap;
                 jb.src_ld = s.lda;
                 jb.m = mq;
                 jb.k = s.k;
@@ -2150,6 +2160,94 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
                                                   : node_at_skel.at(t.out_row));
         }
     };
+    // Full-rank subtrees.  A node whose rank is its column count (ncols =
+    // s) has P = Pi^T, a permutation, and if its children are full rank too,
+    // w~ of the node is W itself: row k of w~ is the row of W at tree
+    // position tpos[h][k].  A slab that reads w~ of such nodes then reads W
+    // (tree order) instead, its block's columns permuted to match (a column
+    // map applied when the block tiles are made; generated blocks take the
+    // tree-order column list): the same products, with no N2S task to wait
+    // for.  N2S tasks whose output nobody reads any more are dropped.
+    std::vector<std::vector<int64_t>> tpos(static_cast<size_t>(nn));
+    for (int64_t h = nn - 1; h >= 1; --h) {
+        const int64_t sh = int64_t(st.skel[h].size()), nc = st.ncols(h);
+        if (sh != nc || int64_t(st.P[h].size()) != sh * nc) continue;
+        if (!st.is_leaf(h) && (tpos[2 * h + 1].empty() || tpos[2 * h + 2].empty())) continue;
+        std::vector<int64_t> v(size_t(sh), -1);
+        bool perm_ok = true;
+        for (int64_t k = 0; k < sh && perm_ok; ++k) {
+            int64_t c1 = -1;
+            for (int64_t c = 0; c < nc && perm_ok; ++c) {
+                const double x = st.P[h][size_t(k * nc + c)];
+                if (x == 1.0 && c1 < 0) c1 = c;
+                else if (x != 0.0) perm_ok = false;
+            }
+            if (c1 < 0) { perm_ok = false; break; }
+            if (st.is_leaf(h)) v[size_t(k)] = st.node_off[h] + c1;
+            else {
+                const int64_t sl = int64_t(st.skel[2 * h + 1].size());
+                v[size_t(k)] = c1 < sl ? tpos[2 * h + 1][size_t(c1)] : tpos[2 * h + 2][size_t(c1 - sl)];
+            }
+        }
+        if (perm_ok) tpos[h] = std::move(v);
+    }
+    std::vector<std::vector<Slab>> dslabs(D.launches.size());
+    std::vector<std::vector<int64_t>> dcmap(D.launches.size()), dkpad(D.launches.size());
+    for (size_t li = 0; li < D.launches.size(); ++li) {
+        const Launch& l = D.launches[li];
+        dslabs[li] = l.slabs;
+        dcmap[li].assign(l.slabs.size(), -1);
+        dkpad[li].assign(l.slabs.size(), -1);
+        for (size_t si = 0; si < l.slabs.size(); ++si) {
+            Slab& sl = dslabs[li][si];
+            if (sl.b_src != B_WTIL) continue;
+            const int64_t a = node_at_skel.at(sl.b_row);
+            const bool two = sl.k != int64_t(st.skel[a].size());
+            if (tpos[a].empty() || (two && tpos[a + 1].empty())) continue;
+            // tree positions of the slab's right-hand-side rows: the leaves
+            // of the node (or of both siblings), consecutive
+            const int64_t t0 = st.node_off[a];
+            const int64_t b0 = leaf_at_pos.at(t0);
+            std::vector<int64_t> inv(size_t(sl.k), -1);  // tree position - t0 -> slab column
+            const int64_t sa = int64_t(st.skel[a].size());
+            for (int64_t c = 0; c < sl.k; ++c) {
+                const int64_t tp = c < sa ? tpos[a][size_t(c)] : tpos[a + 1][size_t(c - sa)];
+                if (tp < t0 || tp >= t0 + sl.k || inv[size_t(tp - t0)] >= 0)
+                    fail(GOFMM_ERR_ARG, "full-rank subtree rows out of place in the tensor-core plan");
+                inv[size_t(tp - t0)] = int32_t(c);
+            }
+            // the chunk layout of W in tree order: each leaf padded to whole chunks
+            std::vector<int32_t> map;
+            bool gapless = true;
+            for (int64_t b = b0, done = 0; done < sl.k; ++b) {
+                const int64_t h = st.leaf_node(b), ns = st.node_size[h];
+                if (done + ns < sl.k && ns % kc != 0) gapless = false;
+                for (int64_t i = 0; i < padk(ns); ++i)
+                    map.push_back(i < ns ? int32_t(inv[size_t(done + i)]) : -1);
+                done += ns;
+            }
+            if (sl.a_src == A_GEN) {
+                // generated blocks: the column list in tree order (no map),
+                // when the leaves leave no padding inside the range
+                if (!gapless) continue;
+                sl.a_col = t0;
+            } else {
+                dcmap[li][si] = int64_t(col_maps.size());
+                dkpad[li][si] = int64_t(map.size());
+                col_maps.insert(col_maps.end(), map.begin(), map.end());
+            }
+            sl.b_src = B_WT;
+            sl.b_row = t0;
+        }
+    }
+    std::vector<char> wtil_read(static_cast<size_t>(nn), 0);
+    for (size_t li = 0; li < D.launches.size(); ++li)
+        for (const Slab& sl : dslabs[li])
+            if (sl.b_src == B_WTIL) {
+                const int64_t a = node_at_skel.at(sl.b_row);
+                wtil_read[size_t(a)] = 1;
+                if (sl.k != int64_t(st.skel[a].size())) wtil_read[size_t(a + 1)] = 1;
+            }
     // The downward pass pulls instead of pushing: a node's S2S task takes
     // the S2N slab of its parent's push into it, (P^T_{p~[l~r~]})[rows of the
     // node] u~_p, as its last slab, so u~ of the node is written once, final
@@ -2165,17 +2263,23 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
                 if (t.slab1 - t.slab0 != 1) fail(GOFMM_ERR_ARG, "unexpected S2N task in the tensor-core plan");
                 pull[node_at_skel.at(t.out_row)] = &l.slabs[size_t(t.slab0)];
             }
-    for (const Launch& l : D.launches) {
+    for (size_t li = 0; li < D.launches.size(); ++li) {
+        const Launch& l = D.launches[li];
         if (l.stage == 3) continue;
         auto slabs_of = [&](const Task& t) {
-            std::vector<const Slab*> v;
-            for (int si = t.slab0; si < t.slab1; ++si) v.push_back(&l.slabs[size_t(si)]);
+            std::vector<SlabRef> v;
+            for (int si = t.slab0; si < t.slab1; ++si)
+                v.push_back(SlabRef{&dslabs[li][size_t(si)], dcmap[li][size_t(si)], dkpad[li][size_t(si)]});
             return v;
         };
         if (l.stage != 2) {
             TcLaunch tl;
             tl.stage = l.stage;
-            for (const Task& t : l.tasks) emit(tl, t, slabs_of(t), task_accumulate(t.flags));
+            for (const Task& t : l.tasks) {
+                // an N2S task whose w~ no slab reads (its readers take W)
+                if (l.stage == 1 && !wtil_read[size_t(node_at_skel.at(t.out_row))]) continue;
+                emit(tl, t, slabs_of(t), task_accumulate(t.flags));
+            }
             tl.piece = T.piece;
             T.launches.push_back(std::move(tl));
             continue;
@@ -2188,7 +2292,7 @@ static void build_tc_plan(const Structure& st, DeviceState& D, TcPrec& T, std::v
             for (int64_t x = h + 1; x > 1; x >>= 1) ++lev;
             auto v = slabs_of(t);
             const auto it = pull.find(h);
-            if (it != pull.end()) v.push_back(it->second);
+            if (it != pull.end()) v.push_back(SlabRef{it->second});
             TcLaunch& tl = lv[lev];
             tl.stage = 2;
             emit(tl, t, v, task_accumulate(t.flags));
@@ -2312,7 +2416,8 @@ TcPrec& tc_plan(Handle& H, DeviceState& D, int precision) {
         CUDA_OK(cudaGetDevice(&dev));
         CUDA_OK(cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, dev));  // the plan's orders use it
         std::vector<TileJob> jobs;
-        build_tc_plan(H.st, D, *t, jobs);
+        std::vector<int32_t> col_maps;
+        build_tc_plan(H.st, D, *t, jobs, col_maps);
         if (t->gen) {
             // point table in index-list order for the generator warps: the
             // coordinates in FP32, then the squared norm of those FP32
@@ -2342,15 +2447,17 @@ TcPrec& tc_plan(Handle& H, DeviceState& D, int precision) {
         if (t->split) t->b_lo = dalloc<uint8_t>(size_t(std::max<int64_t>(t->b_bytes, 16)));
         if (!jobs.empty()) {
             TileJob* dj = dupload(jobs);
+            int32_t* dm = dupload(col_maps.empty() ? std::vector<int32_t>{-1} : col_maps);
             const float* ks = static_cast<const float*>(D.fam[1].kstore);
             const float* ps = static_cast<const float*>(D.fam[1].pstore);
             const unsigned nj = unsigned(jobs.size());
-            if (mode == TC_TF32) tc_tile_kernel<TC_TF32><<<nj, 256>>>(dj, ks, ps, t->b_hi, t->b_lo);
-            else if (mode == TC_BF16) tc_tile_kernel<TC_BF16><<<nj, 256>>>(dj, ks, ps, t->b_hi, t->b_lo);
-            else tc_tile_kernel<TC_BF16X3><<<nj, 256>>>(dj, ks, ps, t->b_hi, t->b_lo);
+            if (mode == TC_TF32) tc_tile_kernel<TC_TF32><<<nj, 256>>>(dj, ks, ps, dm, t->b_hi, t->b_lo);
+            else if (mode == TC_BF16) tc_tile_kernel<TC_BF16><<<nj, 256>>>(dj, ks, ps, dm, t->b_hi, t->b_lo);
+            else tc_tile_kernel<TC_BF16X3><<<nj, 256>>>(dj, ks, ps, dm, t->b_hi, t->b_lo);
             CUDA_OK(cudaGetLastError());
             CUDA_OK(cudaDeviceSynchronize());
             dfree(dj);
+            dfree(dm);
         }
         t->d_err = dalloc<int>(1);
         CUDA_OK(cudaMemset(t->d_err, 0, sizeof(int)));

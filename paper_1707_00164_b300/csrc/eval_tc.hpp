@@ -158,8 +158,10 @@ struct TcParams {
 };
 
 // Conversion of one row-major FP32 block (plan store) into its B tiles.
+// col_map_off >= 0: destination column c of the tile takes source column
+// col_maps[col_map_off + c] (-1: zero) instead of the k_split / k_gap rule.
 struct TileJob {
-    int64_t src_off, dst_off;
+    int64_t src_off, dst_off, col_map_off;
     int32_t src_ld, m, k, n_pad, nchunks, k_split, k_gap, src_store;
 };
 
